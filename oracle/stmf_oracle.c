@@ -1,0 +1,471 @@
+/*
+ * Oracle for FastSTMF (Omanovic, Oblak, Curk: "FastSTMF: Efficient tropical
+ * matrix factorization algorithm for sparse data", arXiv 2205.06619).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded CPU
+ * restatement of the method, written from the paper's definitions and
+ * algorithms.  Only the tests, the package's smoke() check and the CPU
+ * baseline leg of bench.py may load it.  It shares no code, header, table or
+ * helper with the CUDA library, and the CUDA library never calls it.
+ *
+ * Arithmetic modes
+ *   mode 0 (ORC_FP64): every value and every operation in IEEE double.
+ *   mode 1 (ORC_FP32): values are floats held in doubles; every elementary
+ *     add / sub / div result is rounded to float.  For one operation on two
+ *     floats, rounding the double result to float gives the correctly rounded
+ *     float result (double has more than 2*24+2 significand bits), so this
+ *     mode reproduces IEEE fp32 arithmetic bit for bit.  max / min / abs are
+ *     exact in both modes.  Error sums (b-norm) are always accumulated in
+ *     double, in row-major order, from terms rounded in the mode's precision.
+ *
+ * Layouts: row-major doubles.  R is m x n, M is an m x n byte mask (1 = the
+ * entry of R is given/observed), U is m x r, V is r x n.
+ *
+ * Readings of places where the paper is silent or ambiguous are marked
+ * "Reading:" below; every one of them is also listed in the design notes.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_FP64 0
+#define ORC_FP32 1
+
+static double rnd(int mode, double x) { return mode == ORC_FP32 ? (double)(float)x : x; }
+static double add_(int mode, double a, double b) { return rnd(mode, a + b); }
+static double sub_(int mode, double a, double b) { return rnd(mode, a - b); }
+static double div_(int mode, double a, double b) { return rnd(mode, a / b); }
+
+int orc_version(void) { return 1; }
+
+/* ------------------------------------------------------------------------ */
+/* Random draws.  SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) used as a
+ * counter-based generator: draw(key, c) is the output of a SplitMix64 whose
+ * state was key and which has advanced c+1 times.                          */
+uint64_t orc_splitmix64(uint64_t key, uint64_t c)
+{
+    uint64_t z = key + (c + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Random permutation of 0..m-1 (Algorithm 3, "perm <- random permutation"):
+ * Fisher-Yates from the top: for a = m-1 .. 1, b = draw(seed, m-1-a) mod
+ * (a+1), swap perm[a] and perm[b].                                          */
+void orc_randperm(int m, uint64_t seed, int32_t *perm)
+{
+    for (int s = 0; s < m; ++s) perm[s] = s;
+    for (int a = m - 1; a >= 1; --a) {
+        uint64_t x = orc_splitmix64(seed, (uint64_t)(m - 1 - a));
+        int b = (int)(x % (uint64_t)(a + 1));
+        int32_t t = perm[a]; perm[a] = perm[b]; perm[b] = t;
+    }
+}
+
+/* Random Acol picks (Section "Comparison of strategies": U initialised by
+ * averaging randomly chosen columns of R).  For component l, p distinct
+ * columns of 0..n-1 by a partial Fisher-Yates on a fresh identity array:
+ * for q = 0..p-1, b = q + draw(seed ^ 0xA5A5..., l*p+q) mod (n-q).          */
+void orc_acol_picks(int n, int r, int p, uint64_t seed, int32_t *picks)
+{
+    int32_t *arr = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint64_t key = seed ^ 0xA5A5A5A5A5A5A5A5ull;
+    for (int l = 0; l < r; ++l) {
+        for (int t = 0; t < n; ++t) arr[t] = t;
+        for (int q = 0; q < p; ++q) {
+            uint64_t x = orc_splitmix64(key, (uint64_t)l * (uint64_t)p + (uint64_t)q);
+            int b = q + (int)(x % (uint64_t)(n - q));
+            int32_t t = arr[q]; arr[q] = arr[b]; arr[b] = t;
+            picks[l * p + q] = arr[q];
+        }
+    }
+    free(arr);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tropical product (Section "Related work", matrix multiplication):
+ * (U (x) V)_ij = max_l (U_il + V_lj).  Also returns, per entry, the argmax
+ * f(i,j) with ties going to the smaller l (Section "The ByRow strategy",
+ * definition of f(i,j)), and the runner-up P2_ij = max over l != f(i,j).
+ * P2 is -inf when r == 1.  A or P2 may be NULL.                             */
+void orc_maxplus(int mode, int m, int n, int r, const double *U, const double *V,
+                 double *P1, int32_t *A, double *P2)
+{
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) {
+            double best = -INFINITY, second = -INFINITY;
+            int arg = 0;
+            for (int l = 0; l < r; ++l) {
+                double s = add_(mode, U[(size_t)i * r + l], V[(size_t)l * n + j]);
+                if (s > best) { second = best; best = s; arg = l; }
+                else if (s > second) { second = s; }
+            }
+            P1[(size_t)i * n + j] = best;
+            if (A) A[(size_t)i * n + j] = arg;
+            if (P2) P2[(size_t)i * n + j] = second;
+        }
+}
+
+/* Min-plus residuation (Section "Related work", the (min,+) operation over
+ * given entries) in the two shapes the factor updates use:
+ *   residuate_v:  v = (-u)^T (x)* R,  v_t = min over given s of (R_st - u_s)
+ *   residuate_u:  u = R (x)* (-v)^T,  u_s = min over given t of (R_st - v_t)
+ * A row/column with no given entry yields +inf; the return value counts
+ * them (the method needs every row and column to have a given entry).      */
+int orc_residuate_v(int mode, int m, int n, const double *R, const uint8_t *M,
+                    const double *u, double *v)
+{
+    int empty = 0;
+    for (int t = 0; t < n; ++t) {
+        double best = INFINITY;
+        int any = 0;
+        for (int s = 0; s < m; ++s) {
+            if (!M[(size_t)s * n + t]) continue;
+            double d = sub_(mode, R[(size_t)s * n + t], u[s]);
+            if (!any || d < best) best = d;
+            any = 1;
+        }
+        v[t] = best;
+        empty += !any;
+    }
+    return empty;
+}
+
+int orc_residuate_u(int mode, int m, int n, const double *R, const uint8_t *M,
+                    const double *v, double *u)
+{
+    int empty = 0;
+    for (int s = 0; s < m; ++s) {
+        double best = INFINITY;
+        int any = 0;
+        for (int t = 0; t < n; ++t) {
+            if (!M[(size_t)s * n + t]) continue;
+            double d = sub_(mode, R[(size_t)s * n + t], v[t]);
+            if (!any || d < best) best = d;
+            any = 1;
+        }
+        u[s] = best;
+        empty += !any;
+    }
+    return empty;
+}
+
+/* Approximation error in the b-norm over the given entries (Section
+ * "Evaluation metrics", b-norm = sum of absolute values):
+ * f = sum over given (s,t) of |R_st - (U (x) V)_st|, recomputed from
+ * scratch, summed in double in row-major order.                            */
+double orc_error(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                 const double *U, const double *V)
+{
+    double f = 0.0;
+    for (int s = 0; s < m; ++s)
+        for (int t = 0; t < n; ++t) {
+            if (!M[(size_t)s * n + t]) continue;
+            double best = -INFINITY;
+            for (int l = 0; l < r; ++l) {
+                double x = add_(mode, U[(size_t)s * r + l], V[(size_t)l * n + t]);
+                if (x > best) best = x;
+            }
+            f += fabs(sub_(mode, R[(size_t)s * n + t], best));
+        }
+    return f;
+}
+
+static void get_col(int m, int r, const double *U, int k, double *u)
+{
+    for (int s = 0; s < m; ++s) u[s] = U[(size_t)s * r + k];
+}
+static void set_col(int m, int r, double *U, int k, const double *u)
+{
+    for (int s = 0; s < m; ++s) U[(size_t)s * r + k] = u[s];
+}
+
+/* F-ULF (Algorithm 1), in place on U and V; returns the new error.
+ * 1. U_ik <- R_ij - V_kj
+ * 2. V_k. <- (-U_.k)^T (x)* R
+ * 3. U_.k <- R (x)* (-V_k.)^T
+ * 4. f <- ||R - U (x) V||_b
+ * The caller keeps the old U_.k, V_k. for the revert.                      */
+double orc_fulf(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                double *U, double *V, int i, int j, int k)
+{
+    double *u = (double *)malloc(sizeof(double) * (size_t)m);
+    U[(size_t)i * r + k] = sub_(mode, R[(size_t)i * n + j], V[(size_t)k * n + j]);
+    get_col(m, r, U, k, u);
+    orc_residuate_v(mode, m, n, R, M, u, V + (size_t)k * n);
+    orc_residuate_u(mode, m, n, R, M, V + (size_t)k * n, u);
+    set_col(m, r, U, k, u);
+    free(u);
+    return orc_error(mode, m, n, r, R, M, U, V);
+}
+
+/* F-URF (Algorithm 2), in place; returns the new error.
+ * 1. V_kj <- R_ij - U_ik
+ * 2. U_.k <- R (x)* (-V_k.)^T
+ * 3. V_k. <- (-U_.k)^T (x)* R
+ * 4. f <- ||R - U (x) V||_b                                                 */
+double orc_furf(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                double *U, double *V, int i, int j, int k)
+{
+    double *u = (double *)malloc(sizeof(double) * (size_t)m);
+    V[(size_t)k * n + j] = sub_(mode, R[(size_t)i * n + j], U[(size_t)i * r + k]);
+    orc_residuate_u(mode, m, n, R, M, V + (size_t)k * n, u);
+    set_col(m, r, U, k, u);
+    orc_residuate_v(mode, m, n, R, M, u, V + (size_t)k * n);
+    free(u);
+    return orc_error(mode, m, n, r, R, M, U, V);
+}
+
+/* Selection statistics for row i (Section "The ByRow strategy"; Algorithm 3):
+ *   td(s,t)    = |R_st - max_l(U_sl + V_lt)|             (tropical distance)
+ *   td_col[t]  = sum over s of td(s,t)                     (err of ByRow)
+ *   colhist[t*r+l] = count of l in the multiset {f(s,t)}_s
+ *   rowhist[l]     = count of l in the multiset {f(i,t)}_t
+ * Reading: td is defined where R is given, so every sum and multiset runs
+ * over given entries only.  td_col is summed in double in row order.       */
+void orc_row_stats(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                   const double *U, const double *V, int i, double *td_col,
+                   int32_t *colhist, int32_t *rowhist)
+{
+    double *P1 = (double *)malloc(sizeof(double) * (size_t)m * n);
+    int32_t *A = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    orc_maxplus(mode, m, n, r, U, V, P1, A, NULL);
+    for (int t = 0; t < n; ++t) {
+        td_col[t] = 0.0;
+        for (int l = 0; l < r; ++l) colhist[(size_t)t * r + l] = 0;
+    }
+    for (int l = 0; l < r; ++l) rowhist[l] = 0;
+    for (int s = 0; s < m; ++s)
+        for (int t = 0; t < n; ++t) {
+            size_t e = (size_t)s * n + t;
+            if (!M[e]) continue;
+            td_col[t] += fabs(sub_(mode, R[e], P1[e]));
+            colhist[(size_t)t * r + A[e]] += 1;
+            if (s == i) rowhist[A[e]] += 1;
+        }
+    free(P1);
+    free(A);
+}
+
+/* Candidate order for row i (Algorithm 3): the columns j, sorted by
+ * td_col[j] in decreasing order, each with
+ *   k_j = argmax_l count_l({f(i,t)}_t  union  {f(t,j)}_t).
+ * Readings: only j with R_ij given are candidates (F-ULF needs R_ij);
+ * the multiset union adds multiplicities; equal td_col keep the smaller j
+ * first; equal counts keep the smaller l.  Returns the number of
+ * candidates; js/ks receive them in order.                                  */
+int orc_row_order(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                  const double *U, const double *V, int i, int32_t *js, int32_t *ks)
+{
+    double *td_col = (double *)malloc(sizeof(double) * (size_t)n);
+    int32_t *colhist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * r);
+    int32_t *rowhist = (int32_t *)malloc(sizeof(int32_t) * (size_t)r);
+    orc_row_stats(mode, m, n, r, R, M, U, V, i, td_col, colhist, rowhist);
+    int cnt = 0;
+    for (int j = 0; j < n; ++j)
+        if (M[(size_t)i * n + j]) js[cnt++] = j;
+    /* insertion sort, descending td_col; strict comparison keeps equal keys in
+     * increasing j (a stable sort of an increasing list)                    */
+    for (int a = 1; a < cnt; ++a) {
+        int32_t x = js[a];
+        int b = a - 1;
+        while (b >= 0 && td_col[js[b]] < td_col[x]) { js[b + 1] = js[b]; --b; }
+        js[b + 1] = x;
+    }
+    for (int a = 0; a < cnt; ++a) {
+        int j = js[a], best = 0;
+        int32_t bestc = -1;
+        for (int l = 0; l < r; ++l) {
+            int32_t c = rowhist[l] + colhist[(size_t)j * r + l];
+            if (c > bestc) { bestc = c; best = l; }
+        }
+        ks[a] = best;
+    }
+    free(td_col); free(colhist); free(rowhist);
+    return cnt;
+}
+
+/* One ByRow step on row i (Algorithm 3, body of the row loop).
+ * Reading of the garbled nesting: for each j in order, try F-ULF(i,j,k_j);
+ * if the error decreased keep it and end the row, else revert and try
+ * F-URF(i,j,k_j) the same way, else revert and go to the next j.
+ * "Decreases" is strict: f' < f.  On return *f holds the current error;
+ * out = {position in order, j, k, type (0 = F-ULF, 1 = F-URF)} of the kept
+ * update; *tried counts the candidates evaluated (both types count).
+ * Returns 1 if an update was kept, 0 if the row is left unchanged.         */
+int orc_row_step(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                 double *U, double *V, int i, double *f, int32_t *out, int64_t *tried)
+{
+    int32_t *js = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *ucol = (double *)malloc(sizeof(double) * (size_t)m);
+    double *vrow = (double *)malloc(sizeof(double) * (size_t)n);
+    int cnt = orc_row_order(mode, m, n, r, R, M, U, V, i, js, ks);
+    int kept = 0;
+    for (int a = 0; a < cnt && !kept; ++a) {
+        int j = js[a], k = ks[a];
+        for (int type = 0; type < 2; ++type) {
+            get_col(m, r, U, k, ucol);
+            memcpy(vrow, V + (size_t)k * n, sizeof(double) * (size_t)n);
+            double fn = type == 0 ? orc_fulf(mode, m, n, r, R, M, U, V, i, j, k)
+                                  : orc_furf(mode, m, n, r, R, M, U, V, i, j, k);
+            if (tried) *tried += 1;
+            if (fn < *f) {
+                *f = fn;
+                if (out) { out[0] = a; out[1] = j; out[2] = k; out[3] = type; }
+                kept = 1;
+                break;
+            }
+            set_col(m, r, U, k, ucol);
+            memcpy(V + (size_t)k * n, vrow, sizeof(double) * (size_t)n);
+        }
+    }
+    if (!kept && out) { out[0] = -1; out[1] = -1; out[2] = -1; out[3] = -1; }
+    free(js); free(ks); free(ucol); free(vrow);
+    return kept;
+}
+
+/* Random Acol initialisation of U (Section "Comparison of strategies"):
+ * U_sl = mean of the given entries R_s,c over the picked columns c of
+ * component l.  Readings: the sum runs over the picks in order; if none of
+ * the picks is given in row s, U_sl is the mean of the given entries of row
+ * s (summed in column order).                                               */
+void orc_acol_init(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                   const int32_t *picks, int p, double *U)
+{
+    for (int s = 0; s < m; ++s)
+        for (int l = 0; l < r; ++l) {
+            double sum = 0.0;
+            int cnt = 0;
+            for (int q = 0; q < p; ++q) {
+                int c = picks[l * p + q];
+                if (M[(size_t)s * n + c]) { sum = add_(mode, sum, R[(size_t)s * n + c]); ++cnt; }
+            }
+            if (cnt == 0) {
+                for (int t = 0; t < n; ++t)
+                    if (M[(size_t)s * n + t]) { sum = add_(mode, sum, R[(size_t)s * n + t]); ++cnt; }
+            }
+            U[(size_t)s * r + l] = cnt ? div_(mode, sum, (double)cnt) : 0.0;
+        }
+}
+
+/* Preparation steps of Algorithm 3 before the loop:
+ *   if R is not wide, transpose it (Reading: square counts as wide);
+ *   perm <- random permutation, R <- R[perm, :];
+ *   initialise U (Random Acol, or the caller's U0 given in the oriented,
+ *   permuted frame), then compute V = (-U)^T (x)* R (Reading of "compute V").
+ * Outputs the oriented, permuted problem: Ri, Mi (m x n with m <= n), Ui, Vi,
+ * perm_out, and *transposed.  perm_in / picks_in may be NULL (then drawn from
+ * seed).  Returns the number of empty rows + columns (must be 0).           */
+int orc_prepare(int mode, int m0, int n0, int r, const double *R0, const uint8_t *M0,
+                const int32_t *perm_in, const int32_t *picks_in, int p, uint64_t seed,
+                const double *U0, double *Ri, uint8_t *Mi, double *Ui, double *Vi,
+                int32_t *perm_out, int *transposed)
+{
+    int tr = m0 > n0;
+    int m = tr ? n0 : m0, n = tr ? m0 : n0;
+    *transposed = tr;
+    if (perm_in) memcpy(perm_out, perm_in, sizeof(int32_t) * (size_t)m);
+    else orc_randperm(m, seed, perm_out);
+    for (int s = 0; s < m; ++s)
+        for (int t = 0; t < n; ++t) {
+            int so = perm_out[s];
+            size_t src = tr ? (size_t)t * n0 + so : (size_t)so * n0 + t;
+            Ri[(size_t)s * n + t] = R0[src];
+            Mi[(size_t)s * n + t] = M0[src];
+        }
+    if (U0) {
+        memcpy(Ui, U0, sizeof(double) * (size_t)m * r);
+    } else {
+        int32_t *pk = (int32_t *)malloc(sizeof(int32_t) * (size_t)r * p);
+        if (picks_in) memcpy(pk, picks_in, sizeof(int32_t) * (size_t)r * p);
+        else orc_acol_picks(n, r, p, seed, pk);
+        orc_acol_init(mode, m, n, r, Ri, Mi, pk, p, Ui);
+        free(pk);
+    }
+    double *u = (double *)malloc(sizeof(double) * (size_t)m);
+    int empty = 0;
+    for (int l = 0; l < r; ++l) {
+        get_col(m, r, Ui, l, u);
+        empty += orc_residuate_v(mode, m, n, Ri, Mi, u, Vi + (size_t)l * n);
+    }
+    empty += orc_residuate_u(mode, m, n, Ri, Mi, Vi, u); /* checks rows only */
+    free(u);
+    return empty;
+}
+
+/* Post-processing of Algorithm 3: undo the permutation and the transpose.
+ *   not transposed: U_out[perm[s], :] = Ui[s, :], V_out = Vi
+ *   transposed:     U_out = Vi^T (m0 x r),  V_out[:, perm[s]] = Ui[s, :]^T  */
+void orc_finish(int m0, int n0, int r, int transposed, const double *Ui, const double *Vi,
+                const int32_t *perm, double *U_out, double *V_out)
+{
+    if (!transposed) {
+        int m = m0, n = n0;
+        for (int s = 0; s < m; ++s)
+            for (int l = 0; l < r; ++l) U_out[(size_t)perm[s] * r + l] = Ui[(size_t)s * r + l];
+        memcpy(V_out, Vi, sizeof(double) * (size_t)r * n);
+    } else {
+        int m = n0, n = m0;
+        for (int a = 0; a < n; ++a)
+            for (int l = 0; l < r; ++l) U_out[(size_t)a * r + l] = Vi[(size_t)l * n + a];
+        for (int s = 0; s < m; ++s)
+            for (int l = 0; l < r; ++l) V_out[(size_t)l * n0 + perm[s]] = Ui[(size_t)s * r + l];
+    }
+}
+
+/* FastSTMF, Algorithm 3 (STMF_ByRow_RandPerm_TD_A_W).
+ * Sweeps over all rows; stops after `sweeps` sweeps, or earlier when
+ * eps > 0 and the error changed by less than eps over a sweep (Section
+ * "Comparison of strategies": convergence when the change in error is below
+ * a threshold).  f_hist (nullable) receives sweeps+1 errors (initial, then
+ * after each sweep; unused tail left as is).  trace (nullable, capacity
+ * trace_cap records of 6 int32) receives one record per row visit:
+ * {sweep, row, position, j, k, type} (position = -1 when nothing was kept).
+ * counters (nullable) = {sweeps done, candidates tried, updates kept,
+ * trace records written}.  Returns the number of empty rows + columns found
+ * (0 on success; the run is skipped otherwise).                             */
+int orc_factorize(int mode, int m0, int n0, int r, const double *R0, const uint8_t *M0,
+                  int sweeps, double eps, const int32_t *perm_in, const int32_t *picks_in,
+                  int p, uint64_t seed, const double *U0, double *U_out, double *V_out,
+                  double *f_hist, int32_t *trace, int64_t trace_cap, int64_t *counters)
+{
+    int tr = m0 > n0;
+    int m = tr ? n0 : m0, n = tr ? m0 : n0;
+    double *Ri = (double *)malloc(sizeof(double) * (size_t)m * n);
+    uint8_t *Mi = (uint8_t *)malloc((size_t)m * n);
+    double *Ui = (double *)malloc(sizeof(double) * (size_t)m * r);
+    double *Vi = (double *)malloc(sizeof(double) * (size_t)r * n);
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    int transposed = 0;
+    int empty = orc_prepare(mode, m0, n0, r, R0, M0, perm_in, picks_in, p, seed, U0, Ri, Mi,
+                            Ui, Vi, perm, &transposed);
+    int64_t tried = 0, kept = 0, nrec = 0;
+    int done = 0;
+    if (empty == 0) {
+        double f = orc_error(mode, m, n, r, Ri, Mi, Ui, Vi);
+        if (f_hist) f_hist[0] = f;
+        for (int sw = 0; sw < sweeps; ++sw) {
+            double f_prev = f;
+            for (int i = 0; i < m; ++i) {
+                int32_t out[4];
+                kept += orc_row_step(mode, m, n, r, Ri, Mi, Ui, Vi, i, &f, out, &tried);
+                if (trace && nrec < trace_cap) {
+                    int32_t *rec = trace + 6 * nrec;
+                    rec[0] = sw; rec[1] = i; rec[2] = out[0]; rec[3] = out[1];
+                    rec[4] = out[2]; rec[5] = out[3];
+                    ++nrec;
+                }
+            }
+            ++done;
+            if (f_hist) f_hist[sw + 1] = f;
+            if (eps > 0.0 && fabs(f_prev - f) < eps) break;
+        }
+        orc_finish(m0, n0, r, transposed, Ui, Vi, perm, U_out, V_out);
+    }
+    if (counters) { counters[0] = done; counters[1] = tried; counters[2] = kept; counters[3] = nrec; }
+    free(Ri); free(Mi); free(Ui); free(Vi); free(perm);
+    return empty;
+}
