@@ -1,0 +1,186 @@
+/*
+ * stmf.h -- C ABI of the GB300 (sm_103a) FastSTMF hot path.
+ *
+ * FastSTMF (Omanovic, Oblak, Curk, arXiv 2205.06619) approximates a partially
+ * given matrix R (m x n) by a tropical (max,+) product U (x) V with U m x r,
+ * V r x n (Section "Related work", the tropical matrix factorization
+ * problem).  This library computes, on one GPU:
+ *   - the masked max-plus product with per-entry max, argmax and runner-up;
+ *   - the F-ULF / F-URF single-step updates (Algorithms 1 and 2);
+ *   - the full ByRow / TD_A / RandPerm / wide method (Algorithm 3).
+ *
+ * Conventions shared by every entry point
+ *   Memory.  Every array argument is DEVICE memory owned by the caller
+ *     (e.g. a torch CUDA tensor), unless its comment says "host".  The library
+ *     owns only its opaque objects and their device workspaces, and frees them
+ *     in the matching destroy call.
+ *   Layout.  Row-major FP32 with a leading dimension (elements between row
+ *     starts): R and P planes m x n with ld >= n; U m x r with ldu >= r;
+ *     V r x n with ldv >= n.
+ *   Mask.  Bit-packed uint32, row-major, ldm_words >= ceil(n/32) words per
+ *     row; bit (t & 31) of word [s*ldm_words + t/32] set <=> R_st is given
+ *     (observed).  NULL mask = every entry given.  Entries not given are never
+ *     read from R.
+ *   Stream.  Every call enqueues its work on the context's stream; calls that
+ *     return host values (errors, reports) synchronize that stream.
+ *   Errors.  No exception crosses the ABI.  Each call returns an
+ *     stmf_status; STMF_ERR_INVALID is returned, with nothing launched, for a
+ *     bad argument (size < 1, r outside [1, STMF_MAX_RANK], a too-small
+ *     leading dimension, a NULL required pointer, an index out of range, a
+ *     row or column with no given entry, a non-finite given entry).  The text
+ *     of the last error of a context is available from stmf_last_error().
+ *     Device-side waits are bounded: a wait that runs out returns
+ *     STMF_ERR_TIMEOUT and leaves the device usable.
+ */
+#ifndef STMF_H
+#define STMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STMF_MAX_RANK 32
+
+typedef enum {
+    STMF_OK = 0,
+    STMF_ERR_INVALID = 1,  /* bad argument; nothing was launched             */
+    STMF_ERR_CUDA = 2,     /* a CUDA runtime call failed                      */
+    STMF_ERR_OOM = 3,      /* device workspace allocation failed              */
+    STMF_ERR_TIMEOUT = 4,  /* a bounded device-side wait ran out              */
+    STMF_ERR_INTERNAL = 5  /* an internal consistency check failed            */
+} stmf_status;
+
+typedef struct stmf_ctx stmf_ctx;         /* device, stream, error text       */
+typedef struct stmf_problem stmf_problem; /* R, mask, U, V, planes, stats    */
+
+/* Options of the factorization (Algorithm 3 and its readings). */
+typedef struct {
+    int sweeps;          /* passes over all rows (the loop "while not converged") */
+    double eps;          /* > 0: also stop when a sweep changes the error by < eps
+                            (convergence rule of Section "Comparison of strategies") */
+    int window;          /* candidates evaluated per device pass (speculative window);
+                            0 = library default.  Never changes which update is kept. */
+    int select;          /* 0 = keep the first improving candidate in the paper's order
+                            (default, Algorithm 3); 1 = keep the best of the window    */
+    int precision;       /* 0 = FP32 (default); 1 = FP16 screening + FP32 re-check     */
+    int acol_p;          /* Random Acol: columns averaged per component; 0 = 5 (clamped to n) */
+    uint64_t seed;       /* draws the row permutation and the Acol picks (SplitMix64)  */
+    const int32_t *perm;  /* HOST, nullable: explicit row permutation of the oriented R
+                            (length = oriented m); overrides the seed                  */
+    const int32_t *picks; /* HOST, nullable: explicit Acol picks, r x acol_p column
+                            indices of the oriented R; overrides the seed              */
+    const float *U0;     /* DEVICE, nullable: initial U of the oriented, permuted problem
+                            (m x r, ld r); replaces Random Acol                          */
+    int32_t *trace;      /* HOST, nullable: one record of STMF_TRACE_INTS per row visit */
+    int64_t trace_cap;   /* capacity of trace in records                               */
+} stmf_options;
+
+/* A trace record: sweep, row (oriented, permuted index), position of the kept
+ * candidate among the row's candidates (-1: nothing kept), j, k,
+ * type (0 = F-ULF, 1 = F-URF), and the error after the row as two int32
+ * halves of a double (little-endian). */
+#define STMF_TRACE_INTS 8
+
+typedef struct {
+    double f_init;            /* b-norm error after initialisation                  */
+    double f_final;           /* b-norm error at the end                            */
+    int sweeps_done;
+    int transposed;           /* 1 if the input was tall and was transposed          */
+    int64_t candidates_tried; /* sequential-method candidates (up to the kept one)  */
+    int64_t candidates_issued;/* candidates evaluated on the device (>= tried)      */
+    int64_t accepted;         /* updates kept                                        */
+    int64_t refreshes;        /* product/statistics refreshes                        */
+    double seconds;           /* wall time of the sweep loop                         */
+} stmf_report;
+
+/* Context: binds a device and a stream (cudaStream_t passed as void*; NULL =
+ * the legacy default stream).  out receives the new context. */
+stmf_status stmf_create(stmf_ctx **out, int device, void *cuda_stream);
+void stmf_destroy(stmf_ctx *ctx);
+/* Text of the last error of ctx (static storage owned by ctx; "" if none). */
+const char *stmf_last_error(const stmf_ctx *ctx);
+/* Changes the stream of ctx. */
+stmf_status stmf_set_stream(stmf_ctx *ctx, void *cuda_stream);
+
+/* Masked max-plus product with top-2 tracking (Section "Related work",
+ * tropical matrix multiplication; f(i,j) of Section "The ByRow strategy"):
+ *   P1_ij = max_l (U_il + V_lj)
+ *   A_ij  = smallest l attaining P1_ij          (uint8; needs r <= 255)
+ *   P2_ij = max over l != A_ij of (U_il + V_lj) (-inf when r == 1)
+ * Sums and max are FP32 (IEEE, round to nearest).  Entries (i,j) not given by
+ * the mask are written as P1 = P2 = NaN, A = 255.  A and P2 may be NULL.
+ * P1/P2 use ldp, A uses lda (bytes).  Device pointers; no workspace. */
+stmf_status stmf_maxplus(stmf_ctx *ctx, int m, int n, int r,
+                         const float *U, int ldu, const float *V, int ldv,
+                         const uint32_t *mask, int ldm_words,
+                         float *P1, int ldp, uint8_t *A, int lda, float *P2);
+
+/* Selection statistics of the ByRow / TD_A strategy (Section "The ByRow
+ * strategy"; Algorithm 3) over the given entries, from the product above:
+ *   td_col[j]          = sum over given i of |R_ij - (U (x) V)_ij|   (FP64)
+ *   colhist[j*r + l]   = #{given i : f(i,j) = l}                      (int32)
+ *   *f_host            = sum over j of td_col[j]  (the b-norm error)   (HOST)
+ * td_col, colhist device (either may be NULL); f_host may be NULL.  Uses a
+ * device workspace owned by ctx (grown on demand). */
+stmf_status stmf_selection_stats(stmf_ctx *ctx, int m, int n, int r,
+                                 const float *R, int ldr, const uint32_t *mask, int ldm_words,
+                                 const float *U, int ldu, const float *V, int ldv,
+                                 double *td_col, int32_t *colhist, double *f_host);
+
+/* A problem: a copy of R (m x n, not transposed, not permuted) and its mask,
+ * the factors U, V and the device state F-ULF / F-URF need.  U0 (device,
+ * m x r, ld r) may be NULL: then U comes from Random Acol with opts->seed
+ * (opts->picks if given).  V is always computed as (-U)^T (x)* R.  opts may
+ * be NULL (defaults).  Fails with STMF_ERR_INVALID if a row or a column of R
+ * has no given entry. */
+stmf_status stmf_problem_create(stmf_ctx *ctx, int m, int n, int r,
+                                const float *R, int ldr, const uint32_t *mask, int ldm_words,
+                                const float *U0, const stmf_options *opts, stmf_problem **out);
+void stmf_problem_destroy(stmf_problem *prob);
+
+/* F-ULF(i, j, k) (Algorithm 1): U_ik <- R_ij - V_kj; V_k. <- (-U_.k)^T (x)* R;
+ * U_.k <- R (x)* (-V_k.)^T; f' = ||R - U (x) V||_b over given entries.
+ * commit_if_decreases = 1: keep the update only if f' < f (the paper's
+ * revert, Algorithm 3); 0: keep it unconditionally.  Requires R_ij given.
+ * f_new (host) receives f'; accepted (host) receives 1 if kept.
+ * Both nullable. */
+stmf_status stmf_update_U(stmf_problem *prob, int i, int j, int k, int commit_if_decreases,
+                          double *f_new, int *accepted);
+/* F-URF(i, j, k) (Algorithm 2): V_kj <- R_ij - U_ik; U_.k <- R (x)* (-V_k.)^T;
+ * V_k. <- (-U_.k)^T (x)* R; then as stmf_update_U. */
+stmf_status stmf_update_V(stmf_problem *prob, int i, int j, int k, int commit_if_decreases,
+                          double *f_new, int *accepted);
+/* Copies the current factors out (device U m x r ld r, V r x n ld n; either
+ * may be NULL) and the current error (host, nullable). */
+stmf_status stmf_problem_get(stmf_problem *prob, float *U, float *V, double *f);
+
+/* FastSTMF, Algorithm 3 (STMF_ByRow_RandPerm_TD_A_W): transpose a tall R,
+ * permute rows at random, Random Acol init, V by residuation, then sweeps of
+ * the ByRow loop: per row, candidates j in decreasing td_col (given R_ij
+ * only, ties to the smaller j), k by TD_A, F-ULF then F-URF, first strict
+ * decrease kept.  U_out (m x r, ld r) and V_out (r x n, ld n) are device
+ * arrays in the caller's orientation.  report (host) nullable. */
+stmf_status stmf_factorize(stmf_ctx *ctx, int m, int n, int r,
+                           const float *R, int ldr, const uint32_t *mask, int ldm_words,
+                           const stmf_options *opts, float *U_out, float *V_out,
+                           stmf_report *report);
+
+/* Fills *opts with the defaults (sweeps 1, eps 0, library window, first
+ * improving, FP32, acol_p 5, seed 0, no explicit draws, no trace). */
+void stmf_default_options(stmf_options *opts);
+
+/* FP32 add+max issue-rate microbenchmark: runs `iters` dependent-chain
+ * iterations of (FADD, FMNMX) pairs on every SM and returns, in *gops
+ * (host), the measured giga-operations per second (FADD and FMNMX count one
+ * each).  mode 0: 1:1 FADD/FMNMX; 1: FADD only; 2: FMNMX only;
+ * 3: packed half2 HADD2/HMNMX2 (two operations per lane).  Uses the
+ * context's stream and synchronizes it. */
+stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STMF_H */

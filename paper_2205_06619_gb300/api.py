@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in ``include/stmf.h`` (argument marshalling only).
+
+Every computation runs in ``libstmf.so``'s CUDA kernels.  Tensors are torch
+CUDA tensors (device memory and streams come from PyTorch); the functions
+take and return them, pass raw pointers and the current stream to the
+library, and raise :class:`StmfError` on any non-OK status.  There is no CPU
+fallback: if the library is missing or no GPU is present, calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import struct
+
+import numpy as np
+
+from . import build as _build
+
+STMF_MAX_RANK = 32
+STMF_TRACE_INTS = 8
+STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "INTERNAL"}
+
+EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", "stmf_maxplus",
+           "stmf_selection_stats", "stmf_problem_create", "stmf_problem_destroy", "stmf_update_U",
+           "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_default_options",
+           "stmf_peak_addmax"]
+
+
+class StmfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("stmf status %s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("sweeps", C.c_int), ("eps", C.c_double), ("window", C.c_int), ("select", C.c_int),
+                ("precision", C.c_int), ("acol_p", C.c_int), ("seed", C.c_uint64),
+                ("perm", C.c_void_p), ("picks", C.c_void_p), ("U0", C.c_void_p),
+                ("trace", C.c_void_p), ("trace_cap", C.c_int64)]
+
+
+class Report(C.Structure):
+    _fields_ = [("f_init", C.c_double), ("f_final", C.c_double), ("sweeps_done", C.c_int),
+                ("transposed", C.c_int), ("candidates_tried", C.c_int64),
+                ("candidates_issued", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
+                ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Loads libstmf.so (building it in-tree first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libstmf.so is not built (run paper_2205_06619_gb300.build.build())")
+        _build.build()
+    L = C.CDLL(path)
+    P, i, d = C.c_void_p, C.c_int, C.c_double
+    L.stmf_create.argtypes = [C.POINTER(P), i, P]
+    L.stmf_destroy.argtypes = [P]
+    L.stmf_destroy.restype = None
+    L.stmf_last_error.argtypes = [P]
+    L.stmf_last_error.restype = C.c_char_p
+    L.stmf_set_stream.argtypes = [P, P]
+    L.stmf_maxplus.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, i, P]
+    L.stmf_selection_stats.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, P, C.POINTER(d)]
+    L.stmf_problem_create.argtypes = [P, i, i, i, P, i, P, i, P, C.POINTER(Options), C.POINTER(P)]
+    L.stmf_problem_destroy.argtypes = [P]
+    L.stmf_problem_destroy.restype = None
+    L.stmf_update_U.argtypes = [P, i, i, i, i, C.POINTER(d), C.POINTER(i)]
+    L.stmf_update_V.argtypes = [P, i, i, i, i, C.POINTER(d), C.POINTER(i)]
+    L.stmf_problem_get.argtypes = [P, P, P, C.POINTER(d)]
+    L.stmf_factorize.argtypes = [P, i, i, i, P, i, P, i, C.POINTER(Options), P, P, C.POINTER(Report)]
+    L.stmf_default_options.argtypes = [C.POINTER(Options)]
+    L.stmf_default_options.restype = None
+    L.stmf_peak_addmax.argtypes = [P, i, i, C.POINTER(d)]
+    for name in EXPORTS:
+        if name not in ("stmf_destroy", "stmf_last_error", "stmf_problem_destroy", "stmf_default_options"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("stmf needs a CUDA GPU; none is available")
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check_f32(t, name):
+    torch = _torch()
+    if t.dtype != torch.float32 or not t.is_cuda:
+        raise TypeError("%s must be a float32 CUDA tensor" % name)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("%s must be 2-D with unit column stride" % name)
+
+
+def pack_mask(mask):
+    """Boolean mask (m x n; torch or numpy) -> bit-packed uint32 words (m x ceil(n/32)),
+    bit t%32 of word t/32 set when entry t is given.  Returns a CUDA int32 tensor."""
+    torch = _torch()
+    if isinstance(mask, torch.Tensor):
+        mask = mask.detach().cpu().numpy()
+    mask = np.ascontiguousarray(mask, dtype=bool)
+    m, n = mask.shape
+    words = (n + 31) // 32
+    padded = np.zeros((m, words * 32), dtype=bool)
+    padded[:, :n] = mask
+    bits = np.packbits(padded.reshape(m, words, 4, 8)[:, :, :, ::-1], axis=-1).reshape(m, words, 4)
+    packed = bits.astype(np.uint32)
+    w = packed[:, :, 0] | (packed[:, :, 1] << 8) | (packed[:, :, 2] << 16) | (packed[:, :, 3] << 24)
+    return torch.from_numpy(w.view(np.int32).copy()).cuda()
+
+
+class Context:
+    """A library context bound to a CUDA device and (by default) the current stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        st = L.stmf_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise StmfError(st, "stmf_create(device=%d) failed" % device)
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().stmf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st):
+        if st != 0:
+            raise StmfError(st, load().stmf_last_error(self.h).decode())
+
+    def use_current_stream(self):
+        torch = _torch()
+        s = torch.cuda.current_stream(self.device)
+        if s is not self.stream:
+            self.stream = s
+            self.check(load().stmf_set_stream(self.h, C.c_void_p(s.cuda_stream)))
+
+
+_default_ctx = None
+
+
+def context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context(0)
+    _default_ctx.use_current_stream()
+    return _default_ctx
+
+
+def maxplus(U, V, mask_words=None, with_argmax=True, with_runner_up=True):
+    """P1 = U (x) V (max-plus), A = argmax (uint8, smaller l on ties), P2 = runner-up."""
+    torch = _torch()
+    _check_f32(U, "U"); _check_f32(V, "V")
+    m, r = U.shape
+    n = V.shape[1]
+    ctx = context()
+    P1 = torch.empty((m, n), device=U.device, dtype=torch.float32)
+    A = torch.empty((m, n), device=U.device, dtype=torch.uint8) if with_argmax else None
+    P2 = torch.empty((m, n), device=U.device, dtype=torch.float32) if with_runner_up else None
+    ldm = mask_words.shape[1] if mask_words is not None else 0
+    ctx.check(load().stmf_maxplus(ctx.h, m, n, r, _ptr(U), U.stride(0), _ptr(V), V.stride(0), _ptr(mask_words),
+                                  ldm, _ptr(P1), n, _ptr(A), n, _ptr(P2)))
+    return P1, A, P2
+
+
+def selection_stats(R, U, V, mask_words=None):
+    """(td_col float64[n], colhist int32[n, r], f) over the given entries."""
+    torch = _torch()
+    _check_f32(R, "R"); _check_f32(U, "U"); _check_f32(V, "V")
+    m, n = R.shape
+    r = U.shape[1]
+    ctx = context()
+    td = torch.empty(n, device=R.device, dtype=torch.float64)
+    ch = torch.empty((n, r), device=R.device, dtype=torch.int32)
+    f = C.c_double()
+    ldm = mask_words.shape[1] if mask_words is not None else 0
+    ctx.check(load().stmf_selection_stats(ctx.h, m, n, r, _ptr(R), R.stride(0), _ptr(mask_words), ldm,
+                                          _ptr(U), U.stride(0), _ptr(V), V.stride(0), _ptr(td), _ptr(ch),
+                                          C.byref(f)))
+    return td, ch, f.value
+
+
+def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=0, perm=None, picks=None,
+             U0=None, trace=None):
+    o = Options()
+    load().stmf_default_options(C.byref(o))
+    o.sweeps, o.eps, o.window, o.select, o.precision, o.acol_p, o.seed = (
+        sweeps, eps, window, select, precision, acol_p, seed)
+    keep = []
+    if perm is not None:
+        a = np.ascontiguousarray(perm, dtype=np.int32); keep.append(a); o.perm = a.ctypes.data
+    if picks is not None:
+        a = np.ascontiguousarray(picks, dtype=np.int32); keep.append(a); o.picks = a.ctypes.data
+    if U0 is not None:
+        _check_f32(U0, "U0"); keep.append(U0); o.U0 = U0.data_ptr()
+    if trace is not None:
+        keep.append(trace); o.trace = trace.ctypes.data; o.trace_cap = trace.shape[0]
+    return o, keep
+
+
+class Problem:
+    """A problem on the device: F-ULF / F-URF single updates (Algorithms 1, 2)."""
+
+    def __init__(self, R, mask_words=None, rank=3, U0=None, seed=0, acol_p=5, picks=None):
+        _check_f32(R, "R")
+        self.ctx = context()
+        m, n = R.shape
+        self.m, self.n, self.r = m, n, rank
+        o, keep = _options(seed=seed, acol_p=acol_p, picks=picks)
+        h = C.c_void_p()
+        ldm = mask_words.shape[1] if mask_words is not None else 0
+        self.ctx.check(load().stmf_problem_create(self.ctx.h, m, n, rank, _ptr(R), R.stride(0), _ptr(mask_words),
+                                                  ldm, _ptr(U0), C.byref(o), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().stmf_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _update(self, fn, i, j, k, commit_if_decreases):
+        f = C.c_double()
+        acc = C.c_int()
+        self.ctx.check(fn(self.h, i, j, k, int(commit_if_decreases), C.byref(f), C.byref(acc)))
+        return f.value, bool(acc.value)
+
+    def update_U(self, i, j, k, commit_if_decreases=True):
+        """F-ULF(i, j, k); returns (f', kept)."""
+        return self._update(load().stmf_update_U, i, j, k, commit_if_decreases)
+
+    def update_V(self, i, j, k, commit_if_decreases=True):
+        """F-URF(i, j, k); returns (f', kept)."""
+        return self._update(load().stmf_update_V, i, j, k, commit_if_decreases)
+
+    def get(self):
+        torch = _torch()
+        U = torch.empty((self.m, self.r), device="cuda", dtype=torch.float32)
+        V = torch.empty((self.r, self.n), device="cuda", dtype=torch.float32)
+        f = C.c_double()
+        self.ctx.check(load().stmf_problem_get(self.h, _ptr(U), _ptr(V), C.byref(f)))
+        return U, V, f.value
+
+
+def decode_trace(trace: np.ndarray):
+    """Trace records -> list of (sweep, row, pos, j, k, type, f)."""
+    out = []
+    for rec in trace:
+        f = struct.unpack("<d", struct.pack("<ii", int(rec[6]), int(rec[7])))[0]
+        out.append((int(rec[0]), int(rec[1]), int(rec[2]), int(rec[3]), int(rec[4]), int(rec[5]), f))
+    return out
+
+
+def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5,
+              seed=0, perm=None, picks=None, U0=None, trace_cap=0):
+    """FastSTMF (Algorithm 3) on the device.  R: float32 CUDA (m x n).
+
+    Returns (U m x r, V r x n, report dict, trace list or None)."""
+    torch = _torch()
+    _check_f32(R, "R")
+    m, n = R.shape
+    ctx = context()
+    trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
+    o, keep = _options(sweeps, eps, window, select, precision, acol_p, seed, perm, picks, U0, trace)
+    U = torch.empty((m, rank), device=R.device, dtype=torch.float32)
+    V = torch.empty((rank, n), device=R.device, dtype=torch.float32)
+    rep = Report()
+    ldm = mask_words.shape[1] if mask_words is not None else 0
+    ctx.check(load().stmf_factorize(ctx.h, m, n, rank, _ptr(R), R.stride(0), _ptr(mask_words), ldm, C.byref(o),
+                                    _ptr(U), _ptr(V), C.byref(rep)))
+    tr = None
+    if trace is not None:
+        nrec = rep.sweeps_done * min(m, n)      # one record per row visit of the wide problem
+        tr = decode_trace(trace[:min(trace_cap, nrec)])
+    return U, V, rep.as_dict(), tr
+
+
+def peak_addmax(mode=0, iters=4096):
+    """Measured FP32 add+max issue rate in Gop/s (see stmf_peak_addmax)."""
+    ctx = context()
+    g = C.c_double()
+    ctx.check(load().stmf_peak_addmax(ctx.h, mode, iters, C.byref(g)))
+    return g.value

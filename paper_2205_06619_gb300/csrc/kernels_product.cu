@@ -1,0 +1,307 @@
+// Masked max-plus product with top-2 tracking and the ByRow / TD_A selection
+// statistics fused into its epilogue.
+//
+//   P1_ij = max_l (U_il + V_lj)        tropical product (Section "Related work")
+//   A_ij  = smallest argmax l          f(i,j) (Section "The ByRow strategy")
+//   P2_ij = max over l != A_ij         runner-up: max_{l != k} = (A == k ? P2 : P1)
+//   td_col[j]   = sum_i |R_ij - P1_ij|  over given entries (FP64)
+//   colhist[j,l]= #{given i : A_ij = l}
+//
+// (max,+) is not a ring, so this is FADD + FMNMX work on the CUDA cores; the
+// tensor cores have no (max,+) mode.  One CTA computes a 128 x 128 block as
+// four 32 x 128 tiles; each thread owns a 4 x 4 register tile, U and V tiles
+// are staged in shared memory (U broadcast along a warp, V read as float4).
+#include "common.cuh"
+
+#define QNAN __int_as_float(0x7fffffff)
+
+namespace {
+
+constexpr int TR = 32;     // rows per tile
+constexpr int TC = 128;    // columns per tile
+constexpr int TILES = 4;   // tiles per CTA (rows of a CTA = TR * TILES)
+
+template <bool STATS, bool MASKED>
+__global__ void __launch_bounds__(256)
+k_maxplus(int m, int n, int r, const float *__restrict__ U, int ldu,
+          const float *__restrict__ V, int ldv, const uint32_t *__restrict__ mask, int ldm,
+          float *__restrict__ P1, int ldp, uint8_t *__restrict__ A, int lda,
+          float *__restrict__ P2, const float *__restrict__ R, int ldr,
+          double *__restrict__ tdpart, int *__restrict__ chpart)
+{
+    __shared__ float sU[TR][STMF_MAX_RANK + 1];
+    __shared__ __align__(16) float sV[STMF_MAX_RANK][TC];
+    __shared__ double sTd[8][TC];
+    __shared__ int sHist[STATS ? TC * STMF_MAX_RANK : 1];
+
+    const int tid = threadIdx.x, rg = tid >> 5, cl = tid & 31;
+    const int col0 = blockIdx.x * TC;
+    const int part = blockIdx.y;
+    const int c = col0 + cl * 4;
+
+    for (int e = tid; e < r * TC; e += 256) {
+        int l = e / TC, b = e % TC, t = col0 + b;
+        sV[l][b] = t < n ? V[(size_t)l * ldv + t] : 0.f;
+    }
+    if (STATS)
+        for (int e = tid; e < TC * r; e += 256) sHist[e] = 0;
+    double td_acc[4] = {0.0, 0.0, 0.0, 0.0};
+
+    for (int tile = 0; tile < TILES; ++tile) {
+        const int row0 = (part * TILES + tile) * TR;
+        if (row0 >= m) break;
+        __syncthreads();
+        for (int e = tid; e < TR * r; e += 256) {
+            int a = e / r, l = e % r, s = row0 + a;
+            sU[a][l] = s < m ? U[(size_t)s * ldu + l] : 0.f;
+        }
+        __syncthreads();
+
+        float p1[4][4], p2[4][4];
+        int am[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) { p1[i][jj] = -INFINITY; p2[i][jj] = -INFINITY; am[i][jj] = 0; }
+
+        for (int l = 0; l < r; ++l) {
+            float u[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) u[i] = sU[rg * 4 + i][l];
+            const float4 v4 = *reinterpret_cast<const float4 *>(&sV[l][cl * 4]);
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float s = u[i] + v[jj];
+                    // new runner-up = max(old runner-up, min(old max, s)); strict
+                    // '>' keeps the smaller l as argmax on ties
+                    p2[i][jj] = fmaxf(p2[i][jj], fminf(p1[i][jj], s));
+                    am[i][jj] = s > p1[i][jj] ? l : am[i][jj];
+                    p1[i][jj] = fmaxf(p1[i][jj], s);
+                }
+        }
+
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int s = row0 + rg * 4 + i;
+            if (s >= m) continue;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int t = c + jj;
+                if (t >= n) continue;
+                bool given = true;
+                if (MASKED && mask) given = (mask[(size_t)s * ldm + (t >> 5)] >> (t & 31)) & 1u;
+                float q1 = p1[i][jj], q2 = p2[i][jj];
+                int qa = am[i][jj];
+                if (STATS) {
+                    const float rv = R[(size_t)s * ldr + t];
+                    if (MASKED ? given : (rv == rv)) {
+                        td_acc[jj] += (double)fabsf(rv - q1);
+                        atomicAdd(&sHist[(cl * 4 + jj) * r + qa], 1);
+                    }
+                } else {
+                    if (MASKED && !given) { q1 = QNAN; q2 = QNAN; qa = 255; }
+                    if (P1) P1[(size_t)s * ldp + t] = q1;
+                    if (P2) P2[(size_t)s * ldp + t] = q2;
+                    if (A) A[(size_t)s * lda + t] = (uint8_t)qa;
+                }
+            }
+        }
+    }
+
+    if (STATS) {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) sTd[rg][cl * 4 + jj] = td_acc[jj];
+        __syncthreads();
+        if (tid < TC) {
+            double s = 0.0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) s += sTd[g][tid];
+            const int t = col0 + tid;
+            if (t < n) tdpart[(size_t)part * n + t] = s;
+        }
+        for (int e = tid; e < TC * r; e += 256) {
+            const int t = col0 + e / r;
+            if (t < n) chpart[((size_t)part * n + t) * r + e % r] = sHist[e];
+        }
+    }
+}
+
+// Planes-only variant for the internal layout (no mask, vector stores).
+__global__ void __launch_bounds__(256)
+k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *__restrict__ V,
+                 int ld, float *__restrict__ P1, uint8_t *__restrict__ A, float *__restrict__ P2,
+                 const float *__restrict__ R, double *__restrict__ tdpart, int *__restrict__ chpart)
+{
+    __shared__ float sU[TR][STMF_MAX_RANK + 1];
+    __shared__ __align__(16) float sV[STMF_MAX_RANK][TC];
+    __shared__ double sTd[8][TC];
+    __shared__ int sHist[TC * STMF_MAX_RANK];
+
+    const int tid = threadIdx.x, rg = tid >> 5, cl = tid & 31;
+    const int col0 = blockIdx.x * TC;
+    const int part = blockIdx.y;
+    const int c = col0 + cl * 4;
+
+    for (int e = tid; e < r * TC; e += 256) {
+        int l = e / TC, b = e % TC;
+        sV[l][b] = V[(size_t)l * ld + col0 + b];
+    }
+    for (int e = tid; e < TC * r; e += 256) sHist[e] = 0;
+    double td_acc[4] = {0.0, 0.0, 0.0, 0.0};
+
+    for (int tile = 0; tile < TILES; ++tile) {
+        const int row0 = (part * TILES + tile) * TR;
+        if (row0 >= m) break;
+        __syncthreads();
+        for (int e = tid; e < TR * r; e += 256) {
+            int a = e / r, l = e % r;
+            sU[a][l] = U[(size_t)(row0 + a) * r + l];
+        }
+        __syncthreads();
+
+        float p1[4][4], p2[4][4];
+        int am[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) { p1[i][jj] = -INFINITY; p2[i][jj] = -INFINITY; am[i][jj] = 0; }
+
+        for (int l = 0; l < r; ++l) {
+            float u[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) u[i] = sU[rg * 4 + i][l];
+            const float4 v4 = *reinterpret_cast<const float4 *>(&sV[l][cl * 4]);
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const float s = u[i] + v[jj];
+                    p2[i][jj] = fmaxf(p2[i][jj], fminf(p1[i][jj], s));
+                    am[i][jj] = s > p1[i][jj] ? l : am[i][jj];
+                    p1[i][jj] = fmaxf(p1[i][jj], s);
+                }
+        }
+
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const size_t off = (size_t)(row0 + rg * 4 + i) * ld + c;
+            *reinterpret_cast<float4 *>(P1 + off) = make_float4(p1[i][0], p1[i][1], p1[i][2], p1[i][3]);
+            *reinterpret_cast<float4 *>(P2 + off) = make_float4(p2[i][0], p2[i][1], p2[i][2], p2[i][3]);
+            const uint32_t packed = (uint32_t)am[i][0] | ((uint32_t)am[i][1] << 8) |
+                                    ((uint32_t)am[i][2] << 16) | ((uint32_t)am[i][3] << 24);
+            *reinterpret_cast<uint32_t *>(A + off) = packed;
+            const float4 r4 = *reinterpret_cast<const float4 *>(R + off);
+            const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                if (rv[jj] == rv[jj]) {   // given entry (not NaN)
+                    td_acc[jj] += (double)fabsf(rv[jj] - p1[i][jj]);
+                    atomicAdd(&sHist[(cl * 4 + jj) * r + am[i][jj]], 1);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) sTd[rg][cl * 4 + jj] = td_acc[jj];
+    __syncthreads();
+    if (tid < TC) {
+        double s = 0.0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) s += sTd[g][tid];
+        tdpart[(size_t)part * ld + col0 + tid] = s;
+    }
+    for (int e = tid; e < TC * r; e += 256)
+        chpart[((size_t)part * ld + col0 + e / r) * r + e % r] = sHist[e];
+}
+
+// td_col[t] = sum over parts (fixed order); colhist likewise.
+__global__ void k_td_finalize(const double *__restrict__ tdpart, const int *__restrict__ chpart,
+                              int nparts, int ldpart, int n, int r, double *__restrict__ tdcol,
+                              int *__restrict__ colhist)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += tdpart[(size_t)p * ldpart + t];
+    if (tdcol) tdcol[t] = s;
+    if (colhist)
+        for (int l = 0; l < r; ++l) {
+            int h = 0;
+            for (int p = 0; p < nparts; ++p) h += chpart[((size_t)p * ldpart + t) * r + l];
+            colhist[(size_t)t * r + l] = h;
+        }
+}
+
+// Column order of Algorithm 3: decreasing td_col, equal values keep the
+// smaller j first.  Rank by counting (every CTA scans all keys from shared
+// memory), then scatter.
+__global__ void __launch_bounds__(256) k_order(const double *__restrict__ tdcol, int n, int *__restrict__ order)
+{
+    __shared__ double sk[2048];
+    const int j = blockIdx.x * 256 + threadIdx.x;
+    const double kj = j < n ? tdcol[j] : 0.0;
+    int rank = 0;
+    for (int base = 0; base < n; base += 2048) {
+        const int len = min(2048, n - base);
+        __syncthreads();
+        for (int e = threadIdx.x; e < len; e += 256) sk[e] = tdcol[base + e];
+        __syncthreads();
+        if (j < n)
+            for (int e = 0; e < len; ++e) {
+                const double x = sk[e];
+                rank += (x > kj) | ((x == kj) & (base + e < j));
+            }
+    }
+    if (j < n) order[rank] = j;
+}
+
+}  // namespace
+
+cudaError_t launch_maxplus(cudaStream_t st, int m, int n, int r, const float *U, int ldu,
+                           const float *V, int ldv, const uint32_t *mask, int ldm,
+                           float *P1, int ldp, uint8_t *A, int lda, float *P2,
+                           const float *R, int ldr, double *tdpart, int *colhist)
+{
+    dim3 grid((n + TC - 1) / TC, (m + TR * TILES - 1) / (TR * TILES));
+    if (R)
+        k_maxplus<true, true><<<grid, 256, 0, st>>>(m, n, r, U, ldu, V, ldv, mask, ldm, P1, ldp, A,
+                                                    lda, P2, R, ldr, tdpart, colhist);
+    else
+        k_maxplus<false, true><<<grid, 256, 0, st>>>(m, n, r, U, ldu, V, ldv, mask, ldm, P1, ldp, A,
+                                                     lda, P2, R, ldr, tdpart, colhist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planes(cudaStream_t st, stmf_problem *P, int *chpart)
+{
+    dim3 grid(P->np / TC, (P->m + TR * TILES - 1) / (TR * TILES));
+    k_maxplus_planes<<<grid, 256, 0, st>>>(P->m, P->n, P->r, P->U, P->V, P->np, P->P1, P->A, P->P2,
+                                           P->R, P->tdpart, chpart);
+    return cudaGetLastError();
+}
+
+int planes_nparts(int m) { return (m + TR * TILES - 1) / (TR * TILES); }
+
+cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int *chpart, int nparts,
+                                int ldpart, int n, int r, double *tdcol, int *colhist)
+{
+    k_td_finalize<<<(n + 255) / 256, 256, 0, st>>>(tdpart, chpart, nparts, ldpart, n, r, tdcol, colhist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_td_finalize(cudaStream_t st, const double *tdpart, int nparts, int ldpart, int n,
+                               double *tdcol)
+{
+    k_td_finalize<<<(n + 255) / 256, 256, 0, st>>>(tdpart, nullptr, nparts, ldpart, n, 0, tdcol, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order(cudaStream_t st, const double *tdcol, int n, int *order)
+{
+    k_order<<<(n + 255) / 256, 256, 0, st>>>(tdcol, n, order);
+    return cudaGetLastError();
+}

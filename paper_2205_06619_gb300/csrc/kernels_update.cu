@@ -1,0 +1,755 @@
+// Kernels of the F-ULF / F-URF updates (Algorithms 1 and 2) and of the ByRow
+// row loop of Algorithm 3, for a window of candidates evaluated at once.
+//
+// F-ULF(i,j,k) on the state (U, V):
+//   seed   U''_ik = R_ij - V_kj
+//   V'_kt  = min over given s of (R_st - U''_sk)
+//          = min( R_it - U''_ik ,  min over s != i of (R_st - U_sk) )
+//            -- O(n) from the column statistics (min1, argmin, min2) of k
+//   U'_sk  = min over given t of (R_st - V'_kt)            (row pass)
+//   f'     = sum over given (s,t) of |R_st - max(E_st, U'_sk + V'_kt)|
+//            with E = max over l != k of (U_sl + V_lt) = (A == k ? P2 : P1)
+// F-URF is the mirror image (row statistics, then a column pass over RT).
+//
+// Every value of a candidate's U', V' and every term of f' is computed with
+// the same FP32 operations as the plain definition, so they are bit-identical
+// to it; only the order of the error summation differs (FP32 partials of at
+// most 16 terms, FP32 warp trees, FP64 across warps and blocks, all in a
+// fixed order).
+#include "common.cuh"
+
+#define QNAN __int_as_float(0x7fffffff)
+#define FULL 0xffffffffu
+
+// ------------------------------------------------------------------ set-up
+
+// Rp[s][t] = given ? R[s][t] : NaN over the padded mp x ldp area.
+__global__ void k_pack(const float *__restrict__ R, int ldr, const uint32_t *__restrict__ mask, int ldm,
+                       int m, int n, float *__restrict__ Rp, int ldp, int mp, int *__restrict__ bad)
+{
+    const int t = blockIdx.x * 32 + threadIdx.x;
+    const int s = blockIdx.y * 8 + threadIdx.y;
+    if (s >= mp || t >= ldp) return;
+    float v = QNAN;
+    if (s < m && t < n) {
+        const bool given = mask ? ((mask[(size_t)s * ldm + (t >> 5)] >> (t & 31)) & 1u) : true;
+        if (given) {
+            v = R[(size_t)s * ldr + t];
+            if (!isfinite(v)) { atomicOr(bad, 1); v = QNAN; }
+        }
+    }
+    Rp[(size_t)s * ldp + t] = v;
+}
+
+// Oriented, permuted copy for Algorithm 3: Rp[s][t] = R0[perm[s]][t], or for a
+// transposed (tall) input Rp[s][t] = R0[t][perm[s]]; NaN where not given.
+__global__ void k_pack_oriented(const float *__restrict__ R, int ldr, const uint32_t *__restrict__ mask,
+                                int ldm, int m, int n, int transposed, const int *__restrict__ perm,
+                                float *__restrict__ Rp, int ldp, int mp, int *__restrict__ bad)
+{
+    const int t = blockIdx.x * 32 + threadIdx.x;
+    const int s = blockIdx.y * 8 + threadIdx.y;
+    if (s >= mp || t >= ldp) return;
+    float v = QNAN;
+    if (s < m && t < n) {
+        const int so = perm[s];
+        const int a = transposed ? t : so, b = transposed ? so : t;   // source row, column
+        const bool given = mask ? ((mask[(size_t)a * ldm + (b >> 5)] >> (b & 31)) & 1u) : true;
+        if (given) {
+            v = R[(size_t)a * ldr + b];
+            if (!isfinite(v)) { atomicOr(bad, 1); v = QNAN; }
+        }
+    }
+    Rp[(size_t)s * ldp + t] = v;
+}
+
+// Undo the permutation and the transpose (end of Algorithm 3):
+//   not transposed: U_out[perm[s], :] = U[s, :],  V_out = V
+//   transposed:     U_out = V^T,                  V_out[:, perm[s]] = U[s, :]^T
+__global__ void k_unorient(const float *__restrict__ U, const float *__restrict__ V, int m, int n, int r,
+                           int np, int transposed, const int *__restrict__ perm,
+                           float *__restrict__ U_out, float *__restrict__ V_out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m * r) {
+        const int s = e / r, l = e % r;
+        if (!transposed) U_out[(size_t)perm[s] * r + l] = U[e];
+        else V_out[(size_t)l * m + perm[s]] = U[e];
+    }
+    if (e < r * n) {
+        const int l = e / n, t = e % n;
+        if (!transposed) V_out[e] = V[(size_t)l * np + t];
+        else U_out[(size_t)t * r + l] = V[(size_t)l * np + t];
+    }
+}
+
+// Number of rows among the first `rows` that hold no given (non-NaN) entry.
+__global__ void k_empty_rows(const float *__restrict__ X, int ldx, int rows, int *__restrict__ nempty)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= rows) return;
+    int cnt = 0;
+    for (int t = lane; t < ldx; t += 32) cnt += X[(size_t)warp * ldx + t] == X[(size_t)warp * ldx + t];
+    cnt = __reduce_add_sync(FULL, cnt);
+    if (lane == 0 && cnt == 0) atomicAdd(nempty, 1);
+}
+
+__global__ void k_transpose(const float *__restrict__ X, int ldx, int rows, int cols,
+                            float *__restrict__ XT, int ldxt)
+{
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int rr = r0 + y, cc = c0 + threadIdx.x;
+        tile[y][threadIdx.x] = (rr < rows && cc < cols) ? X[(size_t)rr * ldx + cc] : QNAN;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int cc = c0 + y, rr = r0 + threadIdx.x;
+        if (cc < cols && rr < rows) XT[(size_t)cc * ldxt + rr] = tile[threadIdx.x][y];
+    }
+}
+
+// Top-2 residuation statistics of one row of X against y:
+//   d_t = X_st - y_t over given t;  min1 = min d, arg = smallest t with d = min1,
+//   min2 = min over t != arg.  One warp per row.
+__global__ void k_rowstat(const float *__restrict__ X, int ldx, int rows, int cols,
+                          const float *__restrict__ y, int ystride, float *__restrict__ min1,
+                          float *__restrict__ min2, int *__restrict__ arg)
+{
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    float a1 = INFINITY, a2 = INFINITY;
+    int ai = 0x7fffffff;
+    const float *x = X + (size_t)row * ldx;
+    for (int t = lane; t < cols; t += 32) {
+        const float d = x[t] - y[(size_t)t * ystride];
+        if (d < a1) { a2 = a1; a1 = d; ai = t; }     // NaN compares false: skipped
+        else a2 = fminf(a2, d);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float b1 = __shfl_xor_sync(FULL, a1, o), b2 = __shfl_xor_sync(FULL, a2, o);
+        const int bi = __shfl_xor_sync(FULL, ai, o);
+        if (b1 < a1 || (b1 == a1 && bi < ai)) { a2 = fminf(b2, a1); a1 = b1; ai = bi; }
+        else a2 = fminf(a2, b1);
+    }
+    if (lane == 0) { min1[row] = a1; min2[row] = a2; arg[row] = ai; }
+}
+
+// Random Acol (Section "Comparison of strategies"): U_sl = mean of the given
+// R_s,c over the picks c of component l, summed in pick order; if none is
+// given, the mean of the given entries of row s in column order.
+__global__ void k_acol(const float *__restrict__ R, int ld, int m, int n, int r,
+                       const int *__restrict__ picks, int p, float *__restrict__ U)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * r) return;
+    const int s = e / r, l = e % r;
+    const float *row = R + (size_t)s * ld;
+    float sum = 0.f;
+    int cnt = 0;
+    for (int q = 0; q < p; ++q) {
+        const float v = row[picks[l * p + q]];
+        if (v == v) { sum += v; ++cnt; }
+    }
+    if (cnt == 0)
+        for (int t = 0; t < n; ++t) {
+            const float v = row[t];
+            if (v == v) { sum += v; ++cnt; }
+        }
+    U[(size_t)s * r + l] = cnt ? sum / (float)cnt : 0.f;
+}
+
+__global__ void k_copy_rows(const float *__restrict__ src, int lds, float *__restrict__ dst, int ldd,
+                            int rows, int cols)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, s = blockIdx.y;
+    if (t < cols && s < rows) dst[(size_t)s * ldd + t] = src[(size_t)s * lds + t];
+}
+
+// --------------------------------------------------------------- row loop
+
+// Window of candidates (Algorithm 3): the next wj columns j of the order with
+// R_ij given; k_j = argmax_l (rowhist_i[l] + colhist[j][l]) (TD_A, smaller l
+// on ties).  Each j gives F-ULF (slot 2a) then F-URF (slot 2a+1).  At the
+// first window of a row the row histogram is rebuilt.
+__global__ void __launch_bounds__(256) k_window(stmf_problem P, int wmax)
+{
+    __shared__ int sh[STMF_MAX_RANK];
+    __shared__ int sj[STMF_WMAX / 2];
+    __shared__ int scount, spos;
+    stmf_ctl *ctl = P.ctl;
+    const int i = ctl->i, tid = threadIdx.x, r = P.r;
+    const float *Ri = P.R + (size_t)i * P.np;
+    if (ctl->row_start) {
+        if (tid < r) sh[tid] = 0;
+        __syncthreads();
+        const uint8_t *Ai = P.A + (size_t)i * P.np;
+        for (int t = tid; t < P.n; t += 256)
+            if (Ri[t] == Ri[t]) atomicAdd(&sh[Ai[t]], 1);
+        __syncthreads();
+        if (tid < r) P.rowhist[tid] = sh[tid];
+        if (tid == 0) { ctl->pos = 0; ctl->ncand_row = 0; ctl->row_start = 0; }
+        __syncthreads();
+    } else {
+        if (tid < r) sh[tid] = P.rowhist[tid];
+    }
+    if (tid < 32) {
+        const int want = min(ctl->wj, wmax / 2);
+        int pos = ctl->pos, have = 0;
+        const int lane = tid;
+        while (have < want && pos < P.n) {
+            const int q = pos + lane;
+            const int j = q < P.n ? P.order[q] : 0;
+            const bool ok = q < P.n && Ri[j] == Ri[j];
+            const unsigned b = __ballot_sync(FULL, ok);
+            const int rank = __popc(b & ((1u << lane) - 1u));
+            if (ok && have + rank < want) sj[have + rank] = j;
+            const int take = min(__popc(b), want - have);
+            if (take < __popc(b)) {
+                // stop right after the take-th given entry
+                unsigned bb = b;
+                for (int z = 0; z < take; ++z) bb &= bb - 1u;
+                pos += __ffs(bb) - 1;
+            } else {
+                pos += 32;
+            }
+            have += take;
+        }
+        if (lane == 0) { scount = have; spos = min(pos, P.n); }
+    }
+    __syncthreads();
+    const int cnt = scount;
+    if (tid < cnt) {
+        const int j = sj[tid];
+        int best = 0, bestc = -1;
+        for (int l = 0; l < r; ++l) {
+            const int c = sh[l] + P.colhist[(size_t)j * r + l];
+            if (c > bestc) { bestc = c; best = l; }
+        }
+        const int base = ctl->ncand_row / 2;
+        int *c0 = P.cand + 8 * (2 * tid);
+        c0[0] = j; c0[1] = best; c0[2] = 0; c0[3] = base + tid;
+        int *c1 = P.cand + 8 * (2 * tid + 1);
+        c1[0] = j; c1[1] = best; c1[2] = 1; c1[3] = base + tid;
+    }
+    if (tid == 0) {
+        ctl->nc = 2 * cnt;
+        ctl->nu = cnt;
+        ctl->nv = cnt;
+        ctl->exhausted = spos >= P.n;
+        ctl->pos = spos;
+    }
+    if (tid < cnt) { ctl->ulist[tid] = 2 * tid; ctl->vlist[tid] = 2 * tid + 1; }
+}
+
+// Seeds: for F-ULF slots V'_k. from the column statistics; for F-URF slots
+// U'_.k from the row statistics.  grid.y = slot, grid.x covers max(np, mp).
+__global__ void k_seed(stmf_problem P)
+{
+    const stmf_ctl *ctl = P.ctl;
+    const int c = blockIdx.y;
+    if (c >= ctl->nc) return;
+    const int *cd = P.cand + 8 * c;
+    const int j = cd[0], k = cd[1], type = cd[2], i = ctl->i;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (type == 0) {
+        if (x >= P.np) return;
+        const float useed = P.R[(size_t)i * P.np + j] - P.V[(size_t)k * P.np + j];
+        float v = 0.f;
+        if (x < P.n) {
+            const size_t e = (size_t)k * P.np + x;
+            const float rest = P.carg[e] == i ? P.cmin2[e] : P.cmin1[e];
+            v = fminf(P.R[(size_t)i * P.np + x] - useed, rest);
+        }
+        P.Vc[(size_t)c * P.np + x] = v;
+    } else {
+        if (x >= P.mp) return;
+        const float vseed = P.R[(size_t)i * P.np + j] - P.U[(size_t)i * P.r + k];
+        float u = 0.f;
+        if (x < P.m) {
+            const size_t e = (size_t)k * P.mp + x;
+            const float rest = P.rarg[e] == j ? P.rmin2[e] : P.rmin1[e];
+            u = fminf(P.RT[(size_t)j * P.mp + x] - vseed, rest);
+        }
+        P.Uc[(size_t)c * P.mp + x] = u;
+    }
+}
+
+// Warp reduce-scatter of 32 values: afterwards lane L holds op over the warp
+// of value L.  31 shuffles instead of 32 x 5.
+template <bool MIN>
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int o = 16 >> lvl;
+        const bool upper = lane & o;
+#pragma unroll
+        for (int q = 0; q < o; ++q) {
+            const float send = upper ? v[q] : v[q + o];
+            const float keep = upper ? v[q + o] : v[q];
+            const float recv = __shfl_xor_sync(FULL, send, o);
+            v[q] = MIN ? fminf(keep, recv) : keep + recv;
+        }
+    }
+    return v[0];
+}
+
+// term of the b-norm for one entry: |R - max(E, x)| with E = (a == k ? p2 : p1);
+// a NaN R (entry not given) gives 0 through fmaxf.
+__device__ __forceinline__ float bterm(float rv, float p1, float p2, int a, int k, float x)
+{
+    const float e = a == k ? p2 : p1;
+    return fmaxf(fabsf(rv - fmaxf(e, x)), 0.f);
+}
+
+constexpr int CG = 8;   // candidates per phase-1 group
+
+// F-ULF window evaluation.  One CTA owns 4 full rows: phase 1 computes
+// U'_sk of every F-ULF candidate for its rows, phase 2 the candidates' error
+// over those rows.  null_mode: one candidate equal to the current state
+// (k = 0, U'_.0 = U_.0, V'_0. = V_0.): gives the current error in this
+// kernel's summation tree.
+__global__ void __launch_bounds__(256, 2) k_eval_ulf(stmf_problem P, int null_mode)
+{
+    __shared__ float su[STMF_WMAX / 2][4];
+    __shared__ float red[8][32];
+    __shared__ int sslot[STMF_WMAX / 2], sk[STMF_WMAX / 2];
+    const stmf_ctl *ctl = P.ctl;
+    const int nu = null_mode ? 1 : ctl->nu;
+    if (nu == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s0 = blockIdx.x * 4;
+    const int nf4 = P.np >> 2;
+    if (tid < nu) {
+        const int slot = null_mode ? 0 : ctl->ulist[tid];
+        sslot[tid] = slot;
+        sk[tid] = null_mode ? 0 : P.cand[8 * slot + 1];
+    }
+    __syncthreads();
+    const float4 *R4 = reinterpret_cast<const float4 *>(P.R + (size_t)s0 * P.np);
+
+    // ---- phase 1: U'_sk = min over t of (R_st - V'_kt)
+    if (null_mode) {
+        if (tid < 4) su[0][tid] = P.U[(size_t)(s0 + tid) * P.r + 0];
+    } else {
+        for (int g = 0; g < nu; g += CG) {
+            float acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = INFINITY;
+            for (int f = tid; f < nf4; f += 256) {
+                float4 r4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) r4[i] = R4[(size_t)i * nf4 + f];
+#pragma unroll
+                for (int cc = 0; cc < CG; ++cc) {
+                    if (g + cc < nu) {
+                        const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)sslot[g + cc] * P.np)[f];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float a = acc[cc * 4 + i];
+                            a = fminf(a, r4[i].x - v4.x);
+                            a = fminf(a, r4[i].y - v4.y);
+                            a = fminf(a, r4[i].z - v4.z);
+                            a = fminf(a, r4[i].w - v4.w);
+                            acc[cc * 4 + i] = a;
+                        }
+                    }
+                }
+            }
+            const float w = reduce_scatter32<true>(acc, lane);
+            red[warp][lane] = w;
+            __syncthreads();
+            if (tid < 32) {
+                float x = red[0][tid];
+#pragma unroll
+                for (int q = 1; q < 8; ++q) x = fminf(x, red[q][tid]);
+                const int cc = tid >> 2, i = tid & 3;
+                if (g + cc < nu) {
+                    su[g + cc][i] = x;
+                    P.Uc[(size_t)sslot[g + cc] * P.mp + s0 + i] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: error of every candidate over the 4 rows; a thread owns
+    // 2 rows x 4 columns per step (rows 2*rg, 2*rg+1), 128 threads per row pair
+    float sum[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) sum[q] = 0.f;
+    const int rg = tid >> 7, cl = tid & 127;
+    const size_t rowoff = (size_t)(2 * rg) * nf4;
+    const float4 *R4b = R4 + rowoff;
+    const float4 *P14 = reinterpret_cast<const float4 *>(P.P1 + (size_t)s0 * P.np) + rowoff;
+    const float4 *P24 = reinterpret_cast<const float4 *>(P.P2 + (size_t)s0 * P.np) + rowoff;
+    const uint32_t *A4 = reinterpret_cast<const uint32_t *>(P.A + (size_t)s0 * P.np) + rowoff;
+    for (int f = cl; f < nf4; f += 128) {
+        float rv[2][4], p1[2][4], p2[2][4];
+        int a[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float4 x = R4b[(size_t)i * nf4 + f], y = P14[(size_t)i * nf4 + f], z = P24[(size_t)i * nf4 + f];
+            const uint32_t w = A4[(size_t)i * nf4 + f];
+            rv[i][0] = x.x; rv[i][1] = x.y; rv[i][2] = x.z; rv[i][3] = x.w;
+            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
+            p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) a[i][jj] = (w >> (8 * jj)) & 0xff;
+        }
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+            if (cc < nu) {
+                const int k = sk[cc];
+                float4 v4;
+                if (null_mode) v4 = reinterpret_cast<const float4 *>(P.V)[f];
+                else v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)sslot[cc] * P.np)[f];
+                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+                float t[2][4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const float u = su[cc][2 * rg + i];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u + v[jj]);
+                }
+                sum[cc] += ((t[0][0] + t[0][1]) + (t[0][2] + t[0][3])) + ((t[1][0] + t[1][1]) + (t[1][2] + t[1][3]));
+            }
+        }
+    }
+    const float w = reduce_scatter32<false>(sum, lane);
+    red[warp][lane] = w;
+    __syncthreads();
+    if (tid < nu) {
+        double x = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x += (double)red[q][tid];
+        P.part_ulf[(size_t)blockIdx.x * STMF_WMAX + sslot[tid]] = x;
+    }
+}
+
+// F-URF window evaluation.  One CTA owns a strip of 32 full columns: phase 1
+// computes V'_kt of every F-URF candidate for its columns from rows of RT,
+// phase 2 the candidates' error over the strip.
+__global__ void __launch_bounds__(256, 2) k_eval_urf(stmf_problem P, int null_mode)
+{
+    __shared__ __align__(16) float sv[STMF_WMAX / 2][32];
+    __shared__ float red[8][32];
+    __shared__ int sslot[STMF_WMAX / 2], sk[STMF_WMAX / 2];
+    const stmf_ctl *ctl = P.ctl;
+    const int nv = null_mode ? 1 : ctl->nv;
+    if (nv == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t0 = blockIdx.x * 32;
+    if (tid < nv) {
+        const int slot = null_mode ? 1 : ctl->vlist[tid];
+        sslot[tid] = slot;
+        sk[tid] = null_mode ? 0 : P.cand[8 * slot + 1];
+    }
+    __syncthreads();
+
+    // ---- phase 1: V'_kt = min over s of (R_st - U'_sk), warp w owns columns t0+4w..+3
+    if (null_mode) {
+        if (tid < 32) sv[0][tid] = P.V[t0 + tid];
+    } else {
+        const int nf4 = P.mp >> 2;
+        const float4 *X4 = reinterpret_cast<const float4 *>(P.RT + (size_t)(t0 + 4 * warp) * P.mp);
+        for (int g = 0; g < nv; g += CG) {
+            float acc[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[q] = INFINITY;
+            for (int f = lane; f < nf4; f += 32) {
+                float4 x4[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x4[i] = X4[(size_t)i * nf4 + f];
+#pragma unroll
+                for (int cc = 0; cc < CG; ++cc) {
+                    if (g + cc < nv) {
+                        const float4 u4 = reinterpret_cast<const float4 *>(P.Uc + (size_t)sslot[g + cc] * P.mp)[f];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float a = acc[cc * 4 + i];
+                            a = fminf(a, x4[i].x - u4.x);
+                            a = fminf(a, x4[i].y - u4.y);
+                            a = fminf(a, x4[i].z - u4.z);
+                            a = fminf(a, x4[i].w - u4.w);
+                            acc[cc * 4 + i] = a;
+                        }
+                    }
+                }
+            }
+            const float x = reduce_scatter32<true>(acc, lane);
+            const int cc = lane >> 2, i = lane & 3;
+            if (g + cc < nv) {
+                sv[g + cc][4 * warp + i] = x;
+                P.Vc[(size_t)sslot[g + cc] * P.np + t0 + 4 * warp + i] = x;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 2: error over the strip; thread: 4 columns x 2 consecutive rows
+    const int cl = tid & 7, rl = tid >> 3;
+    const int tc = t0 + cl * 4;
+    float sum[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) sum[q] = 0.f;
+    for (int sb = rl * 2; sb < P.m; sb += 64) {
+        float rv[2][4], p1[2][4], p2[2][4];
+        int a[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const size_t off = (size_t)(sb + i) * P.np + tc;
+            const float4 x = *reinterpret_cast<const float4 *>(P.R + off);
+            const float4 y = *reinterpret_cast<const float4 *>(P.P1 + off);
+            const float4 z = *reinterpret_cast<const float4 *>(P.P2 + off);
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(P.A + off);
+            rv[i][0] = x.x; rv[i][1] = x.y; rv[i][2] = x.z; rv[i][3] = x.w;
+            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
+            p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) a[i][jj] = (w >> (8 * jj)) & 0xff;
+        }
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+            if (cc < nv) {
+                const int k = sk[cc];
+                float u[2];
+                if (null_mode) {
+                    u[0] = P.U[(size_t)sb * P.r];
+                    u[1] = P.U[(size_t)(sb + 1) * P.r];
+                } else {
+                    const float2 u2 = *reinterpret_cast<const float2 *>(P.Uc + (size_t)sslot[cc] * P.mp + sb);
+                    u[0] = u2.x; u[1] = u2.y;
+                }
+                const float4 v4 = *reinterpret_cast<const float4 *>(&sv[cc][cl * 4]);
+                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+                float t[2][4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u[i] + v[jj]);
+                sum[cc] += ((t[0][0] + t[0][1]) + (t[0][2] + t[0][3])) + ((t[1][0] + t[1][1]) + (t[1][2] + t[1][3]));
+            }
+        }
+    }
+    const float w = reduce_scatter32<false>(sum, lane);
+    red[warp][lane] = w;
+    __syncthreads();
+    if (tid < nv) {
+        double x = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x += (double)red[q][tid];
+        P.part_urf[(size_t)blockIdx.x * STMF_WMAX + sslot[tid]] = x;
+    }
+}
+
+// Sums the block partials of every candidate (fixed order), picks the kept
+// candidate and commits it.  mode 0: first candidate (in the paper's order)
+// with f' < f;  mode 1: the smallest f' < f of the window (ties: first);
+// mode 2 (null): store the current error of both summation trees.
+__global__ void __launch_bounds__(256) k_select(stmf_problem P, int mode, int nb_ulf, int nb_urf)
+{
+    __shared__ double sf[STMF_WMAX];
+    __shared__ int skept;
+    stmf_ctl *ctl = P.ctl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nc = mode == 2 ? 2 : ctl->nc;
+    for (int c = warp; c < nc; c += 8) {
+        const int type = mode == 2 ? c : P.cand[8 * c + 2];
+        const double *part = type == 0 ? P.part_ulf : P.part_urf;
+        const int nb = type == 0 ? nb_ulf : nb_urf;
+        double x = 0.0;
+        for (int b = lane; b < nb; b += 32) x += part[(size_t)b * STMF_WMAX + c];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        if (lane == 0) { sf[c] = x; P.fc[c] = x; }
+    }
+    __syncthreads();
+    if (mode == 2) {
+        if (tid == 0) { ctl->f_ulf = sf[0]; ctl->f_urf = sf[1]; }
+        return;
+    }
+    if (tid == 0) {
+        int kept = -1;
+        for (int c = 0; c < nc; ++c) {
+            const double fref = P.cand[8 * c + 2] == 0 ? ctl->f_ulf : ctl->f_urf;
+            if (sf[c] < fref) {
+                if (mode == 0) { kept = c; break; }
+                if (kept < 0 || sf[c] < sf[kept]) kept = c;
+            }
+        }
+        skept = kept;
+        ctl->issued += nc;
+        ctl->tried += mode == 0 ? (kept >= 0 ? kept + 1 : nc) : nc;
+        ctl->ncand_row += nc;
+        if (kept >= 0) {
+            const int *cd = P.cand + 8 * kept;
+            ctl->kept = 1;
+            ctl->kept_c = kept;
+            ctl->kept_j = cd[0]; ctl->kept_k = cd[1]; ctl->kept_type = cd[2]; ctl->kept_pos = cd[3];
+            ctl->f_new = sf[kept];
+            ctl->row_done = 1;
+        } else {
+            ctl->kept = 0;
+            ctl->row_done = ctl->exhausted;
+            ctl->wj = min(ctl->wj * 2, STMF_WMAX / 2);
+        }
+    }
+    __syncthreads();
+    const int kept = skept;
+    if (kept >= 0) {
+        const int k = P.cand[8 * kept + 1];
+        for (int s = tid; s < P.m; s += 256) P.U[(size_t)s * P.r + k] = P.Uc[(size_t)kept * P.mp + s];
+        for (int t = tid; t < P.n; t += 256) P.V[(size_t)k * P.np + t] = P.Vc[(size_t)kept * P.np + t];
+    }
+}
+
+// One explicit candidate (stmf_update_U / stmf_update_V): slot 0.
+__global__ void k_single(stmf_problem P, int i, int j, int k, int type)
+{
+    stmf_ctl *ctl = P.ctl;
+    int *c0 = P.cand;
+    c0[0] = j; c0[1] = k; c0[2] = type; c0[3] = 0;
+    ctl->i = i;
+    ctl->nc = 1;
+    ctl->nu = type == 0 ? 1 : 0;
+    ctl->nv = type == 1 ? 1 : 0;
+    ctl->ulist[0] = 0;
+    ctl->vlist[0] = 0;
+    ctl->exhausted = 1;
+    ctl->ncand_row = 0;
+}
+
+// Unconditional commit of slot 0 (commit_if_decreases = 0).
+__global__ void k_commit0(stmf_problem P)
+{
+    stmf_ctl *ctl = P.ctl;
+    const int k = P.cand[1];
+    for (int s = threadIdx.x; s < P.m; s += blockDim.x) P.U[(size_t)s * P.r + k] = P.Uc[s];
+    for (int t = threadIdx.x; t < P.n; t += blockDim.x) P.V[(size_t)k * P.np + t] = P.Vc[t];
+    if (threadIdx.x == 0) {
+        ctl->kept = 1; ctl->kept_c = 0; ctl->kept_k = k; ctl->f_new = P.fc[0];
+    }
+}
+
+__global__ void k_begin_row(stmf_ctl *ctl, int i, int wj0)
+{
+    ctl->i = i;
+    ctl->row_start = 1;
+    ctl->wj = wj0;
+    ctl->kept = 0;
+    ctl->row_done = 0;
+    ctl->kept_pos = -1;
+}
+
+// ---------------------------------------------------------------- launchers
+
+cudaError_t launch_pack(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm, int m, int n,
+                        float *Rp, int ldp, int mp, int *bad)
+{
+    dim3 grid(ldp / 32, mp / 8), block(32, 8);
+    k_pack<<<grid, block, 0, st>>>(R, ldr, mask, ldm, m, n, Rp, ldp, mp, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_oriented(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm,
+                                 int m, int n, int transposed, const int *perm, float *Rp, int ldp, int mp,
+                                 int *bad)
+{
+    dim3 grid(ldp / 32, mp / 8), block(32, 8);
+    k_pack_oriented<<<grid, block, 0, st>>>(R, ldr, mask, ldm, m, n, transposed, perm, Rp, ldp, mp, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unorient(cudaStream_t st, const stmf_problem *P, int transposed, const int *perm,
+                            float *U_out, float *V_out)
+{
+    const int tot = max(P->m * P->r, P->r * P->n);
+    k_unorient<<<(tot + 255) / 256, 256, 0, st>>>(P->U, P->V, P->m, P->n, P->r, P->np, transposed, perm,
+                                                  U_out, V_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_empty_rows(cudaStream_t st, const float *X, int ldx, int rows, int *nempty)
+{
+    k_empty_rows<<<(rows * 32 + 255) / 256, 256, 0, st>>>(X, ldx, rows, nempty);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(cudaStream_t st, const float *X, int ldx, int rows, int cols, float *XT, int ldxt)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, st>>>(X, ldx, rows, cols, XT, ldxt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowstat(cudaStream_t st, const float *X, int ldx, int rows, int cols, const float *y,
+                           int ystride, float *min1, float *min2, int *arg)
+{
+    k_rowstat<<<(rows * 32 + 255) / 256, 256, 0, st>>>(X, ldx, rows, cols, y, ystride, min1, min2, arg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acol(cudaStream_t st, const float *R, int ld, int m, int n, int r, const int *picks, int p,
+                        float *U)
+{
+    k_acol<<<(m * r + 255) / 256, 256, 0, st>>>(R, ld, m, n, r, picks, p, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rows(cudaStream_t st, const float *src, int lds, float *dst, int ldd, int rows, int cols)
+{
+    dim3 grid((cols + 255) / 256, rows);
+    k_copy_rows<<<grid, 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_begin_row(cudaStream_t st, stmf_problem *P, int i, int wj0)
+{
+    k_begin_row<<<1, 1, 0, st>>>(P->ctl, i, wj0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window(cudaStream_t st, stmf_problem *P)
+{
+    k_window<<<1, 256, 0, st>>>(*P, P->window);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots)
+{
+    dim3 grid((max(P->np, P->mp) + 255) / 256, nslots);
+    k_seed<<<grid, 256, 0, st>>>(*P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int null_mode)
+{
+    k_eval_ulf<<<(P->m + 3) / 4, 256, 0, st>>>(*P, null_mode);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_eval_urf<<<(P->n + 31) / 32, 256, 0, st>>>(*P, null_mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int mode)
+{
+    k_select<<<1, 256, 0, st>>>(*P, mode, (P->m + 3) / 4, (P->n + 31) / 32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type)
+{
+    k_single<<<1, 1, 0, st>>>(*P, i, j, k, type);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P)
+{
+    k_commit0<<<1, 256, 0, st>>>(*P);
+    return cudaGetLastError();
+}

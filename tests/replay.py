@@ -1,0 +1,44 @@
+"""Decision-replay harness: runs the oracle in lockstep with a GPU trace.
+
+At each row visit the oracle takes its own ByRow step from the same state.
+Where its decision differs from the GPU's, the difference is accepted only
+when floating-point order can explain it: the two kept candidates' errors
+agree within ``tol`` relative, or either one lies within ``tol`` relative of
+the error before the row (a near-tie with "f decreases").  The oracle then
+adopts the GPU's decision (it applies the same F-ULF / F-URF itself, which in
+FP32 mode reproduces the GPU's factors bit for bit) and continues.
+"""
+import numpy as np
+
+import oracle as orc
+
+
+def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=None):
+    st = orc.prepare(R, M, r, perm=perm, picks=picks, p=p, seed=seed, U0=U0)
+    Ri, Mi, Ui, Vi = st["R"], st["M"], st["U"], st["V"]
+    f = orc.error(Ri, Mi, Ui, Vi)
+    divergences = []
+    for rec in gpu_trace:
+        sweep, i, pos, j, k, typ, f_gpu = rec
+        U0_, V0_ = Ui.copy(), Vi.copy()
+        kept, fn, out, _ = orc.row_step(Ri, Mi, Ui, Vi, i, f)
+        gpu_kept = pos >= 0
+        same = (kept == gpu_kept) and (not kept or tuple(out) == (pos, j, k, typ))
+        if same:
+            f = fn
+            assert abs(f_gpu - f) <= tol * max(f, 1e-30), (rec, f)
+            continue
+        f_old = f
+        f_orc = fn if kept else f_old
+        if gpu_kept:
+            fun = orc.fulf if typ == 0 else orc.furf
+            Ug, Vg, f_g = fun(Ri, Mi, U0_, V0_, i, j, k)
+        else:
+            Ug, Vg, f_g = U0_, V0_, f_old
+        scale = tol * max(f_old, 1e-30)
+        ok = abs(f_g - f_orc) <= scale or abs(f_g - f_old) <= scale or abs(f_orc - f_old) <= scale
+        assert ok, ("decision differs beyond tolerance", rec, out, kept, f_old, f_orc, f_g)
+        divergences.append((rec, out, f_old, f_orc, f_g))
+        Ui, Vi, f = Ug, Vg, f_g
+    U, V = orc.finish(R.shape[0], R.shape[1], st["transposed"], Ui, Vi, st["perm"])
+    return dict(U=U, V=V, f=f, divergences=divergences, perm=st["perm"], transposed=st["transposed"])

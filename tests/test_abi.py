@@ -1,0 +1,77 @@
+"""The C ABI library builds, loads without a GPU and exports every entry
+point that include/stmf.h declares; host-side logic of the binding."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "stmf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(stmf_[a-z_0-9A-Z]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("stmf_maxplus", "stmf_update_U", "stmf_update_V", "stmf_factorize",
+                     "stmf_problem_create", "stmf_create", "stmf_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2205_06619_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_export_list_matches_header():
+    from paper_2205_06619_gb300 import api
+    assert sorted(api.EXPORTS) == sorted(n for n in declared_functions())
+
+
+def test_default_options_without_gpu():
+    from paper_2205_06619_gb300 import api
+    lib = api.load()
+    o = api.Options()
+    lib.stmf_default_options(ctypes.byref(o))
+    assert o.sweeps == 1 and o.acol_p == 5 and o.window == 0 and o.seed == 0 and not o.trace
+
+
+def test_invalid_arguments_fail_without_launch():
+    """A NULL context and bad sizes are rejected on the host (no GPU needed)."""
+    from paper_2205_06619_gb300 import api
+    lib = api.load()
+    st = lib.stmf_maxplus(None, 0, 4, 2, None, 2, None, 4, None, 0, None, 4, None, 4, None)
+    assert st == 1
+
+
+def test_mask_packing_layout():
+    """Bit t%32 of word t/32 of row s <=> entry (s, t) given (include/stmf.h)."""
+    torch = pytest.importorskip("torch")
+    from paper_2205_06619_gb300 import api
+    rng = np.random.default_rng(0)
+    M = rng.random((5, 70)) < 0.5
+    # packing runs on the host; only the final .cuda() needs a GPU
+    if not torch.cuda.is_available():
+        orig = torch.Tensor.cuda
+        torch.Tensor.cuda = lambda self, *a, **k: self
+        try:
+            api_torch = api._torch
+            api._torch = lambda: torch
+            W = api.pack_mask(M).numpy().view(np.uint32)
+        finally:
+            torch.Tensor.cuda = orig
+            api._torch = api_torch
+    else:
+        W = api.pack_mask(M).cpu().numpy().view(np.uint32)
+    assert W.shape == (5, 3)
+    for s in range(5):
+        for t in range(70):
+            assert bool((W[s, t // 32] >> (t % 32)) & 1) == M[s, t]

@@ -1,0 +1,224 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Bars: the max-plus product, argmax and runner-up bit-exact against the
+oracle's FP32 mode; F-ULF / F-URF factors bit-exact; b-norm errors within
+1e-6 relative (FP32 terms are identical on both sides, only the summation
+order differs); decisions identical except where the replay harness shows a
+near-tie within 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2205_06619_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+def api():
+    from paper_2205_06619_gb300 import api as a
+    return a
+
+
+def tg(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+# ----------------------------------------------------------------- product
+
+@pytest.mark.parametrize("m,n,r", [(1, 1, 1), (7, 5, 1), (33, 130, 3), (130, 257, 10), (64, 300, 20),
+                                   (5, 1000, 32), (300, 97, 7), (129, 129, 2)])
+def test_maxplus_bitexact(m, n, r):
+    rng = np.random.default_rng(m * 1000 + n * 10 + r)
+    U = rng.standard_normal((m, r)).astype(np.float32)
+    V = rng.standard_normal((r, n)).astype(np.float32)
+    P1, A, P2 = api().maxplus(tg(U), tg(V))
+    e1, ea, e2 = orc.maxplus(U, V, "fp32")
+    assert np.array_equal(P1.cpu().numpy().astype(np.float64), e1)
+    assert np.array_equal(A.cpu().numpy().astype(np.int32), ea)
+    assert np.array_equal(P2.cpu().numpy().astype(np.float64), e2)
+
+
+@pytest.mark.parametrize("r", [1, 2, 5, 32])
+def test_maxplus_ties_take_smaller_index(r):
+    rng = np.random.default_rng(r)
+    U = rng.integers(0, 3, size=(70, r)).astype(np.float32)
+    V = rng.integers(0, 3, size=(r, 90)).astype(np.float32)
+    P1, A, P2 = api().maxplus(tg(U), tg(V))
+    e1, ea, e2 = orc.maxplus(U, V, "fp32")
+    assert np.array_equal(A.cpu().numpy().astype(np.int32), ea)
+    assert np.array_equal(P2.cpu().numpy().astype(np.float64), e2)
+
+
+def test_maxplus_masked_entries_marked():
+    rng = np.random.default_rng(9)
+    U = rng.standard_normal((40, 4)).astype(np.float32)
+    V = rng.standard_normal((4, 77)).astype(np.float32)
+    M = rng.random((40, 77)) < 0.6
+    P1, A, P2 = api().maxplus(tg(U), tg(V), api().pack_mask(M))
+    e1, ea, e2 = orc.maxplus(U, V, "fp32")
+    P1 = P1.cpu().numpy(); A = A.cpu().numpy(); P2 = P2.cpu().numpy()
+    assert np.array_equal(P1[M].astype(np.float64), e1[M]) and np.all(np.isnan(P1[~M]))
+    assert np.array_equal(A[M].astype(np.int32), ea[M]) and np.all(A[~M] == 255)
+    assert np.array_equal(P2[M].astype(np.float64), e2[M]) and np.all(np.isnan(P2[~M]))
+
+
+@pytest.mark.parametrize("m,n,r,obs", [(50, 70, 3, 0.8), (200, 513, 10, 0.5), (31, 33, 1, 0.3)])
+def test_selection_stats(m, n, r, obs):
+    R, M, _, _ = synth.uniform_planted(m, n, r, 0.01, obs, seed=m + n)
+    rng = np.random.default_rng(m)
+    U = rng.random((m, r)).astype(np.float32)
+    V = rng.random((r, n)).astype(np.float32) - 0.5
+    td, ch, f = api().selection_stats(tg(R), tg(U), tg(V), api().pack_mask(M))
+    e_td, e_ch, _ = orc.row_stats(R, M, U, V, 0)
+    assert np.array_equal(ch.cpu().numpy(), e_ch)
+    td = td.cpu().numpy()
+    assert np.all(np.abs(td - e_td) <= 1e-12 * np.maximum(e_td, 1e-300))
+    e_f = orc.error(R, M, U, V)
+    assert rel(f, e_f) <= 1e-12
+
+
+# ------------------------------------------------------- single updates
+
+def _consistent(R, M, r, seed):
+    rng = np.random.default_rng(seed)
+    U0 = rng.random((R.shape[0], r)).astype(np.float32)
+    V = np.stack([orc.residuate_v(R, M, U0[:, l])[0] for l in range(r)])
+    return U0, V
+
+
+@pytest.mark.parametrize("m,n,r", [(20, 30, 3), (130, 300, 5), (64, 700, 10)])
+def test_update_unconditional_matches_oracle(m, n, r):
+    """F-ULF / F-URF applied unconditionally: factors bit-exact, f' within 1e-6."""
+    R, M, _, _ = synth.uniform_planted(m, n, r, 0.01, 0.8, seed=3 * m + n)
+    U0, V0 = _consistent(R, M, r, seed=m)
+    prob = api().Problem(tg(R), api().pack_mask(M), rank=r, U0=tg(U0))
+    Ug, Vg, fg = prob.get()
+    assert np.array_equal(Vg.cpu().numpy().astype(np.float64), V0)
+    U, V = U0.astype(np.float64), V0
+    f = orc.error(R, M, U, V)
+    assert rel(fg, f) <= TOL
+    rng = np.random.default_rng(7)
+    given = np.argwhere(M)
+    for step in range(12):
+        i, j = given[rng.integers(len(given))]
+        k = int(rng.integers(r))
+        typ = step % 2
+        fn, kept = (prob.update_U if typ == 0 else prob.update_V)(int(i), int(j), k, commit_if_decreases=False)
+        U, V, fo = (orc.fulf if typ == 0 else orc.furf)(R, M, U, V, int(i), int(j), k)
+        assert kept
+        assert rel(fn, fo) <= TOL, (step, fn, fo)
+        Ug, Vg, fg = prob.get()
+        assert np.array_equal(Ug.cpu().numpy().astype(np.float64), U), step
+        assert np.array_equal(Vg.cpu().numpy().astype(np.float64), V), step
+        assert rel(fg, fo) <= TOL
+
+
+def test_update_commit_if_decreases_follows_the_paper():
+    """commit_if_decreases keeps the update exactly when f' < f (Algorithm 3)."""
+    R, M, _, _ = synth.uniform_planted(40, 90, 3, 0.01, 0.8, seed=11)
+    U0, V0 = _consistent(R, M, 3, seed=11)
+    prob = api().Problem(tg(R), api().pack_mask(M), rank=3, U0=tg(U0))
+    U, V = U0.astype(np.float64), V0
+    f = orc.error(R, M, U, V)
+    rng = np.random.default_rng(12)
+    given = np.argwhere(M)
+    n_kept = 0
+    for step in range(30):
+        i, j = (int(x) for x in given[rng.integers(len(given))])
+        k = int(rng.integers(3))
+        typ = step % 2
+        fn, kept = (prob.update_U if typ == 0 else prob.update_V)(i, j, k, commit_if_decreases=True)
+        U2, V2, fo = (orc.fulf if typ == 0 else orc.furf)(R, M, U, V, i, j, k)
+        assert rel(fn, fo) <= TOL
+        if abs(fo - f) > TOL * f:
+            assert kept == (fo < f)
+        if kept:
+            U, V, f = U2, V2, fo
+            n_kept += 1
+        Ug, Vg, _ = prob.get()
+        assert np.array_equal(Ug.cpu().numpy().astype(np.float64), U)
+        assert np.array_equal(Vg.cpu().numpy().astype(np.float64), V)
+    assert n_kept > 0
+
+
+def test_update_rejects_bad_indices():
+    R, M, _, _ = synth.uniform_planted(10, 12, 2, 0.01, 0.7, seed=2)
+    prob = api().Problem(tg(R), api().pack_mask(M), rank=2)
+    i, j = np.argwhere(~M)[0]
+    with pytest.raises(api().StmfError):
+        prob.update_U(int(i), int(j), 0)
+    with pytest.raises(api().StmfError):
+        prob.update_V(0, 0, 5)
+
+
+def test_problem_rejects_empty_column():
+    R = np.ones((6, 8), np.float32)
+    M = np.ones((6, 8), bool)
+    M[:, 3] = False
+    with pytest.raises(api().StmfError):
+        api().Problem(tg(R), api().pack_mask(M), rank=2)
+
+
+# ------------------------------------------------------------ factorize
+
+@pytest.mark.parametrize("shape,transposed", [((40, 70), False), ((70, 40), True)])
+def test_factorize_init_matches_oracle(shape, transposed):
+    """Orientation, RandPerm (SplitMix64), Random Acol and V by residuation."""
+    m, n = shape
+    R, M, _, _ = synth.uniform_planted(m, n, 4, 0.01, 0.8, seed=m)
+    U, V, rep, _ = api().factorize(tg(R), api().pack_mask(M), rank=4, sweeps=0, seed=123)
+    ref = orc.factorize(R, M, 4, sweeps=0, seed=123)
+    assert rep["transposed"] == int(transposed)
+    assert np.array_equal(U.cpu().numpy().astype(np.float64), ref["U"])
+    assert np.array_equal(V.cpu().numpy().astype(np.float64), ref["V"])
+    assert rel(rep["f_init"], ref["f_hist"][0]) <= TOL
+
+
+@pytest.mark.parametrize("window", [2, 8, 64])
+def test_factorize_small_replay(window):
+    """Decisions of every row visit replayed against the oracle; the window
+    size must not change any decision."""
+    from tests.replay import replay
+    R, M, _, _ = synth.uniform_planted(36, 52, 3, 0.01, 0.8, seed=21)
+    U, V, rep, trace = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=3, seed=4, window=window,
+                                       trace_cap=1000)
+    out = replay(R, M, 3, trace, seed=4)
+    assert np.array_equal(U.cpu().numpy().astype(np.float64), out["U"])
+    assert np.array_equal(V.cpu().numpy().astype(np.float64), out["V"])
+    assert rel(rep["f_final"], out["f"]) <= TOL
+    assert len(out["divergences"]) <= 1
+
+
+def test_factorize_workload_small_replay():
+    """The 200 x 100 rank-3 workload (runs as 100 x 200), 10 sweeps."""
+    from tests.replay import replay
+    w = synth.workload_small(seed=0)
+    U, V, rep, trace = api().factorize(tg(w["R"]), api().pack_mask(w["mask"]), rank=3, sweeps=10, seed=0,
+                                       trace_cap=2000)
+    assert rep["transposed"] == 1
+    out = replay(w["R"], w["mask"], 3, trace, seed=0)
+    assert np.array_equal(U.cpu().numpy().astype(np.float64), out["U"])
+    assert np.array_equal(V.cpu().numpy().astype(np.float64), out["V"])
+    assert rel(rep["f_final"], out["f"]) <= TOL
+    assert len(out["divergences"]) <= 2
+    f_hist = [t[6] for t in trace]
+    assert all(b <= a for a, b in zip(f_hist, f_hist[1:]))
+
+
+def test_factorize_ragged_and_degenerate_shapes():
+    from tests.replay import replay
+    for (m, n, r, obs, seed) in [(1, 9, 1, 1.0, 1), (9, 1, 2, 1.0, 2), (17, 33, 1, 0.5, 3), (33, 17, 5, 0.9, 4),
+                                 (2, 2, 2, 1.0, 5)]:
+        R, M, _, _ = synth.uniform_planted(m, n, r, 0.01, obs, seed=seed)
+        U, V, rep, trace = api().factorize(tg(R), api().pack_mask(M), rank=r, sweeps=2, seed=seed, trace_cap=100)
+        out = replay(R, M, r, trace, seed=seed)
+        assert np.array_equal(U.cpu().numpy().astype(np.float64), out["U"]), (m, n, r)
+        assert np.array_equal(V.cpu().numpy().astype(np.float64), out["V"]), (m, n, r)
