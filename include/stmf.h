@@ -93,6 +93,8 @@ typedef struct {
     int64_t candidates_issued;/* candidates evaluated on the device (>= tried)      */
     int64_t accepted;         /* updates kept                                        */
     int64_t refreshes;        /* product/statistics refreshes                        */
+    int64_t windows;          /* device windows evaluated                            */
+    int64_t trace_records;    /* trace records written                               */
     double seconds;           /* wall time of the sweep loop                         */
 } stmf_report;
 
@@ -167,6 +169,25 @@ stmf_status stmf_factorize(stmf_ctx *ctx, int m, int n, int r,
                            const float *R, int ldr, const uint32_t *mask, int ldm_words,
                            const stmf_options *opts, float *U_out, float *V_out,
                            stmf_report *report);
+
+/* The same method in three steps, so that sweeps can be run (and timed) in
+ * pieces on one live problem:
+ *   stmf_factorize_begin: orientation, permutation, Random Acol (or opts->U0),
+ *     V by residuation, product planes and statistics; *out receives the
+ *     problem (free it with stmf_problem_destroy).  opts is copied, except
+ *     that opts->trace, if set, must stay valid until stmf_factorize_end.
+ *   stmf_factorize_run: `sweeps` more sweeps (stops early when eps > 0 and a
+ *     sweep changed the error by less than eps); report (host, nullable)
+ *     receives the cumulative counters of the problem.
+ *   stmf_factorize_end: writes U_out, V_out (device, caller's orientation,
+ *     both nullable) and copies up to trace_cap trace records to trace (host,
+ *     nullable).  The problem stays valid. */
+stmf_status stmf_factorize_begin(stmf_ctx *ctx, int m, int n, int r,
+                                 const float *R, int ldr, const uint32_t *mask, int ldm_words,
+                                 const stmf_options *opts, stmf_problem **out);
+stmf_status stmf_factorize_run(stmf_problem *prob, int sweeps, double eps, stmf_report *report);
+stmf_status stmf_factorize_end(stmf_problem *prob, float *U_out, float *V_out,
+                               int32_t *trace, int64_t trace_cap);
 
 /* Fills *opts with the defaults (sweeps 1, eps 0, library window, first
  * improving, FP32, acol_p 5, seed 0, no explicit draws, no trace). */

@@ -22,8 +22,8 @@ STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "INTERNAL
 
 EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", "stmf_maxplus",
            "stmf_selection_stats", "stmf_problem_create", "stmf_problem_destroy", "stmf_update_U",
-           "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_default_options",
-           "stmf_peak_addmax"]
+           "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_factorize_begin",
+           "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_peak_addmax"]
 
 
 class StmfError(RuntimeError):
@@ -43,7 +43,7 @@ class Report(C.Structure):
     _fields_ = [("f_init", C.c_double), ("f_final", C.c_double), ("sweeps_done", C.c_int),
                 ("transposed", C.c_int), ("candidates_tried", C.c_int64),
                 ("candidates_issued", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
-                ("seconds", C.c_double)]
+                ("windows", C.c_int64), ("trace_records", C.c_int64), ("seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,6 +79,9 @@ def load(build_if_missing: bool = True):
     L.stmf_update_V.argtypes = [P, i, i, i, i, C.POINTER(d), C.POINTER(i)]
     L.stmf_problem_get.argtypes = [P, P, P, C.POINTER(d)]
     L.stmf_factorize.argtypes = [P, i, i, i, P, i, P, i, C.POINTER(Options), P, P, C.POINTER(Report)]
+    L.stmf_factorize_begin.argtypes = [P, i, i, i, P, i, P, i, C.POINTER(Options), C.POINTER(P)]
+    L.stmf_factorize_run.argtypes = [P, i, d, C.POINTER(Report)]
+    L.stmf_factorize_end.argtypes = [P, P, P, P, C.c_int64]
     L.stmf_default_options.argtypes = [C.POINTER(Options)]
     L.stmf_default_options.restype = None
     L.stmf_peak_addmax.argtypes = [P, i, i, C.POINTER(d)]
@@ -303,9 +306,60 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
                                     _ptr(U), _ptr(V), C.byref(rep)))
     tr = None
     if trace is not None:
-        nrec = rep.sweeps_done * min(m, n)      # one record per row visit of the wide problem
-        tr = decode_trace(trace[:min(trace_cap, nrec)])
+        tr = decode_trace(trace[:min(trace_cap, rep.trace_records)])
     return U, V, rep.as_dict(), tr
+
+
+class Factorization:
+    """FastSTMF on one live problem, run in pieces (stmf_factorize_begin / _run / _end).
+
+    ``run(sweeps)`` adds sweeps; ``result()`` returns (U, V) in the caller's
+    orientation; ``report`` holds the cumulative counters."""
+
+    def __init__(self, R, mask_words=None, rank=3, window=0, select=0, precision=0, acol_p=5, seed=0,
+                 perm=None, picks=None, U0=None, trace_cap=0):
+        _check_f32(R, "R")
+        self.ctx = context()
+        self.m, self.n, self.r = R.shape[0], R.shape[1], rank
+        self.trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
+        o, self._keep = _options(0, 0.0, window, select, precision, acol_p, seed, perm, picks, U0, self.trace)
+        h = C.c_void_p()
+        ldm = mask_words.shape[1] if mask_words is not None else 0
+        self.ctx.check(load().stmf_factorize_begin(self.ctx.h, self.m, self.n, rank, _ptr(R), R.stride(0),
+                                                   _ptr(mask_words), ldm, C.byref(o), C.byref(h)))
+        self.h = h
+        self.report = None
+
+    def run(self, sweeps, eps=0.0):
+        rep = Report()
+        self.ctx.check(load().stmf_factorize_run(self.h, sweeps, eps, C.byref(rep)))
+        self.report = rep.as_dict()
+        return self.report
+
+    def result(self):
+        torch = _torch()
+        U = torch.empty((self.m, self.r), device="cuda", dtype=torch.float32)
+        V = torch.empty((self.r, self.n), device="cuda", dtype=torch.float32)
+        cap = 0 if self.trace is None else self.trace.shape[0]
+        tp = None if self.trace is None else C.c_void_p(self.trace.ctypes.data)
+        self.ctx.check(load().stmf_factorize_end(self.h, _ptr(U), _ptr(V), tp, cap))
+        return U, V
+
+    def trace_records(self):
+        if self.trace is None or self.report is None:
+            return []
+        return decode_trace(self.trace[:min(self.trace.shape[0], self.report["trace_records"])])
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().stmf_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def peak_addmax(mode=0, iters=4096):

@@ -1,7 +1,7 @@
 // Internal declarations of the FastSTMF CUDA library (sm_103a).
 //
-// Device layout of a problem (all padded so that every row is a whole number
-// of 256-float chunks and every row count a multiple of 256):
+// Device layout of a problem (every row a whole number of 256-float chunks,
+// every row count a multiple of 256):
 //   R    mp x np  fp32, given entries as given, every other entry (including
 //                 padding) a quiet NaN.  The NaN is the mask of the hot loops:
 //                 x - NaN = NaN, fminf/fmaxf drop a NaN operand, so residuation
@@ -31,29 +31,39 @@ struct stmf_ctx {
     size_t ws_bytes;
 };
 
-// Control block kept in device memory; kernels of one window read and write
-// it, so a window can be replayed from a CUDA graph without host arguments.
+// Control block in device memory.  The kernels of the row loop read and
+// update it, so one sweep runs as a single CUDA graph launch with no host
+// round trip: select decides, commits and advances the row; the graph's
+// conditional nodes read the flags the kernels set.
 struct stmf_ctl {
     int i;             // current row
+    int m;             // rows per sweep
+    int sweep;         // sweep index (for the trace)
     int pos;           // next position in the column order
     int row_start;     // 1 before the first window of a row
-    int wj;            // j-candidates per window (each gives F-ULF and F-URF)
+    int wj;            // j-candidates of the next window (each gives F-ULF, F-URF)
+    int wj0;           // j-candidates of a row's first window
+    int wmax;          // candidates per window (upper bound, even)
     int nc;            // candidates in the current window
-    int ncand_row;     // candidates of the row consumed so far (sequential index)
-    int kept;          // result of the last select: 1 if a candidate was kept
+    int ncand_row;     // candidates of the row consumed so far
+    int kept;          // 1 if the last select kept a candidate
     int row_done;      // 1 once the row is finished (kept or exhausted)
-    int kept_pos;      // position (candidate index / 2) of the kept candidate
-    int kept_j, kept_k, kept_type;
-    int kept_c;        // window slot of the kept candidate
+    int kept_pos, kept_j, kept_k, kept_type, kept_c;
+    int dirty_k;       // -2: planes current; -1: refresh all components; k: refresh k
+    int select_mode;   // 0 first improving (paper), 1 best of window
     int err;           // device-detected error code (0 = none)
     int nu, nv;        // F-ULF / F-URF candidates of the window
     int exhausted;     // 1 when the window reached the end of the row's candidates
     int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // window slots per type
     long long tried;   // sequential-method candidates tried (cumulative)
     long long issued;  // candidates evaluated on the device (cumulative)
-    double f_ulf;      // current error in the F-ULF kernel's summation tree
-    double f_urf;      // current error in the F-URF kernel's summation tree
-    double f_new;      // error after the kept candidate
+    long long accepted;
+    long long refreshes;
+    long long windows;
+    double f;          // current error (sum over j of td_col[j])
+    double f_new;      // error after the kept candidate (f + Delta)
+    int32_t *trace;    // device trace buffer (STMF_TRACE_INTS per record) or NULL
+    long long trace_cap, ntrace;
 };
 
 struct stmf_problem {
@@ -69,18 +79,28 @@ struct stmf_problem {
     double *tdcol;     // np
     int *colhist;      // np x r
     int *rowhist;      // r
+    int *rank;         // np
     int *order;        // np: columns by decreasing td_col, ties to smaller j
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
-    double *part_ulf;  // (mp/4) x STMF_WMAX partial errors of F-ULF blocks
-    double *part_urf;  // (np/32) x STMF_WMAX partial errors of F-URF blocks
+    double *part_ulf;  // (mp/4) x STMF_WMAX partial changes of F-ULF blocks
+    double *part_urf;  // (np/32) x STMF_WMAX partial changes of F-URF blocks
     double *fc;        // STMF_WMAX candidate errors
     stmf_ctl *ctl;     // device control block
     stmf_ctl *ctl_host;// pinned host mirror
-    int window;        // candidates per window (even, <= STMF_WMAX)
-    long long refreshes;
-    int dirty_k;       // component to refresh (-1: all), -2: clean
+    int32_t *trace_dev;// device trace buffer
+    // factorization bookkeeping
+    int transposed;    // input was tall and is stored transposed
+    int m0, n0;        // caller's shape
+    int *perm;         // device permutation (oriented rows -> caller rows/cols)
+    double f_init;     // error after initialisation
+    int sweeps_done;
+    double seconds;    // wall time spent in sweeps
+    // sweep graph
+    cudaGraphExec_t sweep_exec;
+    cudaGraph_t sweep_graph;
+    unsigned long long h_row, h_dirty, h_win;   // cudaGraphConditionalHandle values
 };
 
 // ---------------------------------------------------------------- launchers
@@ -93,7 +113,7 @@ cudaError_t launch_planes(cudaStream_t st, stmf_problem *P, int *chpart);
 int planes_nparts(int m);
 cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int *chpart, int nparts,
                                 int ldpart, int n, int r, double *tdcol, int *colhist);
-cudaError_t launch_order(cudaStream_t st, const double *tdcol, int n, int *order);
+cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P);
 
 // kernels_update.cu
 cudaError_t launch_pack(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm,
@@ -106,19 +126,19 @@ cudaError_t launch_unorient(cudaStream_t st, const stmf_problem *P, int transpos
 cudaError_t launch_empty_rows(cudaStream_t st, const float *X, int ldx, int rows, int *nempty);
 cudaError_t launch_transpose(cudaStream_t st, const float *X, int ldx, int rows, int cols,
                              float *XT, int ldxt);
-cudaError_t launch_rowstat(cudaStream_t st, const float *X, int ldx, int rows, int cols,
-                           const float *y, int ystride, float *min1, float *min2, int *arg);
 cudaError_t launch_acol(cudaStream_t st, const float *R, int ld, int m, int n, int r,
                         const int *picks, int p, float *U);
 cudaError_t launch_copy_rows(cudaStream_t st, const float *src, int lds, float *dst, int ldd,
                              int rows, int cols);
-cudaError_t launch_begin_row(cudaStream_t st, stmf_problem *P, int i, int wj0);
+cudaError_t launch_stats(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_window(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots);
-cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int null_mode);
-cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int mode);
+cudaError_t launch_eval(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);
 cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph);
+cudaError_t launch_sweep_begin(cudaStream_t st, stmf_problem *P, int in_graph);
 
 // peak.cu
 cudaError_t launch_peak(cudaStream_t st, int mode, int iters, int blocks, float *sink);

@@ -218,10 +218,11 @@ k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *
         chpart[((size_t)part * ld + col0 + e / r) * r + e % r] = sHist[e];
 }
 
-// td_col[t] = sum over parts (fixed order); colhist likewise.
+// td_col[t] = sum over parts (fixed order); colhist likewise.  Also clears
+// the rank counters of the column order (when rank != nullptr).
 __global__ void k_td_finalize(const double *__restrict__ tdpart, const int *__restrict__ chpart,
                               int nparts, int ldpart, int n, int r, double *__restrict__ tdcol,
-                              int *__restrict__ colhist)
+                              int *__restrict__ colhist, int *__restrict__ rank)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -234,29 +235,56 @@ __global__ void k_td_finalize(const double *__restrict__ tdpart, const int *__re
             for (int p = 0; p < nparts; ++p) h += chpart[((size_t)p * ldpart + t) * r + l];
             colhist[(size_t)t * r + l] = h;
         }
+    if (rank) rank[t] = 0;
 }
 
 // Column order of Algorithm 3: decreasing td_col, equal values keep the
-// smaller j first.  Rank by counting (every CTA scans all keys from shared
-// memory), then scatter.
-__global__ void __launch_bounds__(256) k_order(const double *__restrict__ tdcol, int n, int *__restrict__ order)
+// smaller j first.  rank_j = #{e : td_e > td_j} + #{e < j : td_e = td_j},
+// counted over a 2-D grid (columns x key chunks held in shared memory) so
+// the O(n^2) comparisons spread over every SM.  td_col >= 0, so its IEEE bit
+// pattern orders like the value and compares as a 64-bit integer.
+constexpr int RANK_CHUNK = 2048;
+__global__ void __launch_bounds__(256) k_rank(const double *__restrict__ tdcol, int n, int *__restrict__ rank)
 {
-    __shared__ double sk[2048];
+    __shared__ unsigned long long sk[RANK_CHUNK];
     const int j = blockIdx.x * 256 + threadIdx.x;
-    const double kj = j < n ? tdcol[j] : 0.0;
-    int rank = 0;
-    for (int base = 0; base < n; base += 2048) {
-        const int len = min(2048, n - base);
-        __syncthreads();
-        for (int e = threadIdx.x; e < len; e += 256) sk[e] = tdcol[base + e];
-        __syncthreads();
-        if (j < n)
-            for (int e = 0; e < len; ++e) {
-                const double x = sk[e];
-                rank += (x > kj) | ((x == kj) & (base + e < j));
-            }
+    const int base = blockIdx.y * RANK_CHUNK;
+    const int len = min(RANK_CHUNK, n - base);
+    for (int e = threadIdx.x; e < len; e += 256) sk[e] = (unsigned long long)__double_as_longlong(tdcol[base + e]);
+    __syncthreads();
+    if (j >= n) return;
+    const unsigned long long kj = (unsigned long long)__double_as_longlong(tdcol[j]);
+    const int jl = j - base;   // chunk-local index of j (may be outside the chunk)
+    int cnt = 0;
+    for (int e = 0; e < len; ++e) {
+        const unsigned long long x = sk[e];
+        cnt += (x > kj) | ((x == kj) & (e < jl));
     }
-    if (j < n) order[rank] = j;
+    if (cnt) atomicAdd(&rank[j], cnt);
+}
+
+// order[rank_j] = j, and the current error f = sum_j td_col[j] (fixed order:
+// strided per thread, then a fixed tree), written to the control block.
+__global__ void __launch_bounds__(1024) k_scatter_f(const double *__restrict__ tdcol, const int *__restrict__ rank,
+                                                    int n, int *__restrict__ order, stmf_ctl *ctl)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += 1024) {
+        order[rank[j]] = j;
+        s += tdcol[j];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 512; o; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && ctl) {
+        ctl->f = red[0];
+        ctl->dirty_k = -2;
+        ctl->refreshes += 1;
+    }
 }
 
 }  // namespace
@@ -289,19 +317,21 @@ int planes_nparts(int m) { return (m + TR * TILES - 1) / (TR * TILES); }
 cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int *chpart, int nparts,
                                 int ldpart, int n, int r, double *tdcol, int *colhist)
 {
-    k_td_finalize<<<(n + 255) / 256, 256, 0, st>>>(tdpart, chpart, nparts, ldpart, n, r, tdcol, colhist);
+    k_td_finalize<<<(n + 255) / 256, 256, 0, st>>>(tdpart, chpart, nparts, ldpart, n, r, tdcol, colhist, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_td_finalize(cudaStream_t st, const double *tdpart, int nparts, int ldpart, int n,
-                               double *tdcol)
+// Product planes, statistics, column order and error of a problem.
+cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P)
 {
-    k_td_finalize<<<(n + 255) / 256, 256, 0, st>>>(tdpart, nullptr, nparts, ldpart, n, 0, tdcol, nullptr);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_order(cudaStream_t st, const double *tdcol, int n, int *order)
-{
-    k_order<<<(n + 255) / 256, 256, 0, st>>>(tdcol, n, order);
+    cudaError_t e = launch_planes(st, P, P->chpart);
+    if (e != cudaSuccess) return e;
+    k_td_finalize<<<(P->n + 255) / 256, 256, 0, st>>>(P->tdpart, P->chpart, planes_nparts(P->m), P->np, P->n, P->r,
+                                                      P->tdcol, P->colhist, P->rank);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 grid((P->n + 255) / 256, (P->n + RANK_CHUNK - 1) / RANK_CHUNK);
+    k_rank<<<grid, 256, 0, st>>>(P->tdcol, P->n, P->rank);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scatter_f<<<1, 1024, 0, st>>>(P->tdcol, P->rank, P->n, P->order, P->ctl);
     return cudaGetLastError();
 }

@@ -13,9 +13,9 @@
 //
 // Every value of a candidate's U', V' and every term of f' is computed with
 // the same FP32 operations as the plain definition, so they are bit-identical
-// to it; only the order of the error summation differs (FP32 partials of at
-// most 16 terms, FP32 warp trees, FP64 across warps and blocks, all in a
-// fixed order).
+// to it.  The error is accumulated as the change f' - f (per-entry differences
+// of the FP32 terms) in FP32 partials of 8 entries, FP32 warp trees and FP64
+// across warps and blocks, all in a fixed order; f' = f + (f' - f).
 #include "common.cuh"
 
 #define QNAN __int_as_float(0x7fffffff)
@@ -110,33 +110,6 @@ __global__ void k_transpose(const float *__restrict__ X, int ldx, int rows, int 
     }
 }
 
-// Top-2 residuation statistics of one row of X against y:
-//   d_t = X_st - y_t over given t;  min1 = min d, arg = smallest t with d = min1,
-//   min2 = min over t != arg.  One warp per row.
-__global__ void k_rowstat(const float *__restrict__ X, int ldx, int rows, int cols,
-                          const float *__restrict__ y, int ystride, float *__restrict__ min1,
-                          float *__restrict__ min2, int *__restrict__ arg)
-{
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= rows) return;
-    float a1 = INFINITY, a2 = INFINITY;
-    int ai = 0x7fffffff;
-    const float *x = X + (size_t)row * ldx;
-    for (int t = lane; t < cols; t += 32) {
-        const float d = x[t] - y[(size_t)t * ystride];
-        if (d < a1) { a2 = a1; a1 = d; ai = t; }     // NaN compares false: skipped
-        else a2 = fminf(a2, d);
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float b1 = __shfl_xor_sync(FULL, a1, o), b2 = __shfl_xor_sync(FULL, a2, o);
-        const int bi = __shfl_xor_sync(FULL, ai, o);
-        if (b1 < a1 || (b1 == a1 && bi < ai)) { a2 = fminf(b2, a1); a1 = b1; ai = bi; }
-        else a2 = fminf(a2, b1);
-    }
-    if (lane == 0) { min1[row] = a1; min2[row] = a2; arg[row] = ai; }
-}
-
 // Random Acol (Section "Comparison of strategies"): U_sl = mean of the given
 // R_s,c over the picks c of component l, summed in pick order; if none is
 // given, the mean of the given entries of row s in column order.
@@ -168,13 +141,85 @@ __global__ void k_copy_rows(const float *__restrict__ src, int lds, float *__res
     if (t < cols && s < rows) dst[(size_t)s * ldd + t] = src[(size_t)s * lds + t];
 }
 
+// ---------------------------------------------------- residuation statistics
+
+__device__ __forceinline__ void top2_push(float d, int idx, float &a1, int &ai, float &a2)
+{
+    // NaN (entry not given) compares false and is dropped by fminf
+    if (d < a1) { a2 = a1; a1 = d; ai = idx; }
+    else a2 = fminf(a2, d);
+}
+
+__device__ __forceinline__ void top2_warp_merge(float &a1, int &ai, float &a2)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float b1 = __shfl_xor_sync(FULL, a1, o), b2 = __shfl_xor_sync(FULL, a2, o);
+        const int bi = __shfl_xor_sync(FULL, ai, o);
+        if (b1 < a1 || (b1 == a1 && bi < ai)) { a2 = fminf(b2, a1); a1 = b1; ai = bi; }
+        else a2 = fminf(a2, b1);
+    }
+}
+
+// Top-2 residuation statistics of the component(s) named by ctl->dirty_k
+// (-1: every component, -2: nothing to do):
+//   column statistics of k (warps 0..n-1, one row of RT each):
+//     d_s = R_st - U_sk over given s; cmin1 = min d, carg = smallest s at the
+//     minimum, cmin2 = min over s != carg
+//   row statistics of k (warps n..n+m-1, one row of R each):
+//     d_t = R_st - V_kt over given t; rmin1, rarg, rmin2 likewise.
+// V'_kt of F-ULF is min(R_it - U''_ik, carg == i ? cmin2 : cmin1) and U'_sk of
+// F-URF is min(R_sj - V''_kj, rarg == j ? rmin2 : rmin1): O(n) / O(m) seeds.
+__global__ void __launch_bounds__(256) k_stats(stmf_problem P)
+{
+    const int dk = P.ctl->dirty_k;
+    if (dk == -2) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= P.n + P.m) return;
+    const bool col = warp < P.n;
+    const int row = col ? warp : warp - P.n;
+    const float4 *x4 = reinterpret_cast<const float4 *>(col ? P.RT + (size_t)row * P.mp : P.R + (size_t)row * P.np);
+    const int len4 = (col ? P.mp : P.np) >> 2;
+    const int l0 = dk < 0 ? 0 : dk, l1 = dk < 0 ? P.r : dk + 1;
+    for (int l = l0; l < l1; ++l) {
+        float a1 = INFINITY, a2 = INFINITY;
+        int ai = 0x7fffffff;
+        for (int f = lane; f < len4; f += 32) {
+            const float4 x = x4[f];
+            float y[4];
+            if (col) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[q] = P.U[(size_t)(4 * f + q) * P.r + l];
+            } else {
+                const float4 v = reinterpret_cast<const float4 *>(P.V + (size_t)l * P.np)[f];
+                y[0] = v.x; y[1] = v.y; y[2] = v.z; y[3] = v.w;
+            }
+            top2_push(x.x - y[0], 4 * f + 0, a1, ai, a2);
+            top2_push(x.y - y[1], 4 * f + 1, a1, ai, a2);
+            top2_push(x.z - y[2], 4 * f + 2, a1, ai, a2);
+            top2_push(x.w - y[3], 4 * f + 3, a1, ai, a2);
+        }
+        top2_warp_merge(a1, ai, a2);
+        if (lane == 0) {
+            if (col) {
+                const size_t e = (size_t)l * P.np + row;
+                P.cmin1[e] = a1; P.cmin2[e] = a2; P.carg[e] = ai;
+            } else {
+                const size_t e = (size_t)l * P.mp + row;
+                P.rmin1[e] = a1; P.rmin2[e] = a2; P.rarg[e] = ai;
+            }
+        }
+    }
+}
+
 // --------------------------------------------------------------- row loop
 
 // Window of candidates (Algorithm 3): the next wj columns j of the order with
-// R_ij given; k_j = argmax_l (rowhist_i[l] + colhist[j][l]) (TD_A, smaller l
-// on ties).  Each j gives F-ULF (slot 2a) then F-URF (slot 2a+1).  At the
+// R_ij given; k_j = argmax_l (rowhist_i[l] + colhist[j][l]) (TD_A; the multiset
+// union adds multiplicities; smaller l on ties).  Each j gives F-ULF (slot 2a)
+// then F-URF (slot 2a+1), the order in which Algorithm 3 tries them.  At the
 // first window of a row the row histogram is rebuilt.
-__global__ void __launch_bounds__(256) k_window(stmf_problem P, int wmax)
+__global__ void __launch_bounds__(256) k_window(stmf_problem P)
 {
     __shared__ int sh[STMF_MAX_RANK];
     __shared__ int sj[STMF_WMAX / 2];
@@ -196,7 +241,7 @@ __global__ void __launch_bounds__(256) k_window(stmf_problem P, int wmax)
         if (tid < r) sh[tid] = P.rowhist[tid];
     }
     if (tid < 32) {
-        const int want = min(ctl->wj, wmax / 2);
+        const int want = min(ctl->wj, ctl->wmax / 2);
         int pos = ctl->pos, have = 0;
         const int lane = tid;
         while (have < want && pos < P.n) {
@@ -208,8 +253,7 @@ __global__ void __launch_bounds__(256) k_window(stmf_problem P, int wmax)
             if (ok && have + rank < want) sj[have + rank] = j;
             const int take = min(__popc(b), want - have);
             if (take < __popc(b)) {
-                // stop right after the take-th given entry
-                unsigned bb = b;
+                unsigned bb = b;          // stop at the first given entry not taken
                 for (int z = 0; z < take; ++z) bb &= bb - 1u;
                 pos += __ffs(bb) - 1;
             } else {
@@ -233,6 +277,8 @@ __global__ void __launch_bounds__(256) k_window(stmf_problem P, int wmax)
         c0[0] = j; c0[1] = best; c0[2] = 0; c0[3] = base + tid;
         int *c1 = P.cand + 8 * (2 * tid + 1);
         c1[0] = j; c1[1] = best; c1[2] = 1; c1[3] = base + tid;
+        ctl->ulist[tid] = 2 * tid;
+        ctl->vlist[tid] = 2 * tid + 1;
     }
     if (tid == 0) {
         ctl->nc = 2 * cnt;
@@ -241,11 +287,10 @@ __global__ void __launch_bounds__(256) k_window(stmf_problem P, int wmax)
         ctl->exhausted = spos >= P.n;
         ctl->pos = spos;
     }
-    if (tid < cnt) { ctl->ulist[tid] = 2 * tid; ctl->vlist[tid] = 2 * tid + 1; }
 }
 
-// Seeds: for F-ULF slots V'_k. from the column statistics; for F-URF slots
-// U'_.k from the row statistics.  grid.y = slot, grid.x covers max(np, mp).
+// Seeds: F-ULF slots get V'_k. from the column statistics, F-URF slots U'_.k
+// from the row statistics.  grid.y = slot, grid.x covers max(np, mp).
 __global__ void k_seed(stmf_problem P)
 {
     const stmf_ctl *ctl = P.ctl;
@@ -256,7 +301,7 @@ __global__ void k_seed(stmf_problem P)
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (type == 0) {
         if (x >= P.np) return;
-        const float useed = P.R[(size_t)i * P.np + j] - P.V[(size_t)k * P.np + j];
+        const float useed = P.R[(size_t)i * P.np + j] - P.V[(size_t)k * P.np + j];   // U''_ik
         float v = 0.f;
         if (x < P.n) {
             const size_t e = (size_t)k * P.np + x;
@@ -266,7 +311,7 @@ __global__ void k_seed(stmf_problem P)
         P.Vc[(size_t)c * P.np + x] = v;
     } else {
         if (x >= P.mp) return;
-        const float vseed = P.R[(size_t)i * P.np + j] - P.U[(size_t)i * P.r + k];
+        const float vseed = P.R[(size_t)i * P.np + j] - P.U[(size_t)i * P.r + k];    // V''_kj
         float u = 0.f;
         if (x < P.m) {
             const size_t e = (size_t)k * P.mp + x;
@@ -307,78 +352,77 @@ __device__ __forceinline__ float bterm(float rv, float p1, float p2, int a, int 
 
 constexpr int CG = 8;   // candidates per phase-1 group
 
-// F-ULF window evaluation.  One CTA owns 4 full rows: phase 1 computes
-// U'_sk of every F-ULF candidate for its rows, phase 2 the candidates' error
-// over those rows.  null_mode: one candidate equal to the current state
-// (k = 0, U'_.0 = U_.0, V'_0. = V_0.): gives the current error in this
-// kernel's summation tree.
-__global__ void __launch_bounds__(256, 2) k_eval_ulf(stmf_problem P, int null_mode)
+struct EvalSmem {
+    float su[STMF_WMAX / 2][4];
+    __align__(16) float sv[STMF_WMAX / 2][32];
+    float red[8][32];
+    int sslot[STMF_WMAX / 2], sk[STMF_WMAX / 2];
+};
+
+// F-ULF part of a window.  One block owns 4 full rows: phase 1 computes
+// U'_sk = min over t of (R_st - V'_kt) for every F-ULF candidate, phase 2 the
+// candidates' change of the error over those rows,
+//   Delta = sum_st ( |R_st - P'_st| - |R_st - P_st| ),
+// accumulated per entry so that its rounding error scales with the size of
+// the change (a candidate that changes nothing gives exactly 0).
+__device__ __forceinline__ void eval_ulf_block(const stmf_problem &P, EvalSmem &S, int b)
 {
-    __shared__ float su[STMF_WMAX / 2][4];
-    __shared__ float red[8][32];
-    __shared__ int sslot[STMF_WMAX / 2], sk[STMF_WMAX / 2];
     const stmf_ctl *ctl = P.ctl;
-    const int nu = null_mode ? 1 : ctl->nu;
+    const int nu = ctl->nu;
     if (nu == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int s0 = blockIdx.x * 4;
+    const int s0 = b * 4;
     const int nf4 = P.np >> 2;
     if (tid < nu) {
-        const int slot = null_mode ? 0 : ctl->ulist[tid];
-        sslot[tid] = slot;
-        sk[tid] = null_mode ? 0 : P.cand[8 * slot + 1];
+        const int slot = ctl->ulist[tid];
+        S.sslot[tid] = slot;
+        S.sk[tid] = P.cand[8 * slot + 1];
     }
     __syncthreads();
     const float4 *R4 = reinterpret_cast<const float4 *>(P.R + (size_t)s0 * P.np);
 
-    // ---- phase 1: U'_sk = min over t of (R_st - V'_kt)
-    if (null_mode) {
-        if (tid < 4) su[0][tid] = P.U[(size_t)(s0 + tid) * P.r + 0];
-    } else {
-        for (int g = 0; g < nu; g += CG) {
-            float acc[32];
+    // ---- phase 1
+    for (int g = 0; g < nu; g += CG) {
+        float acc[32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) acc[q] = INFINITY;
-            for (int f = tid; f < nf4; f += 256) {
-                float4 r4[4];
+        for (int q = 0; q < 32; ++q) acc[q] = INFINITY;
+        for (int f = tid; f < nf4; f += 256) {
+            float4 r4[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) r4[i] = R4[(size_t)i * nf4 + f];
+            for (int i = 0; i < 4; ++i) r4[i] = R4[(size_t)i * nf4 + f];
 #pragma unroll
-                for (int cc = 0; cc < CG; ++cc) {
-                    if (g + cc < nu) {
-                        const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)sslot[g + cc] * P.np)[f];
+            for (int cc = 0; cc < CG; ++cc) {
+                if (g + cc < nu) {
+                    const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[g + cc] * P.np)[f];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float a = acc[cc * 4 + i];
-                            a = fminf(a, r4[i].x - v4.x);
-                            a = fminf(a, r4[i].y - v4.y);
-                            a = fminf(a, r4[i].z - v4.z);
-                            a = fminf(a, r4[i].w - v4.w);
-                            acc[cc * 4 + i] = a;
-                        }
+                    for (int i = 0; i < 4; ++i) {
+                        float a = acc[cc * 4 + i];
+                        a = fminf(a, r4[i].x - v4.x);
+                        a = fminf(a, r4[i].y - v4.y);
+                        a = fminf(a, r4[i].z - v4.z);
+                        a = fminf(a, r4[i].w - v4.w);
+                        acc[cc * 4 + i] = a;
                     }
                 }
             }
-            const float w = reduce_scatter32<true>(acc, lane);
-            red[warp][lane] = w;
-            __syncthreads();
-            if (tid < 32) {
-                float x = red[0][tid];
-#pragma unroll
-                for (int q = 1; q < 8; ++q) x = fminf(x, red[q][tid]);
-                const int cc = tid >> 2, i = tid & 3;
-                if (g + cc < nu) {
-                    su[g + cc][i] = x;
-                    P.Uc[(size_t)sslot[g + cc] * P.mp + s0 + i] = x;
-                }
-            }
-            __syncthreads();
         }
+        const float w = reduce_scatter32<true>(acc, lane);
+        S.red[warp][lane] = w;
+        __syncthreads();
+        if (tid < 32) {
+            float x = S.red[0][tid];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) x = fminf(x, S.red[q][tid]);
+            const int cc = tid >> 2, i = tid & 3;
+            if (g + cc < nu) {
+                S.su[g + cc][i] = x;
+                P.Uc[(size_t)S.sslot[g + cc] * P.mp + s0 + i] = x;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
-    // ---- phase 2: error of every candidate over the 4 rows; a thread owns
-    // 2 rows x 4 columns per step (rows 2*rg, 2*rg+1), 128 threads per row pair
+    // ---- phase 2: thread owns 2 rows x 4 columns per step
     float sum[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) sum[q] = 0.f;
@@ -389,7 +433,7 @@ __global__ void __launch_bounds__(256, 2) k_eval_ulf(stmf_problem P, int null_mo
     const float4 *P24 = reinterpret_cast<const float4 *>(P.P2 + (size_t)s0 * P.np) + rowoff;
     const uint32_t *A4 = reinterpret_cast<const uint32_t *>(P.A + (size_t)s0 * P.np) + rowoff;
     for (int f = cl; f < nf4; f += 128) {
-        float rv[2][4], p1[2][4], p2[2][4];
+        float rv[2][4], p1[2][4], p2[2][4], t0[2][4];
         int a[2][4];
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -399,64 +443,63 @@ __global__ void __launch_bounds__(256, 2) k_eval_ulf(stmf_problem P, int null_mo
             p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
             p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) a[i][jj] = (w >> (8 * jj)) & 0xff;
+            for (int jj = 0; jj < 4; ++jj) {
+                a[i][jj] = (w >> (8 * jj)) & 0xff;
+                t0[i][jj] = fmaxf(fabsf(rv[i][jj] - p1[i][jj]), 0.f);
+            }
         }
 #pragma unroll
         for (int cc = 0; cc < 32; ++cc) {
+            // keep the compiler from hoisting every candidate's loads at once
+            asm volatile("" ::: "memory");
             if (cc < nu) {
-                const int k = sk[cc];
-                float4 v4;
-                if (null_mode) v4 = reinterpret_cast<const float4 *>(P.V)[f];
-                else v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)sslot[cc] * P.np)[f];
+                const int k = S.sk[cc];
+                const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[cc] * P.np)[f];
                 const float v[4] = {v4.x, v4.y, v4.z, v4.w};
                 float t[2][4];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    const float u = su[cc][2 * rg + i];
+                    const float u = S.su[cc][2 * rg + i];
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u + v[jj]);
+                    for (int jj = 0; jj < 4; ++jj)
+                        t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u + v[jj]) - t0[i][jj];
                 }
                 sum[cc] += ((t[0][0] + t[0][1]) + (t[0][2] + t[0][3])) + ((t[1][0] + t[1][1]) + (t[1][2] + t[1][3]));
             }
         }
     }
     const float w = reduce_scatter32<false>(sum, lane);
-    red[warp][lane] = w;
+    S.red[warp][lane] = w;
     __syncthreads();
     if (tid < nu) {
         double x = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x += (double)red[q][tid];
-        P.part_ulf[(size_t)blockIdx.x * STMF_WMAX + sslot[tid]] = x;
+        for (int q = 0; q < 8; ++q) x += (double)S.red[q][tid];
+        P.part_ulf[(size_t)b * STMF_WMAX + S.sslot[tid]] = x;
     }
 }
 
-// F-URF window evaluation.  One CTA owns a strip of 32 full columns: phase 1
-// computes V'_kt of every F-URF candidate for its columns from rows of RT,
-// phase 2 the candidates' error over the strip.
-__global__ void __launch_bounds__(256, 2) k_eval_urf(stmf_problem P, int null_mode)
+// F-URF part of a window.  One block owns a strip of 32 full columns: phase 1
+// computes V'_kt = min over s of (R_st - U'_sk) for its columns from rows of
+// RT, phase 2 the candidates' change of the error over the strip.
+__device__ __forceinline__ void eval_urf_block(const stmf_problem &P, EvalSmem &S, int b)
 {
-    __shared__ __align__(16) float sv[STMF_WMAX / 2][32];
-    __shared__ float red[8][32];
-    __shared__ int sslot[STMF_WMAX / 2], sk[STMF_WMAX / 2];
     const stmf_ctl *ctl = P.ctl;
-    const int nv = null_mode ? 1 : ctl->nv;
+    const int nv = ctl->nv;
     if (nv == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t0 = blockIdx.x * 32;
+    const int t0c = b * 32;
     if (tid < nv) {
-        const int slot = null_mode ? 1 : ctl->vlist[tid];
-        sslot[tid] = slot;
-        sk[tid] = null_mode ? 0 : P.cand[8 * slot + 1];
+        const int slot = ctl->vlist[tid];
+        S.sslot[tid] = slot;
+        S.sk[tid] = P.cand[8 * slot + 1];
     }
     __syncthreads();
 
-    // ---- phase 1: V'_kt = min over s of (R_st - U'_sk), warp w owns columns t0+4w..+3
-    if (null_mode) {
-        if (tid < 32) sv[0][tid] = P.V[t0 + tid];
-    } else {
+    // ---- phase 1: warp w owns columns t0c+4w .. +3
+    {
         const int nf4 = P.mp >> 2;
-        const float4 *X4 = reinterpret_cast<const float4 *>(P.RT + (size_t)(t0 + 4 * warp) * P.mp);
+        const float4 *X4 = reinterpret_cast<const float4 *>(P.RT + (size_t)(t0c + 4 * warp) * P.mp);
         for (int g = 0; g < nv; g += CG) {
             float acc[32];
 #pragma unroll
@@ -468,7 +511,7 @@ __global__ void __launch_bounds__(256, 2) k_eval_urf(stmf_problem P, int null_mo
 #pragma unroll
                 for (int cc = 0; cc < CG; ++cc) {
                     if (g + cc < nv) {
-                        const float4 u4 = reinterpret_cast<const float4 *>(P.Uc + (size_t)sslot[g + cc] * P.mp)[f];
+                        const float4 u4 = reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[g + cc] * P.mp)[f];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             float a = acc[cc * 4 + i];
@@ -484,21 +527,21 @@ __global__ void __launch_bounds__(256, 2) k_eval_urf(stmf_problem P, int null_mo
             const float x = reduce_scatter32<true>(acc, lane);
             const int cc = lane >> 2, i = lane & 3;
             if (g + cc < nv) {
-                sv[g + cc][4 * warp + i] = x;
-                P.Vc[(size_t)sslot[g + cc] * P.np + t0 + 4 * warp + i] = x;
+                S.sv[g + cc][4 * warp + i] = x;
+                P.Vc[(size_t)S.sslot[g + cc] * P.np + t0c + 4 * warp + i] = x;
             }
         }
     }
     __syncthreads();
 
-    // ---- phase 2: error over the strip; thread: 4 columns x 2 consecutive rows
+    // ---- phase 2: thread owns 4 columns x 2 consecutive rows per step
     const int cl = tid & 7, rl = tid >> 3;
-    const int tc = t0 + cl * 4;
+    const int tc = t0c + cl * 4;
     float sum[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) sum[q] = 0.f;
     for (int sb = rl * 2; sb < P.m; sb += 64) {
-        float rv[2][4], p1[2][4], p2[2][4];
+        float rv[2][4], p1[2][4], p2[2][4], t0[2][4];
         int a[2][4];
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -511,92 +554,131 @@ __global__ void __launch_bounds__(256, 2) k_eval_urf(stmf_problem P, int null_mo
             p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
             p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) a[i][jj] = (w >> (8 * jj)) & 0xff;
+            for (int jj = 0; jj < 4; ++jj) {
+                a[i][jj] = (w >> (8 * jj)) & 0xff;
+                t0[i][jj] = fmaxf(fabsf(rv[i][jj] - p1[i][jj]), 0.f);
+            }
         }
 #pragma unroll
         for (int cc = 0; cc < 32; ++cc) {
+            asm volatile("" ::: "memory");
             if (cc < nv) {
-                const int k = sk[cc];
-                float u[2];
-                if (null_mode) {
-                    u[0] = P.U[(size_t)sb * P.r];
-                    u[1] = P.U[(size_t)(sb + 1) * P.r];
-                } else {
-                    const float2 u2 = *reinterpret_cast<const float2 *>(P.Uc + (size_t)sslot[cc] * P.mp + sb);
-                    u[0] = u2.x; u[1] = u2.y;
-                }
-                const float4 v4 = *reinterpret_cast<const float4 *>(&sv[cc][cl * 4]);
+                const int k = S.sk[cc];
+                const float2 u2 = *reinterpret_cast<const float2 *>(P.Uc + (size_t)S.sslot[cc] * P.mp + sb);
+                const float u[2] = {u2.x, u2.y};
+                const float4 v4 = *reinterpret_cast<const float4 *>(&S.sv[cc][cl * 4]);
                 const float v[4] = {v4.x, v4.y, v4.z, v4.w};
                 float t[2][4];
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u[i] + v[jj]);
+                    for (int jj = 0; jj < 4; ++jj)
+                        t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u[i] + v[jj]) - t0[i][jj];
                 sum[cc] += ((t[0][0] + t[0][1]) + (t[0][2] + t[0][3])) + ((t[1][0] + t[1][1]) + (t[1][2] + t[1][3]));
             }
         }
     }
     const float w = reduce_scatter32<false>(sum, lane);
-    red[warp][lane] = w;
+    S.red[warp][lane] = w;
     __syncthreads();
     if (tid < nv) {
         double x = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x += (double)red[q][tid];
-        P.part_urf[(size_t)blockIdx.x * STMF_WMAX + sslot[tid]] = x;
+        for (int q = 0; q < 8; ++q) x += (double)S.red[q][tid];
+        P.part_urf[(size_t)b * STMF_WMAX + S.sslot[tid]] = x;
     }
 }
 
-// Sums the block partials of every candidate (fixed order), picks the kept
-// candidate and commits it.  mode 0: first candidate (in the paper's order)
-// with f' < f;  mode 1: the smallest f' < f of the window (ties: first);
-// mode 2 (null): store the current error of both summation trees.
-__global__ void __launch_bounds__(256) k_select(stmf_problem P, int mode, int nb_ulf, int nb_urf)
+// One launch evaluates the whole window: blocks [0, nb_ulf) run F-ULF rows,
+// the rest F-URF column strips, side by side.
+__global__ void __launch_bounds__(256, 2) k_eval(stmf_problem P, int nb_ulf)
+{
+    __shared__ EvalSmem S;
+    if ((int)blockIdx.x < nb_ulf) eval_ulf_block(P, S, blockIdx.x);
+    else eval_urf_block(P, S, blockIdx.x - nb_ulf);
+}
+
+__device__ __forceinline__ void put_trace(stmf_ctl *ctl, int pos, int j, int k, int type, double f)
+{
+    if (!ctl->trace || ctl->ntrace >= ctl->trace_cap) return;
+    int32_t *rec = ctl->trace + STMF_TRACE_INTS * ctl->ntrace;
+    rec[0] = ctl->sweep; rec[1] = ctl->i; rec[2] = pos; rec[3] = j; rec[4] = k; rec[5] = type;
+    const long long bits = __double_as_longlong(f);
+    rec[6] = (int32_t)(bits & 0xffffffffll);
+    rec[7] = (int32_t)(bits >> 32);
+    ctl->ntrace += 1;
+}
+
+// End of a window: sums the block partials of every candidate (fixed order)
+// into its change Delta = f' - f, keeps the first candidate in the paper's
+// order with Delta < 0 (select_mode 1: the smallest), commits it, writes the
+// trace record and advances the row.  In a graph it also sets the
+// conditions of the row loop: h_win (another window of this row), h_dirty
+// (refresh before the next row), h_row (another row in this sweep).
+__global__ void __launch_bounds__(256) k_select(stmf_problem P, int nb_ulf, int nb_urf, int in_graph, int single,
+                                                cudaGraphConditionalHandle h_row,
+                                                cudaGraphConditionalHandle h_dirty,
+                                                cudaGraphConditionalHandle h_win)
 {
     __shared__ double sf[STMF_WMAX];
     __shared__ int skept;
     stmf_ctl *ctl = P.ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nc = mode == 2 ? 2 : ctl->nc;
+    const int nc = ctl->nc;
     for (int c = warp; c < nc; c += 8) {
-        const int type = mode == 2 ? c : P.cand[8 * c + 2];
+        const int type = P.cand[8 * c + 2];
         const double *part = type == 0 ? P.part_ulf : P.part_urf;
         const int nb = type == 0 ? nb_ulf : nb_urf;
         double x = 0.0;
         for (int b = lane; b < nb; b += 32) x += part[(size_t)b * STMF_WMAX + c];
 #pragma unroll
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-        if (lane == 0) { sf[c] = x; P.fc[c] = x; }
+        if (lane == 0) { sf[c] = x; P.fc[c] = ctl->f + x; }
     }
     __syncthreads();
-    if (mode == 2) {
-        if (tid == 0) { ctl->f_ulf = sf[0]; ctl->f_urf = sf[1]; }
-        return;
-    }
     if (tid == 0) {
         int kept = -1;
         for (int c = 0; c < nc; ++c) {
-            const double fref = P.cand[8 * c + 2] == 0 ? ctl->f_ulf : ctl->f_urf;
-            if (sf[c] < fref) {
-                if (mode == 0) { kept = c; break; }
+            if (sf[c] < 0.0) {
+                if (ctl->select_mode == 0) { kept = c; break; }
                 if (kept < 0 || sf[c] < sf[kept]) kept = c;
             }
         }
         skept = kept;
         ctl->issued += nc;
-        ctl->tried += mode == 0 ? (kept >= 0 ? kept + 1 : nc) : nc;
+        ctl->windows += 1;
+        ctl->tried += (ctl->select_mode == 0 && kept >= 0) ? kept + 1 : nc;
         ctl->ncand_row += nc;
+        ctl->kept = kept >= 0;
         if (kept >= 0) {
             const int *cd = P.cand + 8 * kept;
-            ctl->kept = 1;
             ctl->kept_c = kept;
             ctl->kept_j = cd[0]; ctl->kept_k = cd[1]; ctl->kept_type = cd[2]; ctl->kept_pos = cd[3];
-            ctl->f_new = sf[kept];
-            ctl->row_done = 1;
-        } else {
-            ctl->kept = 0;
-            ctl->row_done = ctl->exhausted;
-            ctl->wj = min(ctl->wj * 2, STMF_WMAX / 2);
+            ctl->f_new = ctl->f + sf[kept];
+        }
+        if (!single) {
+            if (kept >= 0) {
+                const int *cd = P.cand + 8 * kept;
+                ctl->f = ctl->f_new;          // exact value recomputed by the refresh
+                ctl->dirty_k = cd[1];
+                ctl->accepted += 1;
+                put_trace(ctl, cd[3], cd[0], cd[1], cd[2], ctl->f_new);
+                ctl->row_done = 1;
+            } else if (ctl->exhausted) {
+                put_trace(ctl, -1, -1, -1, -1, ctl->f);
+                ctl->row_done = 1;
+            } else {
+                ctl->wj = min(ctl->wj * 2, ctl->wmax / 2);
+                ctl->row_done = 0;
+            }
+            if (ctl->row_done) ctl->i += 1;
+            if (in_graph) {
+                cudaGraphSetConditional(h_win, ctl->row_done ? 0u : 1u);
+                if (ctl->row_done) {
+                    cudaGraphSetConditional(h_dirty, kept >= 0 ? 1u : 0u);
+                    cudaGraphSetConditional(h_row, ctl->i < ctl->m ? 1u : 0u);
+                }
+            }
         }
     }
     __syncthreads();
@@ -605,6 +687,32 @@ __global__ void __launch_bounds__(256) k_select(stmf_problem P, int mode, int nb
         const int k = P.cand[8 * kept + 1];
         for (int s = tid; s < P.m; s += 256) P.U[(size_t)s * P.r + k] = P.Uc[(size_t)kept * P.mp + s];
         for (int t = tid; t < P.n; t += 256) P.V[(size_t)k * P.np + t] = P.Vc[(size_t)kept * P.np + t];
+    }
+}
+
+// Start of a row: row state reset; in a graph, opens the window loop.
+__global__ void k_row_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_win)
+{
+    stmf_ctl *ctl = P.ctl;
+    ctl->row_start = 1;
+    ctl->pos = 0;
+    ctl->ncand_row = 0;
+    ctl->wj = ctl->wj0;
+    ctl->kept = 0;
+    ctl->row_done = 0;
+    if (in_graph) cudaGraphSetConditional(h_win, 1u);
+}
+
+// Start of a sweep: row 0; in a graph, opens the row loop and asks for a
+// refresh if a previous update left the planes stale.
+__global__ void k_sweep_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_row,
+                              cudaGraphConditionalHandle h_dirty)
+{
+    stmf_ctl *ctl = P.ctl;
+    ctl->i = 0;
+    if (in_graph) {
+        cudaGraphSetConditional(h_row, ctl->m > 0 ? 1u : 0u);
+        cudaGraphSetConditional(h_dirty, ctl->dirty_k != -2 ? 1u : 0u);
     }
 }
 
@@ -622,6 +730,7 @@ __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
     ctl->vlist[0] = 0;
     ctl->exhausted = 1;
     ctl->ncand_row = 0;
+    ctl->select_mode = 0;
 }
 
 // Unconditional commit of slot 0 (commit_if_decreases = 0).
@@ -634,16 +743,6 @@ __global__ void k_commit0(stmf_problem P)
     if (threadIdx.x == 0) {
         ctl->kept = 1; ctl->kept_c = 0; ctl->kept_k = k; ctl->f_new = P.fc[0];
     }
-}
-
-__global__ void k_begin_row(stmf_ctl *ctl, int i, int wj0)
-{
-    ctl->i = i;
-    ctl->row_start = 1;
-    ctl->wj = wj0;
-    ctl->kept = 0;
-    ctl->row_done = 0;
-    ctl->kept_pos = -1;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -687,13 +786,6 @@ cudaError_t launch_transpose(cudaStream_t st, const float *X, int ldx, int rows,
     return cudaGetLastError();
 }
 
-cudaError_t launch_rowstat(cudaStream_t st, const float *X, int ldx, int rows, int cols, const float *y,
-                           int ystride, float *min1, float *min2, int *arg)
-{
-    k_rowstat<<<(rows * 32 + 255) / 256, 256, 0, st>>>(X, ldx, rows, cols, y, ystride, min1, min2, arg);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_acol(cudaStream_t st, const float *R, int ld, int m, int n, int r, const int *picks, int p,
                         float *U)
 {
@@ -708,15 +800,16 @@ cudaError_t launch_copy_rows(cudaStream_t st, const float *src, int lds, float *
     return cudaGetLastError();
 }
 
-cudaError_t launch_begin_row(cudaStream_t st, stmf_problem *P, int i, int wj0)
+cudaError_t launch_stats(cudaStream_t st, stmf_problem *P)
 {
-    k_begin_row<<<1, 1, 0, st>>>(P->ctl, i, wj0);
+    const long long threads = (long long)(P->n + P->m) * 32;
+    k_stats<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(*P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_window(cudaStream_t st, stmf_problem *P)
 {
-    k_window<<<1, 256, 0, st>>>(*P, P->window);
+    k_window<<<1, 256, 0, st>>>(*P);
     return cudaGetLastError();
 }
 
@@ -727,18 +820,18 @@ cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots)
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int null_mode)
+static inline int nb_ulf(const stmf_problem *P) { return (P->m + 3) / 4; }
+static inline int nb_urf(const stmf_problem *P) { return (P->n + 31) / 32; }
+
+cudaError_t launch_eval(cudaStream_t st, stmf_problem *P)
 {
-    k_eval_ulf<<<(P->m + 3) / 4, 256, 0, st>>>(*P, null_mode);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_eval_urf<<<(P->n + 31) / 32, 256, 0, st>>>(*P, null_mode);
+    k_eval<<<nb_ulf(P) + nb_urf(P), 256, 0, st>>>(*P, nb_ulf(P));
     return cudaGetLastError();
 }
 
-cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int mode)
+cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single)
 {
-    k_select<<<1, 256, 0, st>>>(*P, mode, (P->m + 3) / 4, (P->n + 31) / 32);
+    k_select<<<1, 256, 0, st>>>(*P, nb_ulf(P), nb_urf(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
     return cudaGetLastError();
 }
 
@@ -751,5 +844,17 @@ cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k,
 cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P)
 {
     k_commit0<<<1, 256, 0, st>>>(*P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph)
+{
+    k_row_begin<<<1, 1, 0, st>>>(*P, in_graph, P->h_win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_begin(cudaStream_t st, stmf_problem *P, int in_graph)
+{
+    k_sweep_begin<<<1, 1, 0, st>>>(*P, in_graph, P->h_row, P->h_dirty);
     return cudaGetLastError();
 }

@@ -70,13 +70,12 @@ stmf_status fail(stmf_ctx *ctx, stmf_status st, const char *fmt, ...)
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);    \
     } while (0)
 
-bool is_device_ptr(const void *p)
-{
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+#define CK2(c, call)                                                                              \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(c, STMF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));               \
+    } while (0)
 
 template <class T>
 cudaError_t dalloc(T **p, size_t count)
@@ -87,14 +86,23 @@ cudaError_t dalloc(T **p, size_t count)
 void problem_free(stmf_problem *P)
 {
     if (!P) return;
+    if (P->sweep_exec) cudaGraphExecDestroy(P->sweep_exec);
+    if (P->sweep_graph) cudaGraphDestroy(P->sweep_graph);
     void *ptrs[] = {P->R, P->RT, P->U, P->V, P->P1, P->P2, P->A, P->cmin1, P->cmin2, P->carg,
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
-                    P->rowhist, P->order, P->cand, P->Uc, P->Vc, P->part_ulf, P->part_urf, P->fc,
-                    P->ctl};
+                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part_ulf, P->part_urf, P->fc,
+                    P->ctl, P->trace_dev, P->perm};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
     delete P;
+}
+
+template <class T>
+cudaError_t set_ctl(stmf_problem *P, T stmf_ctl::*field, T value)
+{
+    // pageable source: the copy has consumed `value` when the call returns
+    return cudaMemcpyAsync(&(P->ctl->*field), &value, sizeof(T), cudaMemcpyHostToDevice, P->ctx->stream);
 }
 
 stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_problem **out)
@@ -105,8 +113,6 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     P->m = m; P->n = n; P->r = r;
     P->mp = stmf_roundup(m, STMF_PAD);
     P->np = stmf_roundup(n, STMF_PAD);
-    P->window = window;
-    P->dirty_k = -1;
     const size_t mp = P->mp, np = P->np;
     const int nparts = planes_nparts(m);
     cudaError_t e = cudaSuccess;
@@ -118,7 +124,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     A(dalloc(&P->rmin1, (size_t)r * mp)); A(dalloc(&P->rmin2, (size_t)r * mp)); A(dalloc(&P->rarg, (size_t)r * mp));
     A(dalloc(&P->tdpart, (size_t)nparts * np)); A(dalloc(&P->chpart, (size_t)nparts * np * r));
     A(dalloc(&P->tdcol, np)); A(dalloc(&P->colhist, np * r)); A(dalloc(&P->rowhist, STMF_MAX_RANK));
-    A(dalloc(&P->order, np)); A(dalloc(&P->cand, 8 * STMF_WMAX));
+    A(dalloc(&P->rank, np)); A(dalloc(&P->order, np)); A(dalloc(&P->cand, 8 * STMF_WMAX));
     A(dalloc(&P->Uc, (size_t)STMF_WMAX * mp)); A(dalloc(&P->Vc, (size_t)STMF_WMAX * np));
     A(dalloc(&P->part_ulf, (mp / 4) * STMF_WMAX)); A(dalloc(&P->part_urf, (np / 32) * STMF_WMAX));
     A(dalloc(&P->fc, STMF_WMAX)); A(dalloc(&P->ctl, 1));
@@ -130,55 +136,34 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
                     cudaGetErrorString(e));
     }
     cudaStream_t st = ctx->stream;
+    stmf_ctl c;
+    memset(&c, 0, sizeof(c));
+    c.m = m;
+    c.wj0 = 2;
+    c.wmax = window;
+    c.dirty_k = -1;
     e = cudaMemsetAsync(P->U, 0, sizeof(float) * mp * r, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->V, 0, sizeof(float) * r * np, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P->ctl, 0, sizeof(stmf_ctl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P1, 0, sizeof(float) * mp * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P2, 0, sizeof(float) * mp * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->A, 0, mp * np, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "memset: %s", cudaGetErrorString(e)); }
     *out = P;
     return STMF_OK;
 }
 
-// Statistics of component k (or of all components when k < 0):
-//   column statistics from U_.k over RT, row statistics from V_k. over R.
-stmf_status refresh_stats(stmf_problem *P, int k)
+// Statistics of the component named by ctl->dirty_k, then planes, td_col,
+// colhist, column order and f (which marks the planes current).
+stmf_status refresh(stmf_problem *P)
 {
     stmf_ctx *ctx = P->ctx;
-    cudaStream_t st = ctx->stream;
-    const int k0 = k < 0 ? 0 : k, k1 = k < 0 ? P->r : k + 1;
-    for (int l = k0; l < k1; ++l) {
-        CK(launch_rowstat(st, P->RT, P->mp, P->n, P->m, P->U + l, P->r, P->cmin1 + (size_t)l * P->np,
-                          P->cmin2 + (size_t)l * P->np, P->carg + (size_t)l * P->np));
-        CK(launch_rowstat(st, P->R, P->np, P->m, P->n, P->V + (size_t)l * P->np, 1, P->rmin1 + (size_t)l * P->mp,
-                          P->rmin2 + (size_t)l * P->mp, P->rarg + (size_t)l * P->mp));
-    }
+    CK(launch_stats(ctx->stream, P));
+    CK(launch_refresh_planes(ctx->stream, P));
     return STMF_OK;
 }
 
-// Product planes, td_col, colhist, the column order and the current error.
-stmf_status refresh_planes(stmf_problem *P)
-{
-    stmf_ctx *ctx = P->ctx;
-    cudaStream_t st = ctx->stream;
-    CK(launch_planes(st, P, P->chpart));
-    CK(launch_td_finalize2(st, P->tdpart, P->chpart, planes_nparts(P->m), P->np, P->n, P->r, P->tdcol, P->colhist));
-    CK(launch_order(st, P->tdcol, P->n, P->order));
-    CK(launch_eval(st, P, 1));
-    CK(launch_select(st, P, 2));
-    P->refreshes++;
-    return STMF_OK;
-}
-
-stmf_status refresh(stmf_problem *P, int k)
-{
-    stmf_status s = refresh_stats(P, k);
-    if (s != STMF_OK) return s;
-    return refresh_planes(P);
-}
-
-// After R (and RT) are packed: checks, U, V, statistics, planes, error.
+// After R is packed: checks, RT, U, V = (-U)^T (x)* R, statistics, planes, f.
 stmf_status problem_init(stmf_problem *P, const float *U0, int acol_p, uint64_t seed, const int32_t *picks_in)
 {
     stmf_ctx *ctx = P->ctx;
@@ -214,16 +199,13 @@ stmf_status problem_init(stmf_problem *P, const float *U0, int acol_p, uint64_t 
         CK(cudaStreamSynchronize(st));
         cudaFree(d_picks);
     }
-    // V = (-U)^T (x)* R: the column minima of component l are min1 of its
+    // V = (-U)^T (x)* R: the column minima of component l are the min1 of its
     // column statistics.
-    stmf_status s = refresh_stats(P, -1);
-    if (s != STMF_OK) return s;
+    CK(set_ctl(P, &stmf_ctl::dirty_k, -1));
+    CK(launch_stats(st, P));
     CK(launch_copy_rows(st, P->cmin1, P->np, P->V, P->np, P->r, P->n));
-    s = refresh_stats(P, -1);   // row statistics of the new V
+    stmf_status s = refresh(P);        // row statistics of the new V, planes, f
     if (s != STMF_OK) return s;
-    s = refresh_planes(P);
-    if (s != STMF_OK) return s;
-    P->dirty_k = -2;
     return STMF_OK;
 }
 
@@ -254,39 +236,283 @@ stmf_status update(stmf_problem *P, int i, int j, int k, int type, int commit_if
         return fail(ctx, STMF_ERR_INVALID, "index out of range (i=%d, j=%d, k=%d)", i, j, k);
     float rij;
     CK(cudaSetDevice(ctx->device));
-    CK(cudaMemcpyAsync(&rij, P->R + (size_t)i * P->np + j, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (rij != rij) return fail(ctx, STMF_ERR_INVALID, "R[%d][%d] is not given", i, j);
     cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(&rij, P->R + (size_t)i * P->np + j, sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (rij != rij) return fail(ctx, STMF_ERR_INVALID, "R[%d][%d] is not given", i, j);
     CK(launch_single(st, P, i, j, k, type));
     CK(launch_seed(st, P, 1));
-    CK(launch_eval(st, P, 0));
-    CK(launch_select(st, P, 0));
+    CK(launch_eval(st, P));
+    CK(launch_select(st, P, 0, 1));
     if (!commit_if_decreases) CK(launch_commit0(st, P));
     stmf_status s = read_ctl(P);
     if (s != STMF_OK) return s;
     const int kept = P->ctl_host->kept;
-    const double fn = commit_if_decreases ? P->ctl_host->f_new : 0.0;
     double fval;
     CK(cudaMemcpyAsync(&fval, P->fc, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    (void)fn;
     if (f_new) *f_new = fval;
     if (accepted) *accepted = kept;
     if (kept) {
-        s = refresh(P, k);
+        CK(set_ctl(P, &stmf_ctl::dirty_k, k));
+        s = refresh(P);
         if (s != STMF_OK) return s;
     }
     return STMF_OK;
 }
 
-void put_trace(const stmf_options *o, int64_t &nrec, int sweep, int i, int pos, int j, int k, int type, double f)
+// The sweep as one graph: sweep_begin, then
+//   while (h_row) {
+//     if (h_dirty) { stats(k), planes, td_col/colhist, rank, order + f }
+//     row_begin
+//     while (h_win) { window, seed, eval, select }
+//   }
+stmf_status build_sweep_graph(stmf_problem *P)
 {
-    if (!o || !o->trace || nrec >= o->trace_cap) return;
-    int32_t *rec = o->trace + STMF_TRACE_INTS * nrec;
-    rec[0] = sweep; rec[1] = i; rec[2] = pos; rec[3] = j; rec[4] = k; rec[5] = type;
-    memcpy(rec + 6, &f, sizeof(double));
-    ++nrec;
+    stmf_ctx *ctx = P->ctx;
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{cap};
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    P->sweep_graph = g;
+    cudaGraphConditionalHandle hr, hd, hw;
+    CK(cudaGraphConditionalHandleCreate(&hr, g, 0, 0));
+    CK(cudaGraphConditionalHandleCreate(&hd, g, 0, 0));
+    CK(cudaGraphConditionalHandleCreate(&hw, g, 0, 0));
+    P->h_row = hr; P->h_dirty = hd; P->h_win = hw;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+
+    cudaGraph_t tmp;
+    CK(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, mode));
+    CK(launch_sweep_begin(cap, P, 1));
+    CK(cudaStreamEndCapture(cap, &tmp));
+    cudaGraphNode_t sb;
+    size_t count = 1;
+    CK(cudaGraphGetNodes(g, &sb, &count));
+
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hr;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wrow;
+    CK(cudaGraphAddNode(&wrow, g, &sb, nullptr, 1, &wp));
+    cudaGraph_t body_row = wp.conditional.phGraph_out[0];
+
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hd;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t nif;
+    CK(cudaGraphAddNode(&nif, body_row, nullptr, nullptr, 0, &ip));
+    cudaGraph_t body_ref = ip.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(cap, body_ref, nullptr, nullptr, 0, mode));
+    CK(launch_stats(cap, P));
+    CK(launch_refresh_planes(cap, P));
+    CK(cudaStreamEndCapture(cap, &tmp));
+
+    CK(cudaStreamBeginCaptureToGraph(cap, body_row, &nif, nullptr, 1, mode));
+    CK(launch_row_begin(cap, P, 1));
+    CK(cudaStreamEndCapture(cap, &tmp));
+    cudaGraphNode_t nodes[4];
+    count = 4;
+    CK(cudaGraphGetNodes(body_row, nodes, &count));
+    cudaGraphNode_t rb = nullptr;
+    for (size_t q = 0; q < count; ++q) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nodes[q], &t));
+        if (t == cudaGraphNodeTypeKernel) rb = nodes[q];
+    }
+    if (!rb) return fail(ctx, STMF_ERR_INTERNAL, "row-begin node not found in the sweep graph");
+
+    cudaGraphNodeParams wp2 = {};
+    wp2.type = cudaGraphNodeTypeConditional;
+    wp2.conditional.handle = hw;
+    wp2.conditional.type = cudaGraphCondTypeWhile;
+    wp2.conditional.size = 1;
+    cudaGraphNode_t wwin;
+    CK(cudaGraphAddNode(&wwin, body_row, &rb, nullptr, 1, &wp2));
+    cudaGraph_t body_win = wp2.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(cap, body_win, nullptr, nullptr, 0, mode));
+    CK(launch_window(cap, P));
+    CK(launch_seed(cap, P, P->ctl_host->wmax));
+    CK(launch_eval(cap, P));
+    CK(launch_select(cap, P, 1, 0));
+    CK(cudaStreamEndCapture(cap, &tmp));
+
+    CK(cudaGraphInstantiate(&P->sweep_exec, g, 0));
+    return STMF_OK;
+}
+
+bool use_graph()
+{
+    const char *e = getenv("STMF_NO_GRAPH");
+    return !(e && e[0] == '1');
+}
+
+// One sweep driven from the host (one synchronisation per window); used when
+// graphs are disabled.
+stmf_status sweep_host(stmf_problem *P)
+{
+    stmf_ctx *ctx = P->ctx;
+    cudaStream_t st = ctx->stream;
+    CK(launch_sweep_begin(st, P, 0));
+    stmf_status s = read_ctl(P);
+    if (s != STMF_OK) return s;
+    for (int i = 0; i < P->m; ++i) {
+        if (P->ctl_host->dirty_k != -2) {
+            s = refresh(P);
+            if (s != STMF_OK) return s;
+        }
+        CK(launch_row_begin(st, P, 0));
+        while (true) {
+            CK(launch_window(st, P));
+            CK(launch_seed(st, P, P->ctl_host->wmax));
+            CK(launch_eval(st, P));
+            CK(launch_select(st, P, 0, 0));
+            s = read_ctl(P);
+            if (s != STMF_OK) return s;
+            if (P->ctl_host->row_done) break;
+        }
+    }
+    return STMF_OK;
+}
+
+// Algorithm 3 preparation: orientation, permutation, packing, init.
+stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, int ldr, const uint32_t *mask,
+                         int ldm_words, const stmf_options *opts, stmf_problem **out)
+{
+    *out = nullptr;
+    stmf_status s = check_common(ctx, m0, n0, r);
+    if (s != STMF_OK) return s;
+    if (!R) return fail(ctx, STMF_ERR_INVALID, "R is required");
+    if (ldr < n0) return fail(ctx, STMF_ERR_INVALID, "ldr < n");
+    if (mask && ldm_words < (n0 + 31) / 32) return fail(ctx, STMF_ERR_INVALID, "ldm_words < ceil(n/32)");
+    stmf_options o;
+    if (opts) o = *opts; else stmf_default_options(&o);
+    if (o.window < 0 || o.window > STMF_WMAX) return fail(ctx, STMF_ERR_INVALID, "window outside [0, %d]", STMF_WMAX);
+    if (o.precision != 0) return fail(ctx, STMF_ERR_INVALID, "precision mode %d is not available", o.precision);
+    if (o.select < 0 || o.select > 1) return fail(ctx, STMF_ERR_INVALID, "select mode %d unknown", o.select);
+    const int tr = m0 > n0;                 // Algorithm 3: a tall R is transposed
+    const int m = tr ? n0 : m0, n = tr ? m0 : n0;
+    std::vector<int> perm;
+    if (o.perm) {
+        perm.assign(o.perm, o.perm + m);
+        std::vector<char> seen(m, 0);
+        for (int x : perm) {
+            if (x < 0 || x >= m || seen[x]) return fail(ctx, STMF_ERR_INVALID, "perm is not a permutation of 0..%d", m - 1);
+            seen[x] = 1;
+        }
+    } else {
+        random_permutation(m, o.seed, perm);
+    }
+    const int window = o.window ? (o.window + 1) / 2 * 2 : STMF_WMAX;
+    stmf_problem *P = nullptr;
+    s = problem_alloc(ctx, m, n, r, window, &P);
+    if (s != STMF_OK) return s;
+    P->transposed = tr; P->m0 = m0; P->n0 = n0;
+    cudaStream_t st = ctx->stream;
+    int *d_bad = nullptr;
+    cudaError_t e = cudaMalloc(&P->perm, sizeof(int) * m);
+    if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->perm, perm.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, tr, P->perm, P->R, P->np, P->mp, d_bad);
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d_bad) cudaFree(d_bad);
+    if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "pack: %s", cudaGetErrorString(e)); }
+    if (bad) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite"); }
+    s = problem_init(P, o.U0, o.acol_p, o.seed, o.picks);
+    if (s != STMF_OK) { problem_free(P); return s; }
+    e = cudaSuccess;
+    if (o.trace && o.trace_cap > 0) {
+        e = cudaMalloc(&P->trace_dev, sizeof(int32_t) * STMF_TRACE_INTS * (size_t)o.trace_cap);
+        if (e == cudaSuccess) e = set_ctl(P, &stmf_ctl::trace, P->trace_dev);
+        if (e == cudaSuccess) e = set_ctl(P, &stmf_ctl::trace_cap, (long long)o.trace_cap);
+    }
+    if (e == cudaSuccess) e = set_ctl(P, &stmf_ctl::select_mode, o.select);
+    if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "trace buffer: %s", cudaGetErrorString(e)); }
+    s = read_ctl(P);
+    if (s != STMF_OK) { problem_free(P); return s; }
+    P->f_init = P->ctl_host->f;
+    *out = P;
+    return STMF_OK;
+}
+
+stmf_status fastmf_run(stmf_problem *P, int sweeps, double eps)
+{
+    stmf_ctx *ctx = P->ctx;
+    cudaStream_t st = ctx->stream;
+    const bool graph = use_graph();
+    if (graph && !P->sweep_exec) {
+        stmf_status s = build_sweep_graph(P);
+        if (s != STMF_OK) return s;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    for (int sw = 0; sw < sweeps; ++sw) {
+        const double f_prev = P->ctl_host->f;
+        CK(set_ctl(P, &stmf_ctl::sweep, P->sweeps_done));
+        if (graph) {
+            CK(cudaGraphLaunch(P->sweep_exec, st));
+        } else {
+            stmf_status s = sweep_host(P);
+            if (s != STMF_OK) return s;
+        }
+        stmf_status s = read_ctl(P);
+        if (s != STMF_OK) return s;
+        if (P->ctl_host->err) return fail(ctx, STMF_ERR_INTERNAL, "device error %d", P->ctl_host->err);
+        P->sweeps_done += 1;
+        const double f = P->ctl_host->f;
+        if (eps > 0.0 && f_prev - f < eps && f - f_prev < eps) break;
+    }
+    if (P->ctl_host->dirty_k != -2) {
+        stmf_status s = refresh(P);
+        if (s != STMF_OK) return s;
+        s = read_ctl(P);
+        if (s != STMF_OK) return s;
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    P->seconds += std::chrono::duration<double>(t1 - t0).count();
+    return STMF_OK;
+}
+
+void fill_report(const stmf_problem *P, stmf_report *rep)
+{
+    if (!rep) return;
+    memset(rep, 0, sizeof(*rep));
+    const stmf_ctl &c = *P->ctl_host;
+    rep->f_init = P->f_init;
+    rep->f_final = c.f;
+    rep->sweeps_done = P->sweeps_done;
+    rep->transposed = P->transposed;
+    rep->candidates_tried = c.tried;
+    rep->candidates_issued = c.issued;
+    rep->accepted = c.accepted;
+    rep->refreshes = c.refreshes;
+    rep->windows = c.windows;
+    rep->trace_records = c.ntrace;
+    rep->seconds = P->seconds;
+}
+
+stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *trace_out, int64_t trace_cap)
+{
+    stmf_ctx *ctx = P->ctx;
+    cudaStream_t st = ctx->stream;
+    if (U_out && V_out) CK(launch_unorient(st, P, P->transposed, P->perm, U_out, V_out));
+    stmf_status s = read_ctl(P);
+    if (s != STMF_OK) return s;
+    if (trace_out && P->trace_dev) {
+        const long long nrec = P->ctl_host->ntrace < trace_cap ? P->ctl_host->ntrace : trace_cap;
+        if (nrec > 0)
+            CK(cudaMemcpyAsync(trace_out, P->trace_dev, sizeof(int32_t) * STMF_TRACE_INTS * nrec,
+                               cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return STMF_OK;
 }
 
 }  // namespace
@@ -415,6 +641,9 @@ stmf_status stmf_problem_create(stmf_ctx *ctx, int m, int n, int r, const float 
     if (bad) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite"); }
     s = problem_init(P, U0, o.acol_p, o.seed, o.picks);
     if (s != STMF_OK) { problem_free(P); return s; }
+    s = read_ctl(P);
+    if (s != STMF_OK) { problem_free(P); return s; }
+    P->f_init = P->ctl_host->f;
     *out = P;
     return STMF_OK;
 }
@@ -443,123 +672,51 @@ stmf_status stmf_problem_get(stmf_problem *P, float *U, float *V, double *f)
     if (f) {
         stmf_status s = read_ctl(P);
         if (s != STMF_OK) return s;
-        *f = P->ctl_host->f_ulf;
+        *f = P->ctl_host->f;
     }
     return STMF_OK;
+}
+
+stmf_status stmf_factorize_begin(stmf_ctx *ctx, int m, int n, int r, const float *R, int ldr, const uint32_t *mask,
+                                 int ldm_words, const stmf_options *opts, stmf_problem **out)
+{
+    if (!out) return fail(ctx, STMF_ERR_INVALID, "out is NULL");
+    return fastmf_begin(ctx, m, n, r, R, ldr, mask, ldm_words, opts, out);
+}
+
+stmf_status stmf_factorize_run(stmf_problem *P, int sweeps, double eps, stmf_report *report)
+{
+    if (!P) return STMF_ERR_INVALID;
+    if (sweeps < 0) return fail(P->ctx, STMF_ERR_INVALID, "sweeps < 0");
+    CK2(P->ctx, cudaSetDevice(P->ctx->device));
+    stmf_status s = fastmf_run(P, sweeps, eps);
+    if (s != STMF_OK) return s;
+    fill_report(P, report);
+    return STMF_OK;
+}
+
+stmf_status stmf_factorize_end(stmf_problem *P, float *U_out, float *V_out, int32_t *trace, int64_t trace_cap)
+{
+    if (!P) return STMF_ERR_INVALID;
+    CK2(P->ctx, cudaSetDevice(P->ctx->device));
+    return fastmf_end(P, U_out, V_out, trace, trace_cap);
 }
 
 stmf_status stmf_factorize(stmf_ctx *ctx, int m0, int n0, int r, const float *R, int ldr, const uint32_t *mask,
                            int ldm_words, const stmf_options *opts, float *U_out, float *V_out, stmf_report *rep)
 {
-    stmf_status s = check_common(ctx, m0, n0, r);
-    if (s != STMF_OK) return s;
-    if (!R || !U_out || !V_out) return fail(ctx, STMF_ERR_INVALID, "R, U_out and V_out are required");
-    if (ldr < n0) return fail(ctx, STMF_ERR_INVALID, "ldr < n");
-    if (mask && ldm_words < (n0 + 31) / 32) return fail(ctx, STMF_ERR_INVALID, "ldm_words < ceil(n/32)");
+    if (!U_out || !V_out) return fail(ctx, STMF_ERR_INVALID, "U_out and V_out are required");
     stmf_options o;
     if (opts) o = *opts; else stmf_default_options(&o);
     if (o.sweeps < 0) return fail(ctx, STMF_ERR_INVALID, "sweeps < 0");
-    if (o.window < 0 || o.window > STMF_WMAX) return fail(ctx, STMF_ERR_INVALID, "window outside [0, %d]", STMF_WMAX);
-    if (o.precision != 0) return fail(ctx, STMF_ERR_INVALID, "precision mode %d is not available", o.precision);
-    const int tr = m0 > n0;                 // Algorithm 3: a tall R is transposed
-    const int m = tr ? n0 : m0, n = tr ? m0 : n0;
-    std::vector<int> perm;
-    if (o.perm) {
-        perm.assign(o.perm, o.perm + m);
-        std::vector<char> seen(m, 0);
-        for (int x : perm) {
-            if (x < 0 || x >= m || seen[x]) return fail(ctx, STMF_ERR_INVALID, "perm is not a permutation of 0..%d", m - 1);
-            seen[x] = 1;
-        }
-    } else {
-        random_permutation(m, o.seed, perm);
-    }
-    const int window = o.window ? (o.window + 1) / 2 * 2 : STMF_WMAX;
     stmf_problem *P = nullptr;
-    s = problem_alloc(ctx, m, n, r, window, &P);
+    stmf_status s = fastmf_begin(ctx, m0, n0, r, R, ldr, mask, ldm_words, &o, &P);
     if (s != STMF_OK) return s;
-    struct Guard { stmf_problem *P; ~Guard() { problem_free(P); } } guard{P};
-    cudaStream_t st = ctx->stream;
-    int *d_perm = nullptr, *d_bad = nullptr;
-    CK(cudaMalloc(&d_perm, sizeof(int) * m));
-    struct Guard2 { int *a; ~Guard2() { if (a) cudaFree(a); } } g2{d_perm};
-    CK(cudaMalloc(&d_bad, sizeof(int)));
-    struct Guard3 { int *a; ~Guard3() { if (a) cudaFree(a); } } g3{d_bad};
-    CK(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
-    CK(launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, tr, d_perm, P->R, P->np, P->mp, d_bad));
-    int bad = 0;
-    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (bad) return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite");
-    s = problem_init(P, o.U0, o.acol_p, o.seed, o.picks);
-    if (s != STMF_OK) return s;
-
-    s = read_ctl(P);
-    if (s != STMF_OK) return s;
-    const double f_init = P->ctl_host->f_ulf;
-    double f = f_init;
-    int64_t nrec = 0;
-    int sweeps_done = 0;
-    long long accepted = 0;
-    const int wj0 = 2;
-    auto t0 = std::chrono::steady_clock::now();
-    for (int sw = 0; sw < o.sweeps; ++sw) {
-        const double f_prev = f;
-        for (int i = 0; i < m; ++i) {
-            if (P->dirty_k != -2) {
-                s = refresh(P, P->dirty_k);
-                if (s != STMF_OK) return s;
-                P->dirty_k = -2;
-            }
-            CK(launch_begin_row(st, P, i, wj0));
-            while (true) {
-                CK(launch_window(st, P));
-                CK(launch_seed(st, P, P->window));
-                CK(launch_eval(st, P, 0));
-                CK(launch_select(st, P, o.select == 1 ? 1 : 0));
-                s = read_ctl(P);
-                if (s != STMF_OK) return s;
-                const stmf_ctl &c = *P->ctl_host;
-                if (c.kept) {
-                    f = c.f_new;
-                    P->dirty_k = c.kept_k;
-                    ++accepted;
-                    put_trace(&o, nrec, sw, i, c.kept_pos, c.kept_j, c.kept_k, c.kept_type, f);
-                    break;
-                }
-                if (c.row_done) {
-                    put_trace(&o, nrec, sw, i, -1, -1, -1, -1, f);
-                    break;
-                }
-            }
-        }
-        ++sweeps_done;
-        if (o.eps > 0.0 && (f_prev - f < o.eps && f - f_prev < o.eps)) break;
-    }
-    if (P->dirty_k != -2) {
-        s = refresh(P, P->dirty_k);
-        if (s != STMF_OK) return s;
-        P->dirty_k = -2;
-    }
-    CK(cudaStreamSynchronize(st));
-    auto t1 = std::chrono::steady_clock::now();
-    CK(launch_unorient(st, P, tr, d_perm, U_out, V_out));
-    s = read_ctl(P);
-    if (s != STMF_OK) return s;
-    if (rep) {
-        memset(rep, 0, sizeof(*rep));
-        rep->f_init = f_init;
-        rep->f_final = P->ctl_host->f_ulf;
-        rep->sweeps_done = sweeps_done;
-        rep->transposed = tr;
-        rep->candidates_tried = P->ctl_host->tried;
-        rep->candidates_issued = P->ctl_host->issued;
-        rep->accepted = accepted;
-        rep->refreshes = P->refreshes;
-        rep->seconds = std::chrono::duration<double>(t1 - t0).count();
-    }
-    return STMF_OK;
+    s = fastmf_run(P, o.sweeps, o.eps);
+    if (s == STMF_OK) s = fastmf_end(P, U_out, V_out, o.trace, o.trace_cap);
+    if (s == STMF_OK) fill_report(P, rep);
+    problem_free(P);
+    return s;
 }
 
 stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops)
