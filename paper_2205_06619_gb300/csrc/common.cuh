@@ -54,6 +54,7 @@ struct stmf_ctl {
     int err;           // device-detected error code (0 = none)
     int nu, nv;        // F-ULF / F-URF candidates of the window
     int exhausted;     // 1 when the window reached the end of the row's candidates
+    int eval_next;     // work queue of the window evaluation (next unit)
     int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // window slots per type
     long long tried;   // sequential-method candidates tried (cumulative)
     long long issued;  // candidates evaluated on the device (cumulative)
@@ -84,8 +85,8 @@ struct stmf_problem {
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
-    double *part_ulf;  // (mp/4) x STMF_WMAX partial changes of F-ULF blocks
-    double *part_urf;  // (np/32) x STMF_WMAX partial changes of F-URF blocks
+    double *part_ulf;  // STMF_WMAX x ceil(m/4) partial changes of the F-ULF units
+    double *part_urf;  // STMF_WMAX x ceil(n/32) partial changes of the F-URF units
     double *fc;        // STMF_WMAX candidate errors
     stmf_ctl *ctl;     // device control block
     stmf_ctl *ctl_host;// pinned host mirror

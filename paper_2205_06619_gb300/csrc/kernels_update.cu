@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_stats(stmf_problem P)
 __global__ void __launch_bounds__(256) k_window(stmf_problem P)
 {
     __shared__ int sh[STMF_MAX_RANK];
-    __shared__ int sj[STMF_WMAX / 2];
+    __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2];
     __shared__ int scount, spos;
     stmf_ctl *ctl = P.ctl;
     const int i = ctl->i, tid = threadIdx.x, r = P.r;
@@ -272,20 +272,30 @@ __global__ void __launch_bounds__(256) k_window(stmf_problem P)
             const int c = sh[l] + P.colhist[(size_t)j * r + l];
             if (c > bestc) { bestc = c; best = l; }
         }
+        sk[tid] = best;
         const int base = ctl->ncand_row / 2;
         int *c0 = P.cand + 8 * (2 * tid);
         c0[0] = j; c0[1] = best; c0[2] = 0; c0[3] = base + tid;
         int *c1 = P.cand + 8 * (2 * tid + 1);
         c1[0] = j; c1[1] = best; c1[2] = 1; c1[3] = base + tid;
-        ctl->ulist[tid] = 2 * tid;
-        ctl->vlist[tid] = 2 * tid + 1;
     }
+    __syncthreads();
     if (tid == 0) {
+        // evaluation lists grouped by k (stable), so the evaluation recomputes
+        // E = max over l != k only when k changes; the slots keep the paper's order
+        int idx[STMF_WMAX / 2];
+        for (int a = 0; a < cnt; ++a) {
+            int b = a - 1;
+            while (b >= 0 && sk[idx[b]] > sk[a]) { idx[b + 1] = idx[b]; --b; }
+            idx[b + 1] = a;
+        }
+        for (int a = 0; a < cnt; ++a) { ctl->ulist[a] = 2 * idx[a]; ctl->vlist[a] = 2 * idx[a] + 1; }
         ctl->nc = 2 * cnt;
         ctl->nu = cnt;
         ctl->nv = cnt;
         ctl->exhausted = spos >= P.n;
         ctl->pos = spos;
+        ctl->eval_next = 0;
     }
 }
 
@@ -342,34 +352,93 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
-// term of the b-norm for one entry: |R - max(E, x)| with E = (a == k ? p2 : p1);
-// a NaN R (entry not given) gives 0 through fmaxf.
-__device__ __forceinline__ float bterm(float rv, float p1, float p2, int a, int k, float x)
+// Warp reduce-scatter of 16 values: afterwards lanes 2L and 2L+1 hold op over
+// the warp of value L.
+__device__ __forceinline__ float reduce_scatter16_min(float (&v)[16], int lane)
 {
-    const float e = a == k ? p2 : p1;
-    return fmaxf(fabsf(rv - fmaxf(e, x)), 0.f);
+#pragma unroll
+    for (int lvl = 0; lvl < 4; ++lvl) {
+        const int o = 8 >> lvl;          // half of the live values
+        const int lo = 16 >> lvl;        // lane offset of this level
+        const bool upper = lane & lo;
+#pragma unroll
+        for (int q = 0; q < o; ++q) {
+            const float send = upper ? v[q] : v[q + o];
+            const float keep = upper ? v[q + o] : v[q];
+            v[q] = fminf(keep, __shfl_xor_sync(FULL, send, lo));
+        }
+    }
+    return fminf(v[0], __shfl_xor_sync(FULL, v[0], 1));
 }
 
-constexpr int CG = 8;   // candidates per phase-1 group
+constexpr int CG = 4;          // candidates per phase-1 group (unrolled)
+constexpr int EVAL_THREADS = 256;
 
 struct EvalSmem {
-    float su[STMF_WMAX / 2][4];
-    __align__(16) float sv[STMF_WMAX / 2][32];
+    float acc[STMF_WMAX / 2][EVAL_THREADS];     // per-thread partial changes, per candidate
+    float su[STMF_WMAX / 2][4];                 // U'_sk of the unit's 4 rows (F-ULF)
+    __align__(16) float sv[STMF_WMAX / 2][32];  // V'_kt of the unit's 32 columns (F-URF)
     float red[8][32];
     int sslot[STMF_WMAX / 2], sk[STMF_WMAX / 2];
+    int unit;
 };
 
-// F-ULF part of a window.  One block owns 4 full rows: phase 1 computes
-// U'_sk = min over t of (R_st - V'_kt) for every F-ULF candidate, phase 2 the
-// candidates' change of the error over those rows,
-//   Delta = sum_st ( |R_st - P'_st| - |R_st - P_st| ),
-// accumulated per entry so that its rounding error scales with the size of
-// the change (a candidate that changes nothing gives exactly 0).
-__device__ __forceinline__ void eval_ulf_block(const stmf_problem &P, EvalSmem &S, int b)
+// E = max over l != k of (U_sl + V_lt) = (A == k ? P2 : P1) for a 4 x 4 tile.
+__device__ __forceinline__ void load_E(float (&E)[4][4], const float4 *p1, const float4 *p2,
+                                       const uint32_t *a, size_t stride4, int k)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 x = p1[i * stride4], y = p2[i * stride4];
+        const uint32_t w = a[i * stride4];
+        E[i][0] = ((w & 0xff) == (uint32_t)k) ? y.x : x.x;
+        E[i][1] = (((w >> 8) & 0xff) == (uint32_t)k) ? y.y : x.y;
+        E[i][2] = (((w >> 16) & 0xff) == (uint32_t)k) ? y.z : x.z;
+        E[i][3] = ((w >> 24) == (uint32_t)k) ? y.w : x.w;
+    }
+}
+
+// Change of the b-norm terms of a 4 x 4 tile for one candidate:
+//   sum over the tile of ( |R - max(E, u_i + v_j)| - t0 ),  t0 = |R - P1|,
+// where a NaN R (entry not given) gives 0 through fmaxf.  Pairwise sums.
+__device__ __forceinline__ float tile_change(const float (&rv)[4][4], const float (&t0)[4][4],
+                                             const float (&E)[4][4], const float (&u)[4], const float (&v)[4])
+{
+    float q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float d[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+            d[jj] = fmaxf(fabsf(rv[i][jj] - fmaxf(E[i][jj], u[i] + v[jj])), 0.f) - t0[i][jj];
+        q[i] = (d[0] + d[1]) + (d[2] + d[3]);
+    }
+    return (q[0] + q[1]) + (q[2] + q[3]);
+}
+
+// Reduces the per-thread partials of every candidate of a unit (fixed order:
+// 32 consecutive threads in FP64 per lane group, then 8 lanes) into
+// part[slot * ldpart + unit].
+__device__ __forceinline__ void reduce_unit(EvalSmem &S, int nc, double *part, int ldpart, int unit)
+{
+    __syncthreads();
+    const int tid = threadIdx.x, cc = tid >> 3, sub = tid & 7;
+    double x = 0.0;
+    if (cc < nc)
+        for (int q = 0; q < 32; ++q) x += (double)S.acc[cc][sub * 32 + q];
+#pragma unroll
+    for (int o = 4; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    if (cc < nc && sub == 0) part[(size_t)S.sslot[cc] * ldpart + unit] = x;
+}
+
+// F-ULF unit: 4 full rows.  Phase 1: U'_sk = min over t of (R_st - V'_kt) for
+// every F-ULF candidate.  Phase 2: the candidates' change of the error over
+// the 4 rows, accumulated per entry (a candidate that changes nothing gives
+// exactly 0).
+__device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S, int b, int ldpart)
 {
     const stmf_ctl *ctl = P.ctl;
     const int nu = ctl->nu;
-    if (nu == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s0 = b * 4;
     const int nf4 = P.np >> 2;
@@ -378,20 +447,22 @@ __device__ __forceinline__ void eval_ulf_block(const stmf_problem &P, EvalSmem &
         S.sslot[tid] = slot;
         S.sk[tid] = P.cand[8 * slot + 1];
     }
+    for (int cc = 0; cc < nu; ++cc) S.acc[cc][tid] = 0.f;
     __syncthreads();
     const float4 *R4 = reinterpret_cast<const float4 *>(P.R + (size_t)s0 * P.np);
 
     // ---- phase 1
     for (int g = 0; g < nu; g += CG) {
-        float acc[32];
+        float acc[4 * CG];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] = INFINITY;
-        for (int f = tid; f < nf4; f += 256) {
+        for (int q = 0; q < 4 * CG; ++q) acc[q] = INFINITY;
+        for (int f = tid; f < nf4; f += EVAL_THREADS) {
             float4 r4[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) r4[i] = R4[(size_t)i * nf4 + f];
 #pragma unroll
             for (int cc = 0; cc < CG; ++cc) {
+                asm volatile("" ::: "memory");
                 if (g + cc < nu) {
                     const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[g + cc] * P.np)[f];
 #pragma unroll
@@ -406,13 +477,13 @@ __device__ __forceinline__ void eval_ulf_block(const stmf_problem &P, EvalSmem &
                 }
             }
         }
-        const float w = reduce_scatter32<true>(acc, lane);
+        const float w = reduce_scatter16_min(acc, lane);
         S.red[warp][lane] = w;
         __syncthreads();
-        if (tid < 32) {
-            float x = S.red[0][tid];
+        if (tid < 16) {
+            float x = S.red[0][2 * tid];
 #pragma unroll
-            for (int q = 1; q < 8; ++q) x = fminf(x, S.red[q][tid]);
+            for (int q = 1; q < 8; ++q) x = fminf(x, S.red[q][2 * tid]);
             const int cc = tid >> 2, i = tid & 3;
             if (g + cc < nu) {
                 S.su[g + cc][i] = x;
@@ -422,71 +493,44 @@ __device__ __forceinline__ void eval_ulf_block(const stmf_problem &P, EvalSmem &
         __syncthreads();
     }
 
-    // ---- phase 2: thread owns 2 rows x 4 columns per step
-    float sum[32];
+    // ---- phase 2: a thread owns the 4 rows x 4 columns of one float4 column
+    const float4 *P14 = reinterpret_cast<const float4 *>(P.P1 + (size_t)s0 * P.np);
+    const float4 *P24 = reinterpret_cast<const float4 *>(P.P2 + (size_t)s0 * P.np);
+    const uint32_t *A4 = reinterpret_cast<const uint32_t *>(P.A + (size_t)s0 * P.np);
+    for (int f = tid; f < nf4; f += EVAL_THREADS) {
+        float rv[4][4], t0[4][4], E[4][4];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) sum[q] = 0.f;
-    const int rg = tid >> 7, cl = tid & 127;
-    const size_t rowoff = (size_t)(2 * rg) * nf4;
-    const float4 *R4b = R4 + rowoff;
-    const float4 *P14 = reinterpret_cast<const float4 *>(P.P1 + (size_t)s0 * P.np) + rowoff;
-    const float4 *P24 = reinterpret_cast<const float4 *>(P.P2 + (size_t)s0 * P.np) + rowoff;
-    const uint32_t *A4 = reinterpret_cast<const uint32_t *>(P.A + (size_t)s0 * P.np) + rowoff;
-    for (int f = cl; f < nf4; f += 128) {
-        float rv[2][4], p1[2][4], p2[2][4], t0[2][4];
-        int a[2][4];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float4 x = R4b[(size_t)i * nf4 + f], y = P14[(size_t)i * nf4 + f], z = P24[(size_t)i * nf4 + f];
-            const uint32_t w = A4[(size_t)i * nf4 + f];
+        for (int i = 0; i < 4; ++i) {
+            const float4 x = R4[(size_t)i * nf4 + f], y = P14[(size_t)i * nf4 + f];
             rv[i][0] = x.x; rv[i][1] = x.y; rv[i][2] = x.z; rv[i][3] = x.w;
-            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
-            p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                a[i][jj] = (w >> (8 * jj)) & 0xff;
-                t0[i][jj] = fmaxf(fabsf(rv[i][jj] - p1[i][jj]), 0.f);
-            }
+            t0[i][0] = fmaxf(fabsf(x.x - y.x), 0.f); t0[i][1] = fmaxf(fabsf(x.y - y.y), 0.f);
+            t0[i][2] = fmaxf(fabsf(x.z - y.z), 0.f); t0[i][3] = fmaxf(fabsf(x.w - y.w), 0.f);
         }
-#pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-            // keep the compiler from hoisting every candidate's loads at once
-            asm volatile("" ::: "memory");
-            if (cc < nu) {
-                const int k = S.sk[cc];
-                const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[cc] * P.np)[f];
-                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-                float t[2][4];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const float u = S.su[cc][2 * rg + i];
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj)
-                        t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u + v[jj]) - t0[i][jj];
-                }
-                sum[cc] += ((t[0][0] + t[0][1]) + (t[0][2] + t[0][3])) + ((t[1][0] + t[1][1]) + (t[1][2] + t[1][3]));
+        int kcur = -1;
+#pragma unroll 1
+        for (int cc = 0; cc < nu; ++cc) {
+            const int k = S.sk[cc];
+            if (k != kcur) {
+                load_E(E, P14 + f, P24 + f, A4 + f, nf4, k);
+                kcur = k;
             }
+            const float4 u4 = *reinterpret_cast<const float4 *>(&S.su[cc][0]);
+            const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[cc] * P.np)[f];
+            const float u[4] = {u4.x, u4.y, u4.z, u4.w};
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+            S.acc[cc][tid] += tile_change(rv, t0, E, u, v);
         }
     }
-    const float w = reduce_scatter32<false>(sum, lane);
-    S.red[warp][lane] = w;
-    __syncthreads();
-    if (tid < nu) {
-        double x = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) x += (double)S.red[q][tid];
-        P.part_ulf[(size_t)b * STMF_WMAX + S.sslot[tid]] = x;
-    }
+    reduce_unit(S, nu, P.part_ulf, ldpart, b);
 }
 
-// F-URF part of a window.  One block owns a strip of 32 full columns: phase 1
-// computes V'_kt = min over s of (R_st - U'_sk) for its columns from rows of
-// RT, phase 2 the candidates' change of the error over the strip.
-__device__ __forceinline__ void eval_urf_block(const stmf_problem &P, EvalSmem &S, int b)
+// F-URF unit: a strip of 32 full columns.  Phase 1: V'_kt = min over s of
+// (R_st - U'_sk) from rows of RT (warp w owns columns 4w .. 4w+3).  Phase 2:
+// the candidates' change of the error over the strip.
+__device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S, int b, int ldpart)
 {
     const stmf_ctl *ctl = P.ctl;
     const int nv = ctl->nv;
-    if (nv == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t0c = b * 32;
     if (tid < nv) {
@@ -494,22 +538,24 @@ __device__ __forceinline__ void eval_urf_block(const stmf_problem &P, EvalSmem &
         S.sslot[tid] = slot;
         S.sk[tid] = P.cand[8 * slot + 1];
     }
+    for (int cc = 0; cc < nv; ++cc) S.acc[cc][tid] = 0.f;
     __syncthreads();
 
-    // ---- phase 1: warp w owns columns t0c+4w .. +3
+    // ---- phase 1
     {
         const int nf4 = P.mp >> 2;
         const float4 *X4 = reinterpret_cast<const float4 *>(P.RT + (size_t)(t0c + 4 * warp) * P.mp);
         for (int g = 0; g < nv; g += CG) {
-            float acc[32];
+            float acc[4 * CG];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) acc[q] = INFINITY;
+            for (int q = 0; q < 4 * CG; ++q) acc[q] = INFINITY;
             for (int f = lane; f < nf4; f += 32) {
                 float4 x4[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) x4[i] = X4[(size_t)i * nf4 + f];
 #pragma unroll
                 for (int cc = 0; cc < CG; ++cc) {
+                    asm volatile("" ::: "memory");
                     if (g + cc < nv) {
                         const float4 u4 = reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[g + cc] * P.mp)[f];
 #pragma unroll
@@ -524,9 +570,9 @@ __device__ __forceinline__ void eval_urf_block(const stmf_problem &P, EvalSmem &
                     }
                 }
             }
-            const float x = reduce_scatter32<true>(acc, lane);
-            const int cc = lane >> 2, i = lane & 3;
-            if (g + cc < nv) {
+            const float x = reduce_scatter16_min(acc, lane);
+            const int cc = lane >> 3, i = (lane >> 1) & 3;
+            if ((lane & 1) == 0 && g + cc < nv) {
                 S.sv[g + cc][4 * warp + i] = x;
                 P.Vc[(size_t)S.sslot[g + cc] * P.np + t0c + 4 * warp + i] = x;
             }
@@ -534,68 +580,60 @@ __device__ __forceinline__ void eval_urf_block(const stmf_problem &P, EvalSmem &
     }
     __syncthreads();
 
-    // ---- phase 2: thread owns 4 columns x 2 consecutive rows per step
+    // ---- phase 2: a thread owns 4 consecutive rows x 4 columns per step
     const int cl = tid & 7, rl = tid >> 3;
     const int tc = t0c + cl * 4;
-    float sum[32];
+    const size_t st4 = (size_t)(P.np >> 2);
+    for (int sb = rl * 4; sb < P.m; sb += 128) {
+        const size_t off4 = ((size_t)sb * P.np + tc) >> 2;
+        const float4 *R4 = reinterpret_cast<const float4 *>(P.R) + off4;
+        const float4 *P14 = reinterpret_cast<const float4 *>(P.P1) + off4;
+        const float4 *P24 = reinterpret_cast<const float4 *>(P.P2) + off4;
+        const uint32_t *A4 = reinterpret_cast<const uint32_t *>(P.A) + off4;
+        float rv[4][4], t0[4][4], E[4][4];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) sum[q] = 0.f;
-    for (int sb = rl * 2; sb < P.m; sb += 64) {
-        float rv[2][4], p1[2][4], p2[2][4], t0[2][4];
-        int a[2][4];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const size_t off = (size_t)(sb + i) * P.np + tc;
-            const float4 x = *reinterpret_cast<const float4 *>(P.R + off);
-            const float4 y = *reinterpret_cast<const float4 *>(P.P1 + off);
-            const float4 z = *reinterpret_cast<const float4 *>(P.P2 + off);
-            const uint32_t w = *reinterpret_cast<const uint32_t *>(P.A + off);
+        for (int i = 0; i < 4; ++i) {
+            const float4 x = R4[i * st4], y = P14[i * st4];
             rv[i][0] = x.x; rv[i][1] = x.y; rv[i][2] = x.z; rv[i][3] = x.w;
-            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
-            p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                a[i][jj] = (w >> (8 * jj)) & 0xff;
-                t0[i][jj] = fmaxf(fabsf(rv[i][jj] - p1[i][jj]), 0.f);
-            }
+            t0[i][0] = fmaxf(fabsf(x.x - y.x), 0.f); t0[i][1] = fmaxf(fabsf(x.y - y.y), 0.f);
+            t0[i][2] = fmaxf(fabsf(x.z - y.z), 0.f); t0[i][3] = fmaxf(fabsf(x.w - y.w), 0.f);
         }
-#pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-            asm volatile("" ::: "memory");
-            if (cc < nv) {
-                const int k = S.sk[cc];
-                const float2 u2 = *reinterpret_cast<const float2 *>(P.Uc + (size_t)S.sslot[cc] * P.mp + sb);
-                const float u[2] = {u2.x, u2.y};
-                const float4 v4 = *reinterpret_cast<const float4 *>(&S.sv[cc][cl * 4]);
-                const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-                float t[2][4];
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj)
-                        t[i][jj] = bterm(rv[i][jj], p1[i][jj], p2[i][jj], a[i][jj], k, u[i] + v[jj]) - t0[i][jj];
-                sum[cc] += ((t[0][0] + t[0][1]) + (t[0][2] + t[0][3])) + ((t[1][0] + t[1][1]) + (t[1][2] + t[1][3]));
+        int kcur = -1;
+#pragma unroll 1
+        for (int cc = 0; cc < nv; ++cc) {
+            const int k = S.sk[cc];
+            if (k != kcur) {
+                load_E(E, P14, P24, A4, st4, k);
+                kcur = k;
             }
+            const float4 u4 = *reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[cc] * P.mp + sb);
+            const float4 v4 = *reinterpret_cast<const float4 *>(&S.sv[cc][cl * 4]);
+            const float u[4] = {u4.x, u4.y, u4.z, u4.w};
+            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+            S.acc[cc][tid] += tile_change(rv, t0, E, u, v);
         }
     }
-    const float w = reduce_scatter32<false>(sum, lane);
-    S.red[warp][lane] = w;
-    __syncthreads();
-    if (tid < nv) {
-        double x = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) x += (double)S.red[q][tid];
-        P.part_urf[(size_t)b * STMF_WMAX + S.sslot[tid]] = x;
-    }
+    reduce_unit(S, nv, P.part_urf, ldpart, b);
 }
 
-// One launch evaluates the whole window: blocks [0, nb_ulf) run F-ULF rows,
-// the rest F-URF column strips, side by side.
-__global__ void __launch_bounds__(256, 2) k_eval(stmf_problem P, int nb_ulf)
+// One launch evaluates the whole window with persistent blocks that take
+// units from a queue: the 32-column F-URF strips (the larger units) first,
+// then the 4-row F-ULF blocks.
+__global__ void __launch_bounds__(EVAL_THREADS, 2) k_eval(stmf_problem P, int nb_ulf, int nb_urf)
 {
     __shared__ EvalSmem S;
-    if ((int)blockIdx.x < nb_ulf) eval_ulf_block(P, S, blockIdx.x);
-    else eval_urf_block(P, S, blockIdx.x - nb_ulf);
+    const int total = (P.ctl->nv ? nb_urf : 0) + (P.ctl->nu ? nb_ulf : 0);
+    const int first_ulf = P.ctl->nv ? nb_urf : 0;
+    while (true) {
+        if (threadIdx.x == 0) S.unit = atomicAdd(&P.ctl->eval_next, 1);
+        __syncthreads();
+        const int u = S.unit;
+        __syncthreads();
+        if (u >= total) break;
+        if (u < first_ulf) eval_urf_unit(P, S, u, nb_urf);
+        else eval_ulf_unit(P, S, u - first_ulf, nb_ulf);
+        __syncthreads();
+    }
 }
 
 __device__ __forceinline__ void put_trace(stmf_ctl *ctl, int pos, int j, int k, int type, double f)
@@ -627,10 +665,10 @@ __global__ void __launch_bounds__(256) k_select(stmf_problem P, int nb_ulf, int 
     const int nc = ctl->nc;
     for (int c = warp; c < nc; c += 8) {
         const int type = P.cand[8 * c + 2];
-        const double *part = type == 0 ? P.part_ulf : P.part_urf;
         const int nb = type == 0 ? nb_ulf : nb_urf;
+        const double *part = (type == 0 ? P.part_ulf : P.part_urf) + (size_t)c * nb;
         double x = 0.0;
-        for (int b = lane; b < nb; b += 32) x += part[(size_t)b * STMF_WMAX + c];
+        for (int b = lane; b < nb; b += 32) x += part[b];
 #pragma unroll
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
         if (lane == 0) { sf[c] = x; P.fc[c] = ctl->f + x; }
@@ -731,6 +769,7 @@ __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
     ctl->exhausted = 1;
     ctl->ncand_row = 0;
     ctl->select_mode = 0;
+    ctl->eval_next = 0;
 }
 
 // Unconditional commit of slot 0 (commit_if_decreases = 0).
@@ -825,7 +864,9 @@ static inline int nb_urf(const stmf_problem *P) { return (P->n + 31) / 32; }
 
 cudaError_t launch_eval(cudaStream_t st, stmf_problem *P)
 {
-    k_eval<<<nb_ulf(P) + nb_urf(P), 256, 0, st>>>(*P, nb_ulf(P));
+    const int units = nb_ulf(P) + nb_urf(P);
+    const int blocks = min(units, 2 * P->ctx->num_sms);
+    k_eval<<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
     return cudaGetLastError();
 }
 
