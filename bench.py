@@ -1,0 +1,331 @@
+"""Benchmark of the FastSTMF hot path on GB300: sweeps/s and max-plus Gop/s.
+
+Workload (default): the gene-expression-scale job, R 1000 x 5000 FP32 with a
+planted rank-10 tropical structure (0.5*log2(1+LogNormal(3,2)) factors),
+N(0, 0.05) noise, 80% of entries given, rank 10 (synthetic stand-in for the
+paper's TCGA matrices, which are not available).
+
+A step is one sweep of Algorithm 3 (every row of the oriented R visited once:
+candidate windows of F-ULF / F-URF updates, select, commit, refresh of the
+product planes and statistics).  The run is one factorization: W untimed
+warm-up sweeps from the Random Acol start, then K timed sweeps of the same
+run, each bracketed by a barrier, a device synchronisation and CUDA events on
+the library's stream; the L2 cache is flushed (a 256 MiB write) before each
+timed sweep, outside its timed span.  The e2e figure covers the whole job
+through the public API from pinned host buffers: the upload of R and the
+mask, initialisation, all W + K sweeps and the download of U, V.
+
+value = sweeps/s summed over ranks (independent replicas, weak scaling).
+gops  = algorithmic max-plus operations of the sequential method per second:
+        2 r N_obs per product refresh + 6 N_obs per candidate tried (up to the
+        kept one); speculative window work is not counted.
+
+``--impl reference`` times the oracle (plain C, FP64 arithmetic rounded to
+FP32) on the host cores on the same workload: a step is one row of the sweep
+that follows the W warm-up sweeps (the start state is the library's state
+after W sweeps, mapped into the oracle's frame; without a GPU it is the
+oracle's own initial state); one untimed row, then K timed rows;
+value = rows/s / m sweeps/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FastSTMF sweeps/s & max-plus Gop/s (% FP32 peak); time-to-error vs plain"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES = 128
+# plain FP32 ALU issue peak for a 1:1 FADD/FMNMX stream: every SM issues 128
+# lane operations per cycle at the maximum clock
+ALU_PEAK_TOPS = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def workload(name, seed):
+    from paper_2205_06619_gb300 import synth
+    if name == "gene":
+        w = synth.workload_gene(seed)
+        w["label"] = "gene-expression 1000x5000 rank-10, 80% given"
+    elif name == "small":
+        w = synth.workload_small(seed)
+        w["label"] = "small 200x100 rank-3, 80% given"
+    elif name == "large":
+        w = synth.workload_large(seed)
+        w["label"] = "large 4000x20000 rank-20, 50% given"
+    else:
+        raise SystemExit("unknown workload " + name)
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rows(R, M, rank, seed, U_start, V_start, budget_s, min_rows=1, max_rows=None, warm_rows=0):
+    """Times the oracle's ByRow steps on the first rows of a sweep from a given
+    state (caller orientation); returns (rows, seconds, per-row times)."""
+    import oracle as orc
+    st = orc.prepare(R, M, rank, seed=seed)
+    assert not st["transposed"]
+    Ri, Mi = st["R"], st["M"]
+    perm = st["perm"]
+    if U_start is not None:
+        Ui = np.ascontiguousarray(U_start[perm], dtype=np.float64)
+        Vi = np.ascontiguousarray(V_start, dtype=np.float64)
+    else:
+        Ui, Vi = st["U"], st["V"]
+    f = orc.error(Ri, Mi, Ui, Vi)
+    times = []
+    i = 0
+    for _ in range(warm_rows):
+        _, f, _, _ = orc.row_step(Ri, Mi, Ui, Vi, i, f)
+        i += 1
+    t_all = time.perf_counter()
+    while True:
+        t = time.perf_counter()
+        _, f, _, _ = orc.row_step(Ri, Mi, Ui, Vi, i, f)
+        times.append(time.perf_counter() - t)
+        i += 1
+        if max_rows is not None and len(times) >= max_rows:
+            break
+        if len(times) >= min_rows and time.perf_counter() - t_all >= budget_s:
+            break
+        if i >= Ri.shape[0]:
+            break
+    return len(times), sum(times), times
+
+
+def run_reference(args):
+    """The oracle on the host cores, on the same workload (see module doc)."""
+    rank_id = int(os.environ.get("RANK", "0"))
+    if rank_id != 0:
+        return
+    w = workload(args.workload, args.seed)
+    R, M, r = w["R"], w["mask"], w["rank"]
+    U_start = V_start = None
+    start = "the oracle's own initial state (sweep 0)"
+    try:
+        import torch
+        if torch.cuda.is_available() and args.warmup > 0:
+            from paper_2205_06619_gb300 import api
+            fz = api.Factorization(torch.from_numpy(R).cuda(), api.pack_mask(M), rank=r, seed=args.seed)
+            fz.run(args.warmup)
+            U, V = fz.result()
+            U_start, V_start = U.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
+            start = ("the state after %d sweeps (the warm-up sweeps of the library's arm, prepared on the GPU "
+                     "and mapped into the oracle's frame)" % args.warmup)
+            fz.close()
+    except Exception as e:  # pragma: no cover - reported in the sample text
+        start += " (GPU preparation failed: %s)" % e
+    rows, secs, _ = oracle_rows(R, M, r, args.seed, U_start, V_start, budget_s=0.0,
+                                min_rows=args.steps, max_rows=args.steps, warm_rows=min(args.warmup, 1))
+    m = min(R.shape)
+    value = rows / secs / m
+    sample = ("%d timed rows (after %d untimed row) of the ByRow sweep of the %s job, from %s; "
+              "sweeps/s = rows/s / %d rows" % (rows, min(args.warmup, 1), w["label"], start, m))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / rows,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64->f32",
+            "data": "synthetic", "config": {"workload": w["label"], "step": "one row of the sweep"},
+            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5, help="timed sweeps")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up sweeps")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gene", choices=["gene", "small", "large"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        raise SystemExit("at least 3 warm-up sweeps are required")
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2205_06619_gb300 import api
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank_id = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # independent replicas: rank q factorizes its own seeded matrix
+    w = workload(args.workload, args.seed + rank_id)
+    R_np, M_np, r = w["R"], w["mask"], w["rank"]
+    n_obs = int(M_np.sum())
+    m_or = min(R_np.shape)
+    R_host = torch.from_numpy(R_np).pin_memory()
+    mask_words_host = api.pack_mask(M_np).cpu().pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ctx = api.context()
+    stream = ctx.stream
+
+    # ---- whole job through the public API (e2e), with the timed sweeps inside
+    barrier()
+    t_e2e = time.perf_counter()
+    R_dev = R_host.to("cuda", non_blocking=True)
+    mask_dev = mask_words_host.to("cuda", non_blocking=True)
+    fz = api.Factorization(R_dev, mask_dev, rank=r, seed=args.seed + rank_id)
+    for _ in range(args.warmup):
+        fz.run(1)
+    rep0 = fz.run(0)
+    times = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            barrier()
+            ev[k][0].record(stream)
+            fz.run(1)
+            ev[k][1].record(stream)
+            barrier()
+        torch.cuda.synchronize()
+    times = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    rep1 = fz.report
+    U, V = fz.result()
+    U_h, V_h = U.cpu(), V.cpu()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t_e2e
+
+    t_timed = sum(times)
+    if dist is not None:
+        tt = torch.tensor([t_timed, t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_timed, t_e2e = float(tt[0]), float(tt[1])
+    sweeps_all = args.steps * world
+    value = sweeps_all / t_timed
+    d_tried = rep1["candidates_tried"] - rep0["candidates_tried"]
+    d_ref = rep1["refreshes"] - rep0["refreshes"]
+    d_win = rep1["windows"] - rep0["windows"]
+    ops = 6.0 * n_obs * d_tried + 2.0 * r * n_obs * d_ref
+    gops = ops / (t_timed / world) / 1e9 * world
+    d_eval_ns = rep1["eval_ns"] - rep0["eval_ns"]
+    d_eval_n = rep1["eval_launches"] - rep0["eval_launches"]
+    d_eval_c = rep1["eval_candidates"] - rep0["eval_candidates"]
+    achieved = (6.0 * n_obs * d_eval_c) / (d_eval_ns * 1e-9) / 1e12 if d_eval_ns else None
+    launches = 4 * d_win + args.steps * m_or + 5 * d_ref + args.steps
+
+    if rank_id != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle  # noqa: F401  (CPU baseline leg only)
+        rows, secs, _ = oracle_rows(R_np, M_np, r, args.seed, U_h.numpy().astype(np.float64),
+                                    V_h.numpy().astype(np.float64), budget_s=args.cpu_budget)
+        cpu = {"value": rows / secs / m_or, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d rows of sweep %d of the same run (oracle started from the library's state "
+                         "after the timed sweeps), %.1f s single-threaded; sweeps/s = rows/s / %d rows"
+                         % (rows, args.warmup + args.steps, secs, m_or)}
+
+    h2d = (R_np.nbytes + mask_words_host.numel() * 4) / (args.warmup + args.steps)
+    d2h = (U_h.numel() + V_h.numel()) * 4 / (args.warmup + args.steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_timed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["label"], "m": int(R_np.shape[0]), "n": int(R_np.shape[1]), "rank": r,
+                   "given": n_obs, "step": "one ByRow sweep (sweeps %d..%d of one run)"
+                                           % (args.warmup, args.warmup + args.steps - 1),
+                   "l2": "flushed (256 MiB write) before every timed sweep",
+                   "parallelism": "independent replicas" if world > 1 else "single GPU"},
+        "gops": gops, "gops_frac_of_alu_peak": gops / (ALU_PEAK_TOPS * 1e3),
+        "candidates_tried_per_sweep": d_tried / args.steps,
+        "roofline": {"kernel": "k_eval (window of F-ULF/F-URF candidates)", "bound": "alu",
+                     "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
+                     "frac": achieved / ALU_PEAK_TOPS if achieved else None, "traffic": None,
+                     "launches": d_eval_n, "avg_launch_us": d_eval_ns / 1e3 / max(d_eval_n, 1),
+                     "candidates_per_launch": d_eval_c / max(d_eval_n, 1),
+                     "timing": "per-launch device time from %globaltimer (kernel runs inside a CUDA graph)"},
+        "e2e": {"value": (args.warmup + args.steps) * world / t_e2e, "unit": "sweeps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "job": "upload + init + %d sweeps + download, public API" % (args.warmup + args.steps)},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -95,6 +95,9 @@ typedef struct {
     int64_t refreshes;        /* product/statistics refreshes                        */
     int64_t windows;          /* device windows evaluated                            */
     int64_t trace_records;    /* trace records written                               */
+    int64_t eval_ns;          /* summed device durations of the window evaluations   */
+    int64_t eval_launches;    /* window evaluations timed                            */
+    int64_t eval_candidates;  /* candidates those evaluations covered                */
     double seconds;           /* wall time of the sweep loop                         */
 } stmf_report;
 

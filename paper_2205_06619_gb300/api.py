@@ -43,7 +43,8 @@ class Report(C.Structure):
     _fields_ = [("f_init", C.c_double), ("f_final", C.c_double), ("sweeps_done", C.c_int),
                 ("transposed", C.c_int), ("candidates_tried", C.c_int64),
                 ("candidates_issued", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
-                ("windows", C.c_int64), ("trace_records", C.c_int64), ("seconds", C.c_double)]
+                ("windows", C.c_int64), ("trace_records", C.c_int64), ("eval_ns", C.c_int64),
+                ("eval_launches", C.c_int64), ("eval_candidates", C.c_int64), ("seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -61,6 +61,10 @@ struct stmf_ctl {
     long long accepted;
     long long refreshes;
     long long windows;
+    unsigned long long ev_t0, ev_t1;   // earliest start / latest end of the running window evaluation
+    long long eval_ns;                 // summed durations of the window evaluations (%globaltimer)
+    long long eval_launches;
+    long long eval_cands;              // candidates those evaluations covered
     double f;          // current error (sum over j of td_col[j])
     double f_new;      // error after the kept candidate (f + Delta)
     int32_t *trace;    // device trace buffer (STMF_TRACE_INTS per record) or NULL

@@ -619,9 +619,20 @@ __device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S
 // One launch evaluates the whole window with persistent blocks that take
 // units from a queue: the 32-column F-URF strips (the larger units) first,
 // then the 4-row F-ULF blocks.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __global__ void __launch_bounds__(EVAL_THREADS, 2) k_eval(stmf_problem P, int nb_ulf, int nb_urf)
 {
     __shared__ EvalSmem S;
+    // the launch's duration (first block start to last block end) is
+    // recorded with the global nanosecond timer: the kernel runs inside a
+    // CUDA graph, where no event can bracket a single node
+    if (threadIdx.x == 0) atomicMin(&P.ctl->ev_t0, global_ns());
     const int total = (P.ctl->nv ? nb_urf : 0) + (P.ctl->nu ? nb_ulf : 0);
     const int first_ulf = P.ctl->nv ? nb_urf : 0;
     while (true) {
@@ -634,6 +645,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) k_eval(stmf_problem P, int nb
         else eval_ulf_unit(P, S, u - first_ulf, nb_ulf);
         __syncthreads();
     }
+    if (threadIdx.x == 0) atomicMax(&P.ctl->ev_t1, global_ns());
 }
 
 __device__ __forceinline__ void put_trace(stmf_ctl *ctl, int pos, int j, int k, int type, double f)
@@ -685,6 +697,13 @@ __global__ void __launch_bounds__(256) k_select(stmf_problem P, int nb_ulf, int 
         skept = kept;
         ctl->issued += nc;
         ctl->windows += 1;
+        if (ctl->ev_t1 > ctl->ev_t0) {
+            ctl->eval_ns += (long long)(ctl->ev_t1 - ctl->ev_t0);
+            ctl->eval_launches += 1;
+            ctl->eval_cands += nc;
+        }
+        ctl->ev_t0 = ~0ull;
+        ctl->ev_t1 = 0ull;
         ctl->tried += (ctl->select_mode == 0 && kept >= 0) ? kept + 1 : nc;
         ctl->ncand_row += nc;
         ctl->kept = kept >= 0;

@@ -142,6 +142,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     c.wj0 = 2;
     c.wmax = window;
     c.dirty_k = -1;
+    c.ev_t0 = ~0ull;
     e = cudaMemsetAsync(P->U, 0, sizeof(float) * mp * r, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->V, 0, sizeof(float) * r * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P1, 0, sizeof(float) * mp * np, st);
@@ -495,6 +496,9 @@ void fill_report(const stmf_problem *P, stmf_report *rep)
     rep->refreshes = c.refreshes;
     rep->windows = c.windows;
     rep->trace_records = c.ntrace;
+    rep->eval_ns = c.eval_ns;
+    rep->eval_launches = c.eval_launches;
+    rep->eval_candidates = c.eval_cands;
     rep->seconds = P->seconds;
 }
 
