@@ -17,6 +17,17 @@
 
 namespace {
 
+// Compensated FP32 accumulation (TwoSum, Knuth): s + c carries the running sum
+// to about u^2 relative accuracy, with FP32 adds only (FP64 is slow on GB300).
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += e;
+}
+
 constexpr int TR = 32;     // rows per tile
 constexpr int TC = 128;    // columns per tile
 constexpr int TILES = 4;   // tiles per CTA (rows of a CTA = TR * TILES)
@@ -129,7 +140,11 @@ k_maxplus(int m, int n, int r, const float *__restrict__ U, int ldu,
     }
 }
 
-// Planes-only variant for the internal layout (no mask, vector stores).
+// Planes for the internal layout (no mask, vector stores), with td_col and
+// colhist partials per 128-row part.  The column sums of td are accumulated
+// in compensated FP32 per thread and combined in FP64; the histogram lives in
+// shared memory as [l][4][32] so the 32 lanes of a warp always hit 32
+// different banks.
 __global__ void __launch_bounds__(256)
 k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *__restrict__ V,
                  int ld, float *__restrict__ P1, uint8_t *__restrict__ A, float *__restrict__ P2,
@@ -138,7 +153,7 @@ k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *
     __shared__ float sU[TR][STMF_MAX_RANK + 1];
     __shared__ __align__(16) float sV[STMF_MAX_RANK][TC];
     __shared__ double sTd[8][TC];
-    __shared__ int sHist[TC * STMF_MAX_RANK];
+    __shared__ int sHist[STMF_MAX_RANK][4][32];
 
     const int tid = threadIdx.x, rg = tid >> 5, cl = tid & 31;
     const int col0 = blockIdx.x * TC;
@@ -149,8 +164,8 @@ k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *
         int l = e / TC, b = e % TC;
         sV[l][b] = V[(size_t)l * ld + col0 + b];
     }
-    for (int e = tid; e < TC * r; e += 256) sHist[e] = 0;
-    double td_acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int e = tid; e < r * 128; e += 256) (&sHist[0][0][0])[e] = 0;
+    float ts[4] = {0.f, 0.f, 0.f, 0.f}, tc[4] = {0.f, 0.f, 0.f, 0.f};
 
     for (int tile = 0; tile < TILES; ++tile) {
         const int row0 = (part * TILES + tile) * TR;
@@ -199,14 +214,14 @@ k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
                 if (rv[jj] == rv[jj]) {   // given entry (not NaN)
-                    td_acc[jj] += (double)fabsf(rv[jj] - p1[i][jj]);
-                    atomicAdd(&sHist[(cl * 4 + jj) * r + am[i][jj]], 1);
+                    two_sum_add(ts[jj], tc[jj], fabsf(rv[jj] - p1[i][jj]));
+                    atomicAdd(&sHist[am[i][jj]][jj][cl], 1);
                 }
             }
         }
     }
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) sTd[rg][cl * 4 + jj] = td_acc[jj];
+    for (int jj = 0; jj < 4; ++jj) sTd[rg][cl * 4 + jj] = (double)ts[jj] + (double)tc[jj];
     __syncthreads();
     if (tid < TC) {
         double s = 0.0;
@@ -214,8 +229,10 @@ k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *
         for (int g = 0; g < 8; ++g) s += sTd[g][tid];
         tdpart[(size_t)part * ld + col0 + tid] = s;
     }
-    for (int e = tid; e < TC * r; e += 256)
-        chpart[((size_t)part * ld + col0 + e / r) * r + e % r] = sHist[e];
+    for (int e = tid; e < TC * r; e += 256) {
+        const int b = e / r, l = e % r;          // column b of the tile = lane b/4, slot b%4
+        chpart[((size_t)part * ld + col0 + b) * r + l] = sHist[l][b & 3][b >> 2];
+    }
 }
 
 // td_col[t] = sum over parts (fixed order); colhist likewise.  Also clears
@@ -243,7 +260,7 @@ __global__ void k_td_finalize(const double *__restrict__ tdpart, const int *__re
 // counted over a 2-D grid (columns x key chunks held in shared memory) so
 // the O(n^2) comparisons spread over every SM.  td_col >= 0, so its IEEE bit
 // pattern orders like the value and compares as a 64-bit integer.
-constexpr int RANK_CHUNK = 2048;
+constexpr int RANK_CHUNK = 512;
 __global__ void __launch_bounds__(256) k_rank(const double *__restrict__ tdcol, int n, int *__restrict__ rank)
 {
     __shared__ unsigned long long sk[RANK_CHUNK];

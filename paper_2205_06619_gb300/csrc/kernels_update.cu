@@ -184,20 +184,31 @@ __global__ void __launch_bounds__(256) k_stats(stmf_problem P)
     for (int l = l0; l < l1; ++l) {
         float a1 = INFINITY, a2 = INFINITY;
         int ai = 0x7fffffff;
-        for (int f = lane; f < len4; f += 32) {
-            const float4 x = x4[f];
-            float y[4];
-            if (col) {
+        // two float4 per lane and step: independent loads in flight
+        for (int f0 = lane; f0 < len4; f0 += 64) {
+            float4 x[2];
+            float y[2][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) y[q] = P.U[(size_t)(4 * f + q) * P.r + l];
-            } else {
-                const float4 v = reinterpret_cast<const float4 *>(P.V + (size_t)l * P.np)[f];
-                y[0] = v.x; y[1] = v.y; y[2] = v.z; y[3] = v.w;
+            for (int h = 0; h < 2; ++h) {
+                const int f = f0 + 32 * h;
+                x[h] = f < len4 ? x4[f] : make_float4(NAN, NAN, NAN, NAN);
+                if (col) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) y[h][q] = f < len4 ? P.U[(size_t)(4 * f + q) * P.r + l] : 0.f;
+                } else {
+                    const float4 v = f < len4 ? reinterpret_cast<const float4 *>(P.V + (size_t)l * P.np)[f]
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                    y[h][0] = v.x; y[h][1] = v.y; y[h][2] = v.z; y[h][3] = v.w;
+                }
             }
-            top2_push(x.x - y[0], 4 * f + 0, a1, ai, a2);
-            top2_push(x.y - y[1], 4 * f + 1, a1, ai, a2);
-            top2_push(x.z - y[2], 4 * f + 2, a1, ai, a2);
-            top2_push(x.w - y[3], 4 * f + 3, a1, ai, a2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int f = f0 + 32 * h;
+                top2_push(x[h].x - y[h][0], 4 * f + 0, a1, ai, a2);
+                top2_push(x[h].y - y[h][1], 4 * f + 1, a1, ai, a2);
+                top2_push(x[h].z - y[h][2], 4 * f + 2, a1, ai, a2);
+                top2_push(x[h].w - y[h][3], 4 * f + 3, a1, ai, a2);
+            }
         }
         top2_warp_merge(a1, ai, a2);
         if (lane == 0) {
@@ -219,7 +230,7 @@ __global__ void __launch_bounds__(256) k_stats(stmf_problem P)
 // union adds multiplicities; smaller l on ties).  Each j gives F-ULF (slot 2a)
 // then F-URF (slot 2a+1), the order in which Algorithm 3 tries them.  At the
 // first window of a row the row histogram is rebuilt.
-__global__ void __launch_bounds__(256) k_window(stmf_problem P)
+__global__ void __launch_bounds__(1024) k_window(stmf_problem P)
 {
     __shared__ int sh[STMF_MAX_RANK];
     __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2];
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(256) k_window(stmf_problem P)
         if (tid < r) sh[tid] = 0;
         __syncthreads();
         const uint8_t *Ai = P.A + (size_t)i * P.np;
-        for (int t = tid; t < P.n; t += 256)
+        for (int t = tid; t < P.n; t += 1024)
             if (Ri[t] == Ri[t]) atomicAdd(&sh[Ai[t]], 1);
         __syncthreads();
         if (tid < r) P.rowhist[tid] = sh[tid];
@@ -462,7 +473,6 @@ __device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S
             for (int i = 0; i < 4; ++i) r4[i] = R4[(size_t)i * nf4 + f];
 #pragma unroll
             for (int cc = 0; cc < CG; ++cc) {
-                asm volatile("" ::: "memory");
                 if (g + cc < nu) {
                     const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[g + cc] * P.np)[f];
 #pragma unroll
@@ -507,15 +517,18 @@ __device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S
             t0[i][2] = fmaxf(fabsf(x.z - y.z), 0.f); t0[i][3] = fmaxf(fabsf(x.w - y.w), 0.f);
         }
         int kcur = -1;
+        // the next candidate's V' columns are loaded one iteration ahead
+        float4 vnext = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[0] * P.np)[f];
 #pragma unroll 1
         for (int cc = 0; cc < nu; ++cc) {
+            const float4 v4 = vnext;
+            if (cc + 1 < nu) vnext = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[cc + 1] * P.np)[f];
             const int k = S.sk[cc];
             if (k != kcur) {
                 load_E(E, P14 + f, P24 + f, A4 + f, nf4, k);
                 kcur = k;
             }
             const float4 u4 = *reinterpret_cast<const float4 *>(&S.su[cc][0]);
-            const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[cc] * P.np)[f];
             const float u[4] = {u4.x, u4.y, u4.z, u4.w};
             const float v[4] = {v4.x, v4.y, v4.z, v4.w};
             S.acc[cc][tid] += tile_change(rv, t0, E, u, v);
@@ -555,7 +568,6 @@ __device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S
                 for (int i = 0; i < 4; ++i) x4[i] = X4[(size_t)i * nf4 + f];
 #pragma unroll
                 for (int cc = 0; cc < CG; ++cc) {
-                    asm volatile("" ::: "memory");
                     if (g + cc < nv) {
                         const float4 u4 = reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[g + cc] * P.mp)[f];
 #pragma unroll
@@ -599,14 +611,17 @@ __device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S
             t0[i][2] = fmaxf(fabsf(x.z - y.z), 0.f); t0[i][3] = fmaxf(fabsf(x.w - y.w), 0.f);
         }
         int kcur = -1;
+        // the next candidate's U' rows are loaded one iteration ahead
+        float4 unext = *reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[0] * P.mp + sb);
 #pragma unroll 1
         for (int cc = 0; cc < nv; ++cc) {
+            const float4 u4 = unext;
+            if (cc + 1 < nv) unext = *reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[cc + 1] * P.mp + sb);
             const int k = S.sk[cc];
             if (k != kcur) {
                 load_E(E, P14, P24, A4, st4, k);
                 kcur = k;
             }
-            const float4 u4 = *reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[cc] * P.mp + sb);
             const float4 v4 = *reinterpret_cast<const float4 *>(&S.sv[cc][cl * 4]);
             const float u[4] = {u4.x, u4.y, u4.z, u4.w};
             const float v[4] = {v4.x, v4.y, v4.z, v4.w};
@@ -665,7 +680,7 @@ __device__ __forceinline__ void put_trace(stmf_ctl *ctl, int pos, int j, int k, 
 // trace record and advances the row.  In a graph it also sets the
 // conditions of the row loop: h_win (another window of this row), h_dirty
 // (refresh before the next row), h_row (another row in this sweep).
-__global__ void __launch_bounds__(256) k_select(stmf_problem P, int nb_ulf, int nb_urf, int in_graph, int single,
+__global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nb_ulf, int nb_urf, int in_graph, int single,
                                                 cudaGraphConditionalHandle h_row,
                                                 cudaGraphConditionalHandle h_dirty,
                                                 cudaGraphConditionalHandle h_win)
@@ -675,7 +690,7 @@ __global__ void __launch_bounds__(256) k_select(stmf_problem P, int nb_ulf, int 
     stmf_ctl *ctl = P.ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = ctl->nc;
-    for (int c = warp; c < nc; c += 8) {
+    for (int c = warp; c < nc; c += 32) {
         const int type = P.cand[8 * c + 2];
         const int nb = type == 0 ? nb_ulf : nb_urf;
         const double *part = (type == 0 ? P.part_ulf : P.part_urf) + (size_t)c * nb;
@@ -742,8 +757,8 @@ __global__ void __launch_bounds__(256) k_select(stmf_problem P, int nb_ulf, int 
     const int kept = skept;
     if (kept >= 0) {
         const int k = P.cand[8 * kept + 1];
-        for (int s = tid; s < P.m; s += 256) P.U[(size_t)s * P.r + k] = P.Uc[(size_t)kept * P.mp + s];
-        for (int t = tid; t < P.n; t += 256) P.V[(size_t)k * P.np + t] = P.Vc[(size_t)kept * P.np + t];
+        for (int s = tid; s < P.m; s += 1024) P.U[(size_t)s * P.r + k] = P.Uc[(size_t)kept * P.mp + s];
+        for (int t = tid; t < P.n; t += 1024) P.V[(size_t)k * P.np + t] = P.Vc[(size_t)kept * P.np + t];
     }
 }
 
@@ -867,7 +882,7 @@ cudaError_t launch_stats(cudaStream_t st, stmf_problem *P)
 
 cudaError_t launch_window(cudaStream_t st, stmf_problem *P)
 {
-    k_window<<<1, 256, 0, st>>>(*P);
+    k_window<<<1, 1024, 0, st>>>(*P);
     return cudaGetLastError();
 }
 
@@ -891,7 +906,7 @@ cudaError_t launch_eval(cudaStream_t st, stmf_problem *P)
 
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single)
 {
-    k_select<<<1, 256, 0, st>>>(*P, nb_ulf(P), nb_urf(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
+    k_select<<<1, 1024, 0, st>>>(*P, nb_ulf(P), nb_urf(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
     return cudaGetLastError();
 }
 
