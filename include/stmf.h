@@ -135,6 +135,27 @@ stmf_status stmf_selection_stats(stmf_ctx *ctx, int m, int n, int r,
                                  const float *U, int ldu, const float *V, int ldv,
                                  double *td_col, int32_t *colhist, double *f_host);
 
+/* stmf_selection_stats without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * when they call (a process whose device-memory budget is fixed at start-up,
+ * or a loop that cannot pay for cudaMalloc's synchronisation).  Arguments,
+ * layouts and results are those of stmf_selection_stats.  Its scratch is one
+ * file-scope device array of STMF_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * the library holds until the process exits; a problem needs
+ *   8 * (ceil(m/128) * n + n + 1) + 4 * ceil(m/128) * n * r  bytes,
+ * and larger problems are rejected with STMF_ERR_INVALID (nothing launched).
+ * The first call made for a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race; serialise them.  Nothing in the array needs clearing between calls. */
+#define STMF_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+stmf_status stmf_selection_stats_noalloc(stmf_ctx *ctx, int m, int n, int r,
+                                         const float *R, int ldr, const uint32_t *mask, int ldm_words,
+                                         const float *U, int ldu, const float *V, int ldv,
+                                         double *td_col, int32_t *colhist, double *f_host);
+
 /* A problem: a copy of R (m x n, not transposed, not permuted) and its mask,
  * the factors U, V and the device state F-ULF / F-URF need.  U0 (device,
  * m x r, ld r) may be NULL: then U comes from Random Acol with opts->seed

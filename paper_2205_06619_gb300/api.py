@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "INTERNAL
 EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", "stmf_maxplus",
            "stmf_selection_stats", "stmf_problem_create", "stmf_problem_destroy", "stmf_update_U",
            "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_factorize_begin",
-           "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_peak_addmax"]
+           "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_peak_addmax",
+           "stmf_selection_stats_noalloc"]
 
 
 class StmfError(RuntimeError):
@@ -73,6 +74,7 @@ def load(build_if_missing: bool = True):
     L.stmf_set_stream.argtypes = [P, P]
     L.stmf_maxplus.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, i, P]
     L.stmf_selection_stats.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, P, C.POINTER(d)]
+    L.stmf_selection_stats_noalloc.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, P, C.POINTER(d)]
     L.stmf_problem_create.argtypes = [P, i, i, i, P, i, P, i, P, C.POINTER(Options), C.POINTER(P)]
     L.stmf_problem_destroy.argtypes = [P]
     L.stmf_problem_destroy.restype = None
@@ -209,6 +211,26 @@ def selection_stats(R, U, V, mask_words=None):
     ctx.check(load().stmf_selection_stats(ctx.h, m, n, r, _ptr(R), R.stride(0), _ptr(mask_words), ldm,
                                           _ptr(U), U.stride(0), _ptr(V), V.stride(0), _ptr(td), _ptr(ch),
                                           C.byref(f)))
+    return td, ch, f.value
+
+
+def selection_stats_noalloc(R, U, V, mask_words=None, td_col=None, colhist=None):
+    """Same results as :func:`selection_stats`, computed without any device
+    allocation inside the library (its scratch is a fixed static array; see
+    stmf_selection_stats_noalloc in include/stmf.h).  Output tensors may be
+    passed in so that this call allocates nothing either."""
+    torch = _torch()
+    _check_f32(R, "R"); _check_f32(U, "U"); _check_f32(V, "V")
+    m, n = R.shape
+    r = U.shape[1]
+    ctx = context()
+    td = td_col if td_col is not None else torch.empty(n, device=R.device, dtype=torch.float64)
+    ch = colhist if colhist is not None else torch.empty((n, r), device=R.device, dtype=torch.int32)
+    f = C.c_double()
+    ldm = mask_words.shape[1] if mask_words is not None else 0
+    ctx.check(load().stmf_selection_stats_noalloc(ctx.h, m, n, r, _ptr(R), R.stride(0), _ptr(mask_words), ldm,
+                                                  _ptr(U), U.stride(0), _ptr(V), V.stride(0), _ptr(td), _ptr(ch),
+                                                  C.byref(f)))
     return td, ch, f.value
 
 
