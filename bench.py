@@ -49,6 +49,19 @@ FP32_LANES = 128
 # plain FP32 ALU issue peak for a 1:1 FADD/FMNMX stream: every SM issues 128
 # lane operations per cycle at the maximum clock
 ALU_PEAK_TOPS = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM bytes (read + write) per k_eval launch from the ncu capture summarised in
+# profiles/k_eval_gene_1000x5000_r10.md (cold cache, gene workload); valid only
+# for the kernel source it was taken on
+EVAL_TRAFFIC = {"source_sha256_prefix": "3ec2fe87cea8704f", "bytes": 91.86e6, "workload": "gene"}
+
+
+def eval_traffic(workload_name):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2205_06619_gb300", "csrc", "kernels_update.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != EVAL_TRAFFIC["source_sha256_prefix"] or workload_name != EVAL_TRAFFIC["workload"]:
+        return None
+    return EVAL_TRAFFIC["bytes"]
 
 
 def workload(name, seed):
@@ -311,7 +324,8 @@ def main():
         "candidates_tried_per_sweep": d_tried / args.steps,
         "roofline": {"kernel": "k_eval (window of F-ULF/F-URF candidates)", "bound": "alu",
                      "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
-                     "frac": achieved / ALU_PEAK_TOPS if achieved else None, "traffic": None,
+                     "frac": achieved / ALU_PEAK_TOPS if achieved else None,
+                     "traffic": eval_traffic(args.workload), "traffic_unit": "bytes per launch",
                      "launches": d_eval_n, "avg_launch_us": d_eval_ns / 1e3 / max(d_eval_n, 1),
                      "candidates_per_launch": d_eval_c / max(d_eval_n, 1),
                      "timing": "per-launch device time from %globaltimer (kernel runs inside a CUDA graph)"},
