@@ -213,6 +213,34 @@ stmf_status stmf_factorize_run(stmf_problem *prob, int sweeps, double eps, stmf_
 stmf_status stmf_factorize_end(stmf_problem *prob, float *U_out, float *V_out,
                                int32_t *trace, int64_t trace_cap);
 
+/* One problem of a batch (all pointers device memory, caller orientation). */
+typedef struct {
+    int m, n, r;                 /* shape and rank                                   */
+    const float *R;              /* m x n, ld ldr                                    */
+    int ldr;
+    const uint32_t *mask;        /* bit-packed, nullable                             */
+    int ldm_words;
+    float *U_out;                /* m x r, ld r                                      */
+    float *V_out;                /* r x n, ld n                                      */
+    uint64_t seed;               /* draws its permutation and Acol picks             */
+    int sweeps;                  /* sweeps of this problem                           */
+} stmf_batch_problem;
+
+/* Many independent FastSTMF problems (Algorithm 3 each) of uneven size and
+ * rank in ONE device launch: the whole job -- every problem's sweeps, rows,
+ * windows, refreshes and convergence tests -- is one CUDA graph whose
+ * branches (one per problem, each a device-driven loop of conditional nodes)
+ * run concurrently.  Decisions, factors and errors are exactly those of
+ * stmf_factorize on each problem with the same options.  opts (nullable):
+ * eps, select and window apply to every problem; window == 0 lets the
+ * library's autotuner pick each problem's window from one timed sweep per size
+ * class on scratch copies (cached in ctx).  reports (host, nprob entries) and
+ * tuned_windows (host, nprob ints) are nullable.  Set-up (allocation,
+ * initialisation) runs before the launch; report[i].seconds is the wall time
+ * of the single launch. */
+stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs,
+                                   const stmf_options *opts, stmf_report *reports, int *tuned_windows);
+
 /* Fills *opts with the defaults (sweeps 1, eps 0, library window, first
  * improving, FP32, acol_p 5, seed 0, no explicit draws, no trace). */
 void stmf_default_options(stmf_options *opts);

@@ -24,7 +24,7 @@ EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", 
            "stmf_selection_stats", "stmf_problem_create", "stmf_problem_destroy", "stmf_update_U",
            "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_factorize_begin",
            "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_peak_addmax",
-           "stmf_selection_stats_noalloc"]
+           "stmf_selection_stats_noalloc", "stmf_factorize_batched"]
 
 
 class StmfError(RuntimeError):
@@ -38,6 +38,12 @@ class Options(C.Structure):
                 ("precision", C.c_int), ("acol_p", C.c_int), ("seed", C.c_uint64),
                 ("perm", C.c_void_p), ("picks", C.c_void_p), ("U0", C.c_void_p),
                 ("trace", C.c_void_p), ("trace_cap", C.c_int64)]
+
+
+class BatchProblem(C.Structure):
+    _fields_ = [("m", C.c_int), ("n", C.c_int), ("r", C.c_int), ("R", C.c_void_p), ("ldr", C.c_int),
+                ("mask", C.c_void_p), ("ldm_words", C.c_int), ("U_out", C.c_void_p), ("V_out", C.c_void_p),
+                ("seed", C.c_uint64), ("sweeps", C.c_int)]
 
 
 class Report(C.Structure):
@@ -85,6 +91,8 @@ def load(build_if_missing: bool = True):
     L.stmf_factorize_begin.argtypes = [P, i, i, i, P, i, P, i, C.POINTER(Options), C.POINTER(P)]
     L.stmf_factorize_run.argtypes = [P, i, d, C.POINTER(Report)]
     L.stmf_factorize_end.argtypes = [P, P, P, P, C.c_int64]
+    L.stmf_factorize_batched.argtypes = [P, i, C.POINTER(BatchProblem), C.POINTER(Options), C.POINTER(Report),
+                                         C.POINTER(i)]
     L.stmf_default_options.argtypes = [C.POINTER(Options)]
     L.stmf_default_options.restype = None
     L.stmf_peak_addmax.argtypes = [P, i, i, C.POINTER(d)]
@@ -331,6 +339,36 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     if trace is not None:
         tr = decode_trace(trace[:min(trace_cap, rep.trace_records)])
     return U, V, rep.as_dict(), tr
+
+
+def factorize_batched(problems, window=0, select=0, eps=0.0):
+    """Many independent problems in one device launch (stmf_factorize_batched).
+
+    problems: list of dicts with R (float32 CUDA m x n), mask_words (or None),
+    rank, sweeps, seed.  window=0 lets the library's autotuner choose each
+    problem's window.  Returns (list of (U, V, report dict), tuned windows)."""
+    torch = _torch()
+    ctx = context()
+    n = len(problems)
+    arr = (BatchProblem * max(n, 1))()
+    outs = []
+    for q, pr in enumerate(problems):
+        R = pr["R"]
+        _check_f32(R, "R")
+        m, nn = R.shape
+        r = pr["rank"]
+        U = torch.empty((m, r), device=R.device, dtype=torch.float32)
+        V = torch.empty((r, nn), device=R.device, dtype=torch.float32)
+        mw = pr.get("mask_words")
+        arr[q] = BatchProblem(m, nn, r, R.data_ptr(), R.stride(0), 0 if mw is None else mw.data_ptr(),
+                              0 if mw is None else mw.shape[1], U.data_ptr(), V.data_ptr(), pr.get("seed", 0),
+                              pr.get("sweeps", 1))
+        outs.append((U, V))
+    o, keep = _options(0, eps, window, select)
+    reps = (Report * max(n, 1))()
+    tuned = (C.c_int * max(n, 1))()
+    ctx.check(load().stmf_factorize_batched(ctx.h, n, arr, C.byref(o), reps, tuned))
+    return [(U, V, reps[q].as_dict()) for q, (U, V) in enumerate(outs)], [tuned[q] for q in range(n)]
 
 
 class Factorization:

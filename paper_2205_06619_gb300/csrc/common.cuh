@@ -29,6 +29,7 @@ struct stmf_ctx {
     char err[512];
     void *ws;          // workspace for stmf_selection_stats
     size_t ws_bytes;
+    void *tune;        // autotuner cache (std::map of size class -> window), owned
 };
 
 // Control block in device memory.  The kernels of the row loop read and
@@ -65,6 +66,9 @@ struct stmf_ctl {
     long long eval_ns;                 // summed durations of the window evaluations (%globaltimer)
     long long eval_launches;
     long long eval_cands;              // candidates those evaluations covered
+    int sweep_target;  // sweeps of a device-driven job (batched form)
+    double eps;        // convergence threshold of a device-driven job (0: off)
+    double f_prev;     // error at the start of the current sweep
     double f;          // current error (sum over j of td_col[j])
     double f_new;      // error after the kept candidate (f + Delta)
     int32_t *trace;    // device trace buffer (STMF_TRACE_INTS per record) or NULL
@@ -106,6 +110,7 @@ struct stmf_problem {
     cudaGraphExec_t sweep_exec;
     cudaGraph_t sweep_graph;
     unsigned long long h_row, h_dirty, h_win;   // cudaGraphConditionalHandle values
+    unsigned long long h_sweep;                 // sweep loop of a device-driven job
 };
 
 // ---------------------------------------------------------------- launchers
@@ -144,6 +149,8 @@ cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k,
 cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph);
 cudaError_t launch_sweep_begin(cudaStream_t st, stmf_problem *P, int in_graph);
+cudaError_t launch_job_begin(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_sweep_end(cudaStream_t st, stmf_problem *P);
 
 // peak.cu
 cudaError_t launch_peak(cudaStream_t st, int mode, int iters, int blocks, float *sink);

@@ -788,6 +788,27 @@ __global__ void k_sweep_begin(stmf_problem P, int in_graph, cudaGraphConditional
     }
 }
 
+// Device-driven job (batched form): opens the sweep loop.
+__global__ void k_job_begin(stmf_problem P, cudaGraphConditionalHandle h_sweep)
+{
+    stmf_ctl *ctl = P.ctl;
+    ctl->f_prev = ctl->f;
+    cudaGraphSetConditional(h_sweep, ctl->sweep < ctl->sweep_target ? 1u : 0u);
+}
+
+// End of a sweep of a device-driven job: next sweep unless the target is
+// reached or (eps > 0) the sweep changed the error by less than eps
+// (convergence rule of Section "Comparison of strategies").
+__global__ void k_sweep_end(stmf_problem P, cudaGraphConditionalHandle h_sweep)
+{
+    stmf_ctl *ctl = P.ctl;
+    ctl->sweep += 1;
+    const double d = ctl->f_prev - ctl->f;
+    const bool converged = ctl->eps > 0.0 && d < ctl->eps && -d < ctl->eps;
+    ctl->f_prev = ctl->f;
+    cudaGraphSetConditional(h_sweep, (ctl->sweep < ctl->sweep_target && !converged) ? 1u : 0u);
+}
+
 // One explicit candidate (stmf_update_U / stmf_update_V): slot 0.
 __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
 {
@@ -925,6 +946,18 @@ cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P)
 cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph)
 {
     k_row_begin<<<1, 1, 0, st>>>(*P, in_graph, P->h_win);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_job_begin(cudaStream_t st, stmf_problem *P)
+{
+    k_job_begin<<<1, 1, 0, st>>>(*P, P->h_sweep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_end(cudaStream_t st, stmf_problem *P)
+{
+    k_sweep_end<<<1, 1, 0, st>>>(*P, P->h_sweep);
     return cudaGetLastError();
 }
 

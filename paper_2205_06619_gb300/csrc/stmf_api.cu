@@ -6,6 +6,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <chrono>
+#include <cmath>
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -262,12 +264,105 @@ stmf_status update(stmf_problem *P, int i, int j, int k, int type, int commit_if
     return STMF_OK;
 }
 
-// The sweep as one graph: sweep_begin, then
+// Captures `launch` into graph g after the nodes deps (nullable), and returns
+// the node(s) the capture ended with (exactly one for one kernel).
+template <class Launch>
+stmf_status capture_into(stmf_ctx *ctx, cudaStream_t cap, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                         Launch launch, cudaGraphNode_t *last)
+{
+    CK(cudaStreamBeginCaptureToGraph(cap, g, deps, nullptr, ndeps, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch(cap);
+    if (e != cudaSuccess) {
+        cudaGraph_t tmp;
+        cudaStreamEndCapture(cap, &tmp);
+        return fail(ctx, STMF_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+    }
+    if (last) {
+        cudaStreamCaptureStatus stat;
+        const cudaGraphNode_t *dep = nullptr;
+        size_t nd = 0;
+        CK(cudaStreamGetCaptureInfo(cap, &stat, nullptr, nullptr, &dep, nullptr, &nd));
+        if (nd != 1) return fail(ctx, STMF_ERR_INTERNAL, "capture ended with %zu nodes", nd);
+        *last = dep[0];
+    }
+    cudaGraph_t tmp;
+    CK(cudaStreamEndCapture(cap, &tmp));
+    return STMF_OK;
+}
+
+stmf_status add_conditional(stmf_ctx *ctx, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                            cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, cudaGraphNode_t *node,
+                            cudaGraph_t *body)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    CK(cudaGraphAddNode(node, g, deps, nullptr, ndeps, &p));
+    *body = p.conditional.phGraph_out[0];
+    return STMF_OK;
+}
+
+#define CS(call)                            \
+    do {                                    \
+        stmf_status s_ = (call);            \
+        if (s_ != STMF_OK) return s_;       \
+    } while (0)
+
+// Adds one problem's row loop to graph g (its conditional handles are created
+// on `top`, the graph that will be instantiated):
+//   sweep_begin;
 //   while (h_row) {
 //     if (h_dirty) { stats(k), planes, td_col/colhist, rank, order + f }
-//     row_begin
+//     row_begin;
 //     while (h_win) { window, seed, eval, select }
 //   }
+// With job = true the row loop is wrapped in a device-driven sweep loop:
+//   job_begin; while (h_sweep) { <row loop>; sweep_end }
+stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, bool job, cudaStream_t cap)
+{
+    stmf_ctx *ctx = P->ctx;
+    cudaGraphConditionalHandle hr, hd, hw, hs = 0;
+    CK(cudaGraphConditionalHandleCreate(&hr, top, 0, 0));
+    CK(cudaGraphConditionalHandleCreate(&hd, top, 0, 0));
+    CK(cudaGraphConditionalHandleCreate(&hw, top, 0, 0));
+    if (job) CK(cudaGraphConditionalHandleCreate(&hs, top, 0, 0));
+    P->h_row = hr; P->h_dirty = hd; P->h_win = hw; P->h_sweep = hs;
+
+    cudaGraph_t target = g;
+    if (job) {
+        cudaGraphNode_t jb, wsw;
+        CS(capture_into(ctx, cap, g, nullptr, 0, [&](cudaStream_t c) { return launch_job_begin(c, P); }, &jb));
+        CS(add_conditional(ctx, g, &jb, 1, hs, cudaGraphCondTypeWhile, &wsw, &target));
+    }
+    cudaGraphNode_t sb, wrow;
+    CS(capture_into(ctx, cap, target, nullptr, 0, [&](cudaStream_t c) { return launch_sweep_begin(c, P, 1); }, &sb));
+    cudaGraph_t body_row;
+    CS(add_conditional(ctx, target, &sb, 1, hr, cudaGraphCondTypeWhile, &wrow, &body_row));
+    if (job)
+        CS(capture_into(ctx, cap, target, &wrow, 1, [&](cudaStream_t c) { return launch_sweep_end(c, P); }, nullptr));
+
+    cudaGraphNode_t nif, rb, wwin;
+    cudaGraph_t body_ref, body_win;
+    CS(add_conditional(ctx, body_row, nullptr, 0, hd, cudaGraphCondTypeIf, &nif, &body_ref));
+    CS(capture_into(ctx, cap, body_ref, nullptr, 0, [&](cudaStream_t c) {
+        cudaError_t e = launch_stats(c, P);
+        return e != cudaSuccess ? e : launch_refresh_planes(c, P);
+    }, nullptr));
+    CS(capture_into(ctx, cap, body_row, &nif, 1, [&](cudaStream_t c) { return launch_row_begin(c, P, 1); }, &rb));
+    CS(add_conditional(ctx, body_row, &rb, 1, hw, cudaGraphCondTypeWhile, &wwin, &body_win));
+    CS(capture_into(ctx, cap, body_win, nullptr, 0, [&](cudaStream_t c) {
+        cudaError_t e = launch_window(c, P);
+        if (e == cudaSuccess) e = launch_seed(c, P, P->ctl_host->wmax);
+        if (e == cudaSuccess) e = launch_eval(c, P);
+        if (e == cudaSuccess) e = launch_select(c, P, 1, 0);
+        return e;
+    }, nullptr));
+    return STMF_OK;
+}
+
+// The sweep of one problem as one graph (the host loops over sweeps).
 stmf_status build_sweep_graph(stmf_problem *P)
 {
     stmf_ctx *ctx = P->ctx;
@@ -277,72 +372,7 @@ stmf_status build_sweep_graph(stmf_problem *P)
     cudaGraph_t g;
     CK(cudaGraphCreate(&g, 0));
     P->sweep_graph = g;
-    cudaGraphConditionalHandle hr, hd, hw;
-    CK(cudaGraphConditionalHandleCreate(&hr, g, 0, 0));
-    CK(cudaGraphConditionalHandleCreate(&hd, g, 0, 0));
-    CK(cudaGraphConditionalHandleCreate(&hw, g, 0, 0));
-    P->h_row = hr; P->h_dirty = hd; P->h_win = hw;
-    const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
-
-    cudaGraph_t tmp;
-    CK(cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, mode));
-    CK(launch_sweep_begin(cap, P, 1));
-    CK(cudaStreamEndCapture(cap, &tmp));
-    cudaGraphNode_t sb;
-    size_t count = 1;
-    CK(cudaGraphGetNodes(g, &sb, &count));
-
-    cudaGraphNodeParams wp = {};
-    wp.type = cudaGraphNodeTypeConditional;
-    wp.conditional.handle = hr;
-    wp.conditional.type = cudaGraphCondTypeWhile;
-    wp.conditional.size = 1;
-    cudaGraphNode_t wrow;
-    CK(cudaGraphAddNode(&wrow, g, &sb, nullptr, 1, &wp));
-    cudaGraph_t body_row = wp.conditional.phGraph_out[0];
-
-    cudaGraphNodeParams ip = {};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = hd;
-    ip.conditional.type = cudaGraphCondTypeIf;
-    ip.conditional.size = 1;
-    cudaGraphNode_t nif;
-    CK(cudaGraphAddNode(&nif, body_row, nullptr, nullptr, 0, &ip));
-    cudaGraph_t body_ref = ip.conditional.phGraph_out[0];
-    CK(cudaStreamBeginCaptureToGraph(cap, body_ref, nullptr, nullptr, 0, mode));
-    CK(launch_stats(cap, P));
-    CK(launch_refresh_planes(cap, P));
-    CK(cudaStreamEndCapture(cap, &tmp));
-
-    CK(cudaStreamBeginCaptureToGraph(cap, body_row, &nif, nullptr, 1, mode));
-    CK(launch_row_begin(cap, P, 1));
-    CK(cudaStreamEndCapture(cap, &tmp));
-    cudaGraphNode_t nodes[4];
-    count = 4;
-    CK(cudaGraphGetNodes(body_row, nodes, &count));
-    cudaGraphNode_t rb = nullptr;
-    for (size_t q = 0; q < count; ++q) {
-        cudaGraphNodeType t;
-        CK(cudaGraphNodeGetType(nodes[q], &t));
-        if (t == cudaGraphNodeTypeKernel) rb = nodes[q];
-    }
-    if (!rb) return fail(ctx, STMF_ERR_INTERNAL, "row-begin node not found in the sweep graph");
-
-    cudaGraphNodeParams wp2 = {};
-    wp2.type = cudaGraphNodeTypeConditional;
-    wp2.conditional.handle = hw;
-    wp2.conditional.type = cudaGraphCondTypeWhile;
-    wp2.conditional.size = 1;
-    cudaGraphNode_t wwin;
-    CK(cudaGraphAddNode(&wwin, body_row, &rb, nullptr, 1, &wp2));
-    cudaGraph_t body_win = wp2.conditional.phGraph_out[0];
-    CK(cudaStreamBeginCaptureToGraph(cap, body_win, nullptr, nullptr, 0, mode));
-    CK(launch_window(cap, P));
-    CK(launch_seed(cap, P, P->ctl_host->wmax));
-    CK(launch_eval(cap, P));
-    CK(launch_select(cap, P, 1, 0));
-    CK(cudaStreamEndCapture(cap, &tmp));
-
+    CS(add_problem_nodes(P, g, g, false, cap));
     CK(cudaGraphInstantiate(&P->sweep_exec, g, 0));
     return STMF_OK;
 }
@@ -519,6 +549,142 @@ stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *tra
     return STMF_OK;
 }
 
+// ------------------------------------------------------------ autotuner
+// Picks the candidate window (candidates evaluated per device pass) of a
+// problem size class.  Each trial runs the first rows of sweep 0 on a scratch
+// copy of the problem, host-driven, and is scored by its device time: the
+// window evaluations' summed durations plus a fixed cost per window for the
+// window, seed and select kernels and the graph step.  Decisions do not depend
+// on the window, so only speed is compared.
+constexpr double TUNE_WINDOW_OVERHEAD_S = 12e-6;
+
+stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, int ldr, const uint32_t *mask,
+                         int ldm_words, const stmf_options *opts, stmf_problem **out);
+stmf_status sweep_rows_host(stmf_problem *P, int rows);
+
+uint64_t size_class(int m, int n, int r)
+{
+    const int mo = m < n ? m : n, no = m < n ? n : m;
+    const double e = (double)stmf_roundup(mo, STMF_PAD) * stmf_roundup(no, STMF_PAD);
+    const int lg = (int)std::floor(std::log2(e));
+    return ((uint64_t)lg << 8) | (uint64_t)r;
+}
+
+stmf_status tune_window(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_options &base, int *best)
+{
+    auto *cache = static_cast<std::map<uint64_t, int> *>(ctx->tune);
+    if (!cache) ctx->tune = cache = new std::map<uint64_t, int>();
+    const uint64_t key = size_class(bp.m, bp.n, bp.r);
+    auto it = cache->find(key);
+    if (it != cache->end()) { *best = it->second; return STMF_OK; }
+    const int trial[3] = {16, 32, 64};
+    double best_cost = 1e30;
+    int best_w = 64;
+    for (int w : trial) {
+        stmf_options o = base;
+        o.window = w; o.trace = nullptr; o.trace_cap = 0; o.perm = nullptr; o.picks = nullptr; o.U0 = nullptr;
+        o.seed = bp.seed;
+        stmf_problem *P = nullptr;
+        CS(fastmf_begin(ctx, bp.m, bp.n, bp.r, bp.R, bp.ldr, bp.mask, bp.ldm_words, &o, &P));
+        stmf_status s = sweep_rows_host(P, 24);
+        if (s == STMF_OK) s = read_ctl(P);
+        if (s != STMF_OK) { problem_free(P); return s; }
+        const double cost = P->ctl_host->eval_ns * 1e-9 + P->ctl_host->windows * TUNE_WINDOW_OVERHEAD_S;
+        problem_free(P);
+        if (cost < best_cost) { best_cost = cost; best_w = w; }
+    }
+    (*cache)[key] = best_w;
+    *best = best_w;
+    return STMF_OK;
+}
+
+// Rows 0..rows-1 of sweep 0, host-driven (used by the autotuner).
+stmf_status sweep_rows_host(stmf_problem *P, int rows)
+{
+    stmf_ctx *ctx = P->ctx;
+    cudaStream_t st = ctx->stream;
+    CK(launch_sweep_begin(st, P, 0));
+    stmf_status s = read_ctl(P);
+    if (s != STMF_OK) return s;
+    const int nr = rows < P->m ? rows : P->m;
+    for (int i = 0; i < nr; ++i) {
+        if (P->ctl_host->dirty_k != -2) CS(refresh(P));
+        CK(launch_row_begin(st, P, 0));
+        while (true) {
+            CK(launch_window(st, P));
+            CK(launch_seed(st, P, P->ctl_host->wmax));
+            CK(launch_eval(st, P));
+            CK(launch_select(st, P, 0, 0));
+            CS(read_ctl(P));
+            if (P->ctl_host->row_done) break;
+        }
+    }
+    return STMF_OK;
+}
+
+// ------------------------------------------------------------ batched form
+stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, const stmf_options *opts,
+                    stmf_report *reports, int *tuned)
+{
+    stmf_options o;
+    if (opts) o = *opts; else stmf_default_options(&o);
+    if (o.precision != 0) return fail(ctx, STMF_ERR_INVALID, "precision mode %d is not available", o.precision);
+    if (o.window < 0 || o.window > STMF_WMAX) return fail(ctx, STMF_ERR_INVALID, "window outside [0, %d]", STMF_WMAX);
+    for (int q = 0; q < nprob; ++q) {
+        const stmf_batch_problem &b = probs[q];
+        CS(check_common(ctx, b.m, b.n, b.r));
+        if (!b.R || !b.U_out || !b.V_out) return fail(ctx, STMF_ERR_INVALID, "problem %d: R, U_out, V_out required", q);
+        if (b.ldr < b.n) return fail(ctx, STMF_ERR_INVALID, "problem %d: ldr < n", q);
+        if (b.mask && b.ldm_words < (b.n + 31) / 32) return fail(ctx, STMF_ERR_INVALID, "problem %d: ldm_words", q);
+        if (b.sweeps < 0) return fail(ctx, STMF_ERR_INVALID, "problem %d: sweeps < 0", q);
+    }
+    std::vector<int> win(nprob, o.window ? (o.window + 1) / 2 * 2 : 0);
+    if (!o.window)
+        for (int q = 0; q < nprob; ++q) CS(tune_window(ctx, probs[q], o, &win[q]));
+    if (tuned)
+        for (int q = 0; q < nprob; ++q) tuned[q] = win[q];
+
+    std::vector<stmf_problem *> Ps(nprob, nullptr);
+    struct Free { std::vector<stmf_problem *> &v; ~Free() { for (auto *p : v) problem_free(p); } } fr{Ps};
+    for (int q = 0; q < nprob; ++q) {
+        const stmf_batch_problem &b = probs[q];
+        stmf_options po = o;
+        po.window = win[q]; po.seed = b.seed; po.perm = nullptr; po.picks = nullptr; po.U0 = nullptr;
+        po.trace = nullptr; po.trace_cap = 0;
+        CS(fastmf_begin(ctx, b.m, b.n, b.r, b.R, b.ldr, b.mask, b.ldm_words, &po, &Ps[q]));
+        CK(set_ctl(Ps[q], &stmf_ctl::sweep_target, b.sweeps));
+        CK(set_ctl(Ps[q], &stmf_ctl::eps, o.eps));
+        CK(set_ctl(Ps[q], &stmf_ctl::sweep, 0));
+    }
+    // one graph: one independent device-driven job per problem
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{cap};
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    struct GG { cudaGraph_t g; cudaGraphExec_t x = nullptr; ~GG() { if (x) cudaGraphExecDestroy(x); cudaGraphDestroy(g); } } gg{g};
+    for (int q = 0; q < nprob; ++q) CS(add_problem_nodes(Ps[q], g, g, true, cap));
+    CK(cudaGraphInstantiate(&gg.x, g, 0));
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));
+    auto t0 = std::chrono::steady_clock::now();
+    CK(cudaGraphLaunch(gg.x, st));
+    CK(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int q = 0; q < nprob; ++q) {
+        stmf_problem *P = Ps[q];
+        CS(read_ctl(P));
+        if (P->ctl_host->err) return fail(ctx, STMF_ERR_INTERNAL, "problem %d: device error %d", q, P->ctl_host->err);
+        if (P->ctl_host->dirty_k != -2) { CS(refresh(P)); CS(read_ctl(P)); }
+        P->sweeps_done = P->ctl_host->sweep;
+        P->seconds = secs;
+        CK(launch_unorient(st, P, P->transposed, P->perm, probs[q].U_out, probs[q].V_out));
+        if (reports) fill_report(P, &reports[q]);
+    }
+    CK(cudaStreamSynchronize(st));
+    return STMF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -555,6 +721,7 @@ void stmf_destroy(stmf_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->ws) cudaFree(ctx->ws);
+    delete static_cast<std::map<uint64_t, int> *>(ctx->tune);
     delete ctx;
 }
 
@@ -721,6 +888,15 @@ stmf_status stmf_factorize(stmf_ctx *ctx, int m0, int n0, int r, const float *R,
     if (s == STMF_OK) fill_report(P, rep);
     problem_free(P);
     return s;
+}
+
+stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs,
+                                   const stmf_options *opts, stmf_report *reports, int *tuned_windows)
+{
+    if (!ctx) return STMF_ERR_INVALID;
+    if (nprob < 0 || (nprob > 0 && !probs)) return fail(ctx, STMF_ERR_INVALID, "bad problem list");
+    if (nprob == 0) return STMF_OK;
+    return batched(ctx, nprob, probs, opts, reports, tuned_windows);
 }
 
 stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops)
