@@ -241,6 +241,39 @@ typedef struct {
 stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs,
                                    const stmf_options *opts, stmf_report *reports, int *tuned_windows);
 
+/* ---- Learned initialisation of U (a spec addition; the paper uses
+ * Random Acol, Section "Comparison of strategies").  A row of R is summarised
+ * by a 32-quantile sketch of its given entries centred on the row median; an
+ * MLP 32 -> 128 -> 128 -> r (ReLU, BF16 weights, FP32 accumulation) maps the
+ * sketch to the row of U minus its median.  Random Acol stays the fallback. */
+typedef struct stmf_mlp stmf_mlp;
+
+/* sketch[s*32 + q] = v[floor((q+0.5)*c/32)] - median_s and median[s] =
+ * v[floor(c/2)], where v are the c given entries of row s sorted ascending
+ * (nearest-rank quantiles).  R, mask, sketch (m x 32), median (m) device;
+ * n <= 12288. */
+stmf_status stmf_row_sketch(stmf_ctx *ctx, int m, int n, const float *R, int ldr, const uint32_t *mask,
+                            int ldm_words, float *sketch, float *median);
+/* Number of parameters of the MLP for rank r (-1 if r is out of range).
+ * Layout: W1 [32 x 128] | W2 [128 x 128] | W3 [128 x r] | b1 [128] | b2 [128] | b3 [r]
+ * (row-major, input index first). */
+int stmf_mlp_param_count(int r);
+/* Creates an MLP from host FP32 parameters (copied); Adam state zeroed. */
+stmf_status stmf_mlp_create(stmf_ctx *ctx, int r, const float *params_host, stmf_mlp **out);
+void stmf_mlp_destroy(stmf_mlp *mlp);
+/* Copies the FP32 master parameters to host memory. */
+stmf_status stmf_mlp_get_params(stmf_mlp *mlp, float *params_host);
+/* Y (B x r, device) = MLP(X (B x 32, device)), BF16 weights, FP32 accumulation. */
+stmf_status stmf_mlp_forward(stmf_mlp *mlp, int B, const float *X, float *Y);
+/* Mean squared error of MLP(X) against T (B x r, device) and its gradient
+ * with respect to every parameter (loss, grad_host nullable; grad in the
+ * parameter layout).  Every gradient element is a fixed-order FP32 sum. */
+stmf_status stmf_mlp_gradient(stmf_mlp *mlp, int B, const float *X, const float *T, double *loss,
+                              float *grad_host);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the FP32 master parameters
+ * with learning rate lr; loss (host, nullable) receives the batch loss. */
+stmf_status stmf_mlp_train_step(stmf_mlp *mlp, int B, const float *X, const float *T, float lr, double *loss);
+
 /* Fills *opts with the defaults (sweeps 1, eps 0, library window, first
  * improving, FP32, acol_p 5, seed 0, no explicit draws, no trace). */
 void stmf_default_options(stmf_options *opts);

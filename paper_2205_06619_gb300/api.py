@@ -24,7 +24,9 @@ EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", 
            "stmf_selection_stats", "stmf_problem_create", "stmf_problem_destroy", "stmf_update_U",
            "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_factorize_begin",
            "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_peak_addmax",
-           "stmf_selection_stats_noalloc", "stmf_factorize_batched"]
+           "stmf_selection_stats_noalloc", "stmf_factorize_batched", "stmf_row_sketch", "stmf_mlp_param_count",
+           "stmf_mlp_create", "stmf_mlp_destroy", "stmf_mlp_get_params", "stmf_mlp_forward", "stmf_mlp_gradient",
+           "stmf_mlp_train_step"]
 
 
 class StmfError(RuntimeError):
@@ -93,11 +95,21 @@ def load(build_if_missing: bool = True):
     L.stmf_factorize_end.argtypes = [P, P, P, P, C.c_int64]
     L.stmf_factorize_batched.argtypes = [P, i, C.POINTER(BatchProblem), C.POINTER(Options), C.POINTER(Report),
                                          C.POINTER(i)]
+    L.stmf_row_sketch.argtypes = [P, i, i, P, i, P, i, P, P]
+    L.stmf_mlp_param_count.argtypes = [i]
+    L.stmf_mlp_create.argtypes = [P, i, P, C.POINTER(P)]
+    L.stmf_mlp_destroy.argtypes = [P]
+    L.stmf_mlp_destroy.restype = None
+    L.stmf_mlp_get_params.argtypes = [P, P]
+    L.stmf_mlp_forward.argtypes = [P, i, P, P]
+    L.stmf_mlp_gradient.argtypes = [P, i, P, P, C.POINTER(d), P]
+    L.stmf_mlp_train_step.argtypes = [P, i, P, P, C.c_float, C.POINTER(d)]
     L.stmf_default_options.argtypes = [C.POINTER(Options)]
     L.stmf_default_options.restype = None
     L.stmf_peak_addmax.argtypes = [P, i, i, C.POINTER(d)]
     for name in EXPORTS:
-        if name not in ("stmf_destroy", "stmf_last_error", "stmf_problem_destroy", "stmf_default_options"):
+        if name not in ("stmf_destroy", "stmf_last_error", "stmf_problem_destroy", "stmf_default_options",
+                        "stmf_mlp_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -369,6 +381,71 @@ def factorize_batched(problems, window=0, select=0, eps=0.0):
     tuned = (C.c_int * max(n, 1))()
     ctx.check(load().stmf_factorize_batched(ctx.h, n, arr, C.byref(o), reps, tuned))
     return [(U, V, reps[q].as_dict()) for q, (U, V) in enumerate(outs)], [tuned[q] for q in range(n)]
+
+
+def row_sketch(R, mask_words=None):
+    """(sketch m x 32, median m): nearest-rank quantiles of each row's given
+    entries, centred on the row median (stmf_row_sketch)."""
+    torch = _torch()
+    _check_f32(R, "R")
+    m, n = R.shape
+    ctx = context()
+    sk = torch.empty((m, 32), device=R.device, dtype=torch.float32)
+    md = torch.empty(m, device=R.device, dtype=torch.float32)
+    ldm = mask_words.shape[1] if mask_words is not None else 0
+    ctx.check(load().stmf_row_sketch(ctx.h, m, n, _ptr(R), R.stride(0), _ptr(mask_words), ldm, _ptr(sk), _ptr(md)))
+    return sk, md
+
+
+class MLP:
+    """The learned-initialisation network on the device (stmf_mlp_*)."""
+
+    def __init__(self, rank, params):
+        self.ctx = context()
+        self.r = rank
+        self.np = load().stmf_mlp_param_count(rank)
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.np
+        h = C.c_void_p()
+        self.ctx.check(load().stmf_mlp_create(self.ctx.h, rank, p.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().stmf_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(self.np, np.float32)
+        self.ctx.check(load().stmf_mlp_get_params(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def forward(self, X):
+        torch = _torch()
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], self.r), device=X.device, dtype=torch.float32)
+        self.ctx.check(load().stmf_mlp_forward(self.h, X.shape[0], _ptr(X), _ptr(Y)))
+        return Y
+
+    def gradient(self, X, T):
+        g = np.empty(self.np, np.float32)
+        loss = C.c_double()
+        X, T = X.contiguous(), T.contiguous()
+        self.ctx.check(load().stmf_mlp_gradient(self.h, X.shape[0], _ptr(X), _ptr(T), C.byref(loss),
+                                                g.ctypes.data_as(C.c_void_p)))
+        return loss.value, g
+
+    def train_step(self, X, T, lr):
+        loss = C.c_double()
+        self.ctx.check(load().stmf_mlp_train_step(self.h, X.shape[0], _ptr(X), _ptr(T), C.c_float(lr),
+                                                  C.byref(loss)))
+        return loss.value
 
 
 class Factorization:

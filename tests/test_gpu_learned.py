@@ -1,0 +1,72 @@
+"""GPU parity of the learned-initialisation kernels with the FP64 reference:
+row sketch (bit-exact), MLP forward and gradient (BF16 weights, FP32
+accumulation; the reference uses the same BF16-rounded weights)."""
+import numpy as np
+import pytest
+
+from oracle import mlp as om
+from paper_2205_06619_gb300 import learned_init, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(x):
+    """Round float32 values to bfloat16 (round to nearest even), as floats."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _bf16_params(p, r):
+    q = np.asarray(p, dtype=np.float32).copy()
+    nw = om.SK * om.HID + om.HID * om.HID + om.HID * r
+    q[:nw] = _bf16(q[:nw])
+    return q
+
+
+def test_row_sketch_bitexact():
+    from paper_2205_06619_gb300 import api
+    for (m, n, obs, seed) in [(40, 77, 0.6, 1), (17, 5000, 0.8, 2), (9, 33, 0.2, 3)]:
+        R, M, _, _ = synth.lognormal_planted(m, n, 4, 0.05, obs, seed)
+        sk, md = api.row_sketch(torch.from_numpy(R).cuda(), api.pack_mask(M))
+        esk, emd = om.row_sketch(R, M)
+        assert np.array_equal(md.cpu().numpy().astype(np.float64), emd)
+        # sketch = v[idx] - median, subtracted in FP32 on the GPU
+        vals = (esk + emd[:, None]).astype(np.float32)          # the quantile values themselves (exact)
+        exp = vals - emd[:, None].astype(np.float32)            # FP32 subtraction
+        assert np.array_equal(sk.cpu().numpy(), exp)
+
+
+@pytest.mark.parametrize("r,B", [(10, 256), (3, 45), (20, 1)])
+def test_mlp_forward_and_gradient_match_reference(r, B):
+    from paper_2205_06619_gb300 import api
+    rng = np.random.default_rng(r + B)
+    p = learned_init.init_params(r, seed=r)
+    p[-(2 * om.HID + r):] = rng.normal(0, 0.1, size=2 * om.HID + r).astype(np.float32)
+    net = api.MLP(r, p)
+    X = rng.normal(size=(B, om.SK)).astype(np.float32)
+    T = rng.normal(size=(B, r)).astype(np.float32)
+    Xg, Tg = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    pb = _bf16_params(p, r)
+    Y = net.forward(Xg).cpu().numpy()
+    eY, _ = om.forward(pb, X, r)
+    assert np.allclose(Y, eY, rtol=1e-4, atol=1e-4)
+    loss, g = net.gradient(Xg, Tg)
+    eloss, eg = om.loss_and_grad(pb, X, T, r)
+    assert abs(loss - eloss) <= 1e-4 * abs(eloss)
+    assert np.linalg.norm(g - eg) <= 1e-4 * np.linalg.norm(eg)
+
+
+def test_training_reduces_loss_and_init_is_valid():
+    from paper_2205_06619_gb300 import api
+    X, T = learned_init.training_set(count=12, m=60, n=300, rank=10, sweeps=3, seed=0)
+    net, hist = learned_init.train(X, T, rank=10, epochs=15, batch=64, lr=2e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    R, M = learned_init.gene_like(50, 240, seed=99)
+    Rg, Mw = torch.from_numpy(R).cuda(), api.pack_mask(M)
+    U0 = learned_init.predict_U(net, Rg, Mw)
+    assert torch.isfinite(U0).all()
+    perm = np.arange(50, dtype=np.int32)
+    U, V, rep, _ = api.factorize(Rg, Mw, rank=10, sweeps=2, perm=perm, U0=U0)
+    assert rep["f_final"] <= rep["f_init"]
