@@ -249,13 +249,83 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Learned initialisation vs Random Acol: sweeps and time to reach the
+    plain method's final error on fresh matrices (same permutation for both)."""
+    import torch
+    from paper_2205_06619_gb300 import api, learned_init
+    m, n = args.learned_m, args.learned_n
+    T_sweeps = args.learned_sweeps
+    t = time.perf_counter()
+    X, T = learned_init.training_set(args.learned_train, m, n, 10, T_sweeps, seed=args.seed)
+    t_data = time.perf_counter() - t
+    t = time.perf_counter()
+    net, hist = learned_init.train(X, T, 10, epochs=args.learned_epochs, batch=256, lr=1e-3, seed=args.seed)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t
+    rng = np.random.default_rng(args.seed + 12345)
+    rows = []
+    for q in range(args.learned_eval):
+        R, M = learned_init.gene_like(m, n, int(rng.integers(0, 2**31 - 1)))
+        Rg, Mw = torch.from_numpy(R).cuda(), api.pack_mask(M)
+        perm = rng.permutation(min(m, n)).astype(np.int32)
+        seed = int(rng.integers(0, 2**31 - 1))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fz = api.Factorization(Rg, Mw, rank=10, seed=seed, perm=perm)
+        rep = fz.run(T_sweeps)
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t
+        f_target, f0_plain = rep["f_final"], rep["f_init"]
+        fz.close()
+        t = time.perf_counter()
+        U0 = learned_init.predict_U(net, Rg, Mw)
+        U0 = U0[torch.from_numpy(perm.astype(np.int64)).cuda()].contiguous()
+        fz = api.Factorization(Rg, Mw, rank=10, seed=seed, perm=perm, U0=U0)
+        f0_learn = fz.run(0)["f_init"]
+        sw = 0
+        while sw < 2 * T_sweeps:
+            rep = fz.run(1)
+            sw += 1
+            if rep["f_final"] <= f_target:
+                break
+        torch.cuda.synchronize()
+        t_learn = time.perf_counter() - t
+        fz.close()
+        rows.append(dict(f_target=f_target, f0_plain=f0_plain, f0_learned=f0_learn, sweeps_learned=sw,
+                         reached=rep["f_final"] <= f_target, t_plain=t_plain, t_learned=t_learn,
+                         f_learned_end=rep["f_final"]))
+    ok = [r for r in rows if r["reached"]]
+    line = {"metric": METRIC, "value": float(np.mean([r["t_plain"] / r["t_learned"] for r in rows])),
+            "unit": "time-to-equal-error speedup vs Random Acol (mean over matrices)", "n_gpus": 1, "steps": len(rows),
+            "warmup": 0, "higher_is_better": True, "dtype": "f32 (MLP: bf16 weights, f32 accumulation)",
+            "data": "synthetic", "vs_baseline": None, "scaling": "weak",
+            "config": {"workload": "learned init: train on %d method factorizations of %dx%d rank-10 gene-like "
+                                   "matrices (%d sweeps), evaluate on %d fresh ones" %
+                                   (args.learned_train, m, n, T_sweeps, args.learned_eval)},
+            "train": {"samples": int(X.shape[0]), "epochs": args.learned_epochs, "loss_first": hist[0],
+                      "loss_last": hist[-1], "data_seconds": t_data, "train_seconds": t_train},
+            "reached_fraction": len(ok) / len(rows),
+            "sweeps_to_equal_error_learned_mean": float(np.mean([r["sweeps_learned"] for r in rows])),
+            "sweeps_plain": T_sweeps,
+            "init_error_ratio_mean": float(np.mean([r["f0_learned"] / r["f0_plain"] for r in rows])),
+            "per_matrix": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5, help="timed sweeps")
     ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up sweeps")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gene", choices=["gene", "small", "large", "batch"])
+    ap.add_argument("--workload", default="gene", choices=["gene", "small", "large", "batch", "learned"])
+    ap.add_argument("--learned-train", type=int, default=200)
+    ap.add_argument("--learned-eval", type=int, default=16)
+    ap.add_argument("--learned-m", type=int, default=200)
+    ap.add_argument("--learned-n", type=int, default=1000)
+    ap.add_argument("--learned-sweeps", type=int, default=10)
+    ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--batch-scale", type=float, default=0.25, help="size scale of the batch workload")
     ap.add_argument("--seed", type=int, default=0)
@@ -270,6 +340,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "learned":
+        run_learned(args)
         return
 
     import torch
