@@ -65,7 +65,13 @@ typedef struct {
                             0 = library default.  Never changes which update is kept. */
     int select;          /* 0 = keep the first improving candidate in the paper's order
                             (default, Algorithm 3); 1 = keep the best of the window    */
-    int precision;       /* 0 = FP32 (default); 1 = FP16 screening + FP32 re-check     */
+    int precision;       /* 0 = FP32 (default); 1 = FP16 screening + FP32 re-check:
+                            each window's candidates are first evaluated in packed
+                            half2 arithmetic; a candidate is dropped only when a
+                            rigorous error bound proves its FP32 change >= 0, and the
+                            others are re-evaluated in FP32 in the paper's order, so
+                            the kept updates are those of precision 0.  Extra device
+                            memory: three mp x np half planes.                        */
     int acol_p;          /* Random Acol: columns averaged per component; 0 = 5 (clamped to n) */
     uint64_t seed;       /* draws the row permutation and the Acol picks (SplitMix64)  */
     const int32_t *perm;  /* HOST, nullable: explicit row permutation of the oriented R
@@ -99,6 +105,8 @@ typedef struct {
     int64_t eval_launches;    /* window evaluations timed                            */
     int64_t eval_candidates;  /* candidates those evaluations covered                */
     double seconds;           /* wall time of the sweep loop                         */
+    int64_t candidates_screened; /* candidates the FP16 screen proved non-improving
+                                    (precision 1; counted in candidates_issued)   */
 } stmf_report;
 
 /* Context: binds a device and a stream (cudaStream_t passed as void*; NULL =

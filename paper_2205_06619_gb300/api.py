@@ -53,7 +53,8 @@ class Report(C.Structure):
                 ("transposed", C.c_int), ("candidates_tried", C.c_int64),
                 ("candidates_issued", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
                 ("windows", C.c_int64), ("trace_records", C.c_int64), ("eval_ns", C.c_int64),
-                ("eval_launches", C.c_int64), ("eval_candidates", C.c_int64), ("seconds", C.c_double)]
+                ("eval_launches", C.c_int64), ("eval_candidates", C.c_int64), ("seconds", C.c_double),
+                ("candidates_screened", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -353,7 +354,7 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     return U, V, rep.as_dict(), tr
 
 
-def factorize_batched(problems, window=0, select=0, eps=0.0):
+def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0):
     """Many independent problems in one device launch (stmf_factorize_batched).
 
     problems: list of dicts with R (float32 CUDA m x n), mask_words (or None),
@@ -376,7 +377,7 @@ def factorize_batched(problems, window=0, select=0, eps=0.0):
                               0 if mw is None else mw.shape[1], U.data_ptr(), V.data_ptr(), pr.get("seed", 0),
                               pr.get("sweeps", 1))
         outs.append((U, V))
-    o, keep = _options(0, eps, window, select)
+    o, keep = _options(0, eps, window, select, precision)
     reps = (Report * max(n, 1))()
     tuned = (C.c_int * max(n, 1))()
     ctx.check(load().stmf_factorize_batched(ctx.h, n, arr, C.byref(o), reps, tuned))

@@ -11,7 +11,10 @@
 //   U    mp x r   row-major (rows >= m are 0).
 //   V    r x np   row-major (columns >= n are 0).
 //   P1, P2 mp x np fp32, A mp x np uint8: top-2 planes of U (x) V.
+//   Rh, P1h, P2h mp x np fp16 (precision 1 only): R, P1, P2 rounded to
+//                 nearest half at given entries, a quiet NaN elsewhere.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,6 +76,10 @@ struct stmf_ctl {
     double f_new;      // error after the kept candidate (f + Delta)
     int32_t *trace;    // device trace buffer (STMF_TRACE_INTS per record) or NULL
     long long trace_cap, ntrace;
+    // FP16 screening (precision 1)
+    unsigned scr_mr;   // running max of |R| over given entries (float bits)
+    unsigned scr_mp;   // running max of the finite |P1|, |P2| over given entries (float bits)
+    long long screened;// candidates the screen proved non-improving (cumulative)
 };
 
 struct stmf_problem {
@@ -96,6 +103,14 @@ struct stmf_problem {
     double *part_ulf;  // STMF_WMAX x ceil(m/4) partial changes of the F-ULF units
     double *part_urf;  // STMF_WMAX x ceil(n/32) partial changes of the F-URF units
     double *fc;        // STMF_WMAX candidate errors
+    // FP16 screening (precision 1; all NULL otherwise)
+    int precision;
+    __half *Rh, *P1h, *P2h;
+    int scr_blocks;    // row blocks of the screen
+    double *scr_sum;   // STMF_WMAX x scr_blocks screened changes
+    double *scr_cnt;   // STMF_WMAX x scr_blocks counts of possibly changed given entries
+    float *scr_umax;   // STMF_WMAX x scr_blocks max |U'_sk| over the block's rows
+    float *scr_vmax;   // STMF_WMAX max |V'_kt| over t < n
     stmf_ctl *ctl;     // device control block
     stmf_ctl *ctl_host;// pinned host mirror
     int32_t *trace_dev;// device trace buffer
@@ -143,7 +158,8 @@ cudaError_t launch_copy_rows(cudaStream_t st, const float *src, int lds, float *
 cudaError_t launch_stats(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_window(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots);
-cudaError_t launch_eval(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode = 0);
+cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph);
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);
 cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P);
@@ -151,6 +167,12 @@ cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph);
 cudaError_t launch_sweep_begin(cudaStream_t st, stmf_problem *P, int in_graph);
 cudaError_t launch_job_begin(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_sweep_end(cudaStream_t st, stmf_problem *P);
+
+// kernels_screen.cu
+constexpr int SCR_ROWS = 8;
+constexpr int SCR_THREADS = 128;
+cudaError_t screen_prepare(stmf_problem *P);
+cudaError_t launch_screen(cudaStream_t st, stmf_problem *P);
 
 // peak.cu
 cudaError_t launch_peak(cudaStream_t st, int mode, int iters, int blocks, float *sink);

@@ -144,12 +144,27 @@ k_maxplus(int m, int n, int r, const float *__restrict__ U, int ldu,
 // colhist partials per 128-row part.  The column sums of td are accumulated
 // in compensated FP32 per thread and combined in FP64; the histogram lives in
 // shared memory as [l][4][32] so the 32 lanes of a warp always hit 32
-// different banks.
+// different banks.  HALF (FP16 screening) also writes R, P1, P2 rounded to
+// nearest half at given entries (a quiet NaN elsewhere) and raises the
+// running maxima of |R| and of the finite |P1|, |P2| over given entries.
+struct HalfPlanes {
+    __half *Rh, *P1h, *P2h;
+    unsigned *mr, *mp;
+};
+
+__device__ __forceinline__ unsigned pack_halves(__half a, __half b)
+{
+    return (unsigned)__half_as_ushort(a) | ((unsigned)__half_as_ushort(b) << 16);
+}
+
+template <bool HALF>
 __global__ void __launch_bounds__(256)
 k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *__restrict__ V,
                  int ld, float *__restrict__ P1, uint8_t *__restrict__ A, float *__restrict__ P2,
-                 const float *__restrict__ R, double *__restrict__ tdpart, int *__restrict__ chpart)
+                 const float *__restrict__ R, double *__restrict__ tdpart, int *__restrict__ chpart,
+                 HalfPlanes H)
 {
+    float hmr = 0.f, hmp = 0.f;
     __shared__ float sU[TR][STMF_MAX_RANK + 1];
     __shared__ __align__(16) float sV[STMF_MAX_RANK][TC];
     __shared__ double sTd[8][TC];
@@ -218,6 +233,37 @@ k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *
                     atomicAdd(&sHist[am[i][jj]][jj][cl], 1);
                 }
             }
+            if (HALF) {
+                __half hr[4], h1[4], h2[4];
+                const __half qnan = __ushort_as_half((unsigned short)0x7e00);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const bool given = rv[jj] == rv[jj];
+                    hr[jj] = given ? __float2half_rn(rv[jj]) : qnan;
+                    h1[jj] = given ? __float2half_rn(p1[i][jj]) : qnan;
+                    h2[jj] = given ? __float2half_rn(p2[i][jj]) : qnan;
+                    if (given) {
+                        hmr = fmaxf(hmr, fabsf(rv[jj]));
+                        hmp = fmaxf(hmp, fabsf(p1[i][jj]));
+                        if (fabsf(p2[i][jj]) < INFINITY) hmp = fmaxf(hmp, fabsf(p2[i][jj]));
+                    }
+                }
+                *reinterpret_cast<uint2 *>(H.Rh + off) = make_uint2(pack_halves(hr[0], hr[1]), pack_halves(hr[2], hr[3]));
+                *reinterpret_cast<uint2 *>(H.P1h + off) = make_uint2(pack_halves(h1[0], h1[1]), pack_halves(h1[2], h1[3]));
+                *reinterpret_cast<uint2 *>(H.P2h + off) = make_uint2(pack_halves(h2[0], h2[1]), pack_halves(h2[2], h2[3]));
+            }
+        }
+    }
+    if (HALF) {
+        // non-negative floats order like their bit patterns
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            hmr = fmaxf(hmr, __shfl_xor_sync(0xffffffffu, hmr, o));
+            hmp = fmaxf(hmp, __shfl_xor_sync(0xffffffffu, hmp, o));
+        }
+        if (cl == 0) {
+            atomicMax(H.mr, __float_as_uint(hmr));
+            atomicMax(H.mp, __float_as_uint(hmp));
         }
     }
 #pragma unroll
@@ -324,8 +370,14 @@ cudaError_t launch_maxplus(cudaStream_t st, int m, int n, int r, const float *U,
 cudaError_t launch_planes(cudaStream_t st, stmf_problem *P, int *chpart)
 {
     dim3 grid(P->np / TC, (P->m + TR * TILES - 1) / (TR * TILES));
-    k_maxplus_planes<<<grid, 256, 0, st>>>(P->m, P->n, P->r, P->U, P->V, P->np, P->P1, P->A, P->P2,
-                                           P->R, P->tdpart, chpart);
+    if (P->precision == 1) {
+        const HalfPlanes H{P->Rh, P->P1h, P->P2h, &P->ctl->scr_mr, &P->ctl->scr_mp};
+        k_maxplus_planes<true><<<grid, 256, 0, st>>>(P->m, P->n, P->r, P->U, P->V, P->np, P->P1, P->A, P->P2,
+                                                     P->R, P->tdpart, chpart, H);
+    } else {
+        k_maxplus_planes<false><<<grid, 256, 0, st>>>(P->m, P->n, P->r, P->U, P->V, P->np, P->P1, P->A, P->P2,
+                                                      P->R, P->tdpart, chpart, HalfPlanes{});
+    }
     return cudaGetLastError();
 }
 

@@ -286,9 +286,9 @@ __global__ void __launch_bounds__(1024) k_window(stmf_problem P)
         sk[tid] = best;
         const int base = ctl->ncand_row / 2;
         int *c0 = P.cand + 8 * (2 * tid);
-        c0[0] = j; c0[1] = best; c0[2] = 0; c0[3] = base + tid;
+        c0[0] = j; c0[1] = best; c0[2] = 0; c0[3] = base + tid; c0[4] = 0;
         int *c1 = P.cand + 8 * (2 * tid + 1);
-        c1[0] = j; c1[1] = best; c1[2] = 1; c1[3] = base + tid;
+        c1[0] = j; c1[1] = best; c1[2] = 1; c1[3] = base + tid; c1[4] = 0;
     }
     __syncthreads();
     if (tid == 0) {
@@ -445,7 +445,10 @@ __device__ __forceinline__ void reduce_unit(EvalSmem &S, int nc, double *part, i
 // F-ULF unit: 4 full rows.  Phase 1: U'_sk = min over t of (R_st - V'_kt) for
 // every F-ULF candidate.  Phase 2: the candidates' change of the error over
 // the 4 rows, accumulated per entry (a candidate that changes nothing gives
-// exactly 0).
+// exactly 0).  MODE 0 runs both phases, MODE 1 phase 1 only, MODE 2 phase 2
+// only, with U' read back from Uc (the window's lists then hold the
+// candidates the FP16 screen kept).
+template <int MODE>
 __device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S, int b, int ldpart)
 {
     const stmf_ctl *ctl = P.ctl;
@@ -458,12 +461,17 @@ __device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S
         S.sslot[tid] = slot;
         S.sk[tid] = P.cand[8 * slot + 1];
     }
-    for (int cc = 0; cc < nu; ++cc) S.acc[cc][tid] = 0.f;
+    if (MODE != 1)
+        for (int cc = 0; cc < nu; ++cc) S.acc[cc][tid] = 0.f;
     __syncthreads();
     const float4 *R4 = reinterpret_cast<const float4 *>(P.R + (size_t)s0 * P.np);
 
+    if (MODE == 2) {
+        if (tid < 4 * nu) S.su[tid >> 2][tid & 3] = P.Uc[(size_t)S.sslot[tid >> 2] * P.mp + s0 + (tid & 3)];
+        __syncthreads();
+    }
     // ---- phase 1
-    for (int g = 0; g < nu; g += CG) {
+    for (int g = 0; g < nu && MODE != 2; g += CG) {
         float acc[4 * CG];
 #pragma unroll
         for (int q = 0; q < 4 * CG; ++q) acc[q] = INFINITY;
@@ -503,6 +511,7 @@ __device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S
         __syncthreads();
     }
 
+    if (MODE == 1) return;
     // ---- phase 2: a thread owns the 4 rows x 4 columns of one float4 column
     const float4 *P14 = reinterpret_cast<const float4 *>(P.P1 + (size_t)s0 * P.np);
     const float4 *P24 = reinterpret_cast<const float4 *>(P.P2 + (size_t)s0 * P.np);
@@ -539,7 +548,9 @@ __device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S
 
 // F-URF unit: a strip of 32 full columns.  Phase 1: V'_kt = min over s of
 // (R_st - U'_sk) from rows of RT (warp w owns columns 4w .. 4w+3).  Phase 2:
-// the candidates' change of the error over the strip.
+// the candidates' change of the error over the strip.  MODE as for F-ULF
+// (MODE 2 reads V' back from Vc).
+template <int MODE>
 __device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S, int b, int ldpart)
 {
     const stmf_ctl *ctl = P.ctl;
@@ -551,11 +562,16 @@ __device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S
         S.sslot[tid] = slot;
         S.sk[tid] = P.cand[8 * slot + 1];
     }
-    for (int cc = 0; cc < nv; ++cc) S.acc[cc][tid] = 0.f;
+    if (MODE != 1)
+        for (int cc = 0; cc < nv; ++cc) S.acc[cc][tid] = 0.f;
     __syncthreads();
 
+    if (MODE == 2) {
+        for (int e = tid; e < 32 * nv; e += EVAL_THREADS)
+            S.sv[e >> 5][e & 31] = P.Vc[(size_t)S.sslot[e >> 5] * P.np + t0c + (e & 31)];
+    }
     // ---- phase 1
-    {
+    if (MODE != 2) {
         const int nf4 = P.mp >> 2;
         const float4 *X4 = reinterpret_cast<const float4 *>(P.RT + (size_t)(t0c + 4 * warp) * P.mp);
         for (int g = 0; g < nv; g += CG) {
@@ -591,6 +607,7 @@ __device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S
         }
     }
     __syncthreads();
+    if (MODE == 1) return;
 
     // ---- phase 2: a thread owns 4 consecutive rows x 4 columns per step
     const int cl = tid & 7, rl = tid >> 3;
@@ -641,6 +658,7 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(EVAL_THREADS, 2) k_eval(stmf_problem P, int nb_ulf, int nb_urf)
 {
     __shared__ EvalSmem S;
@@ -656,8 +674,8 @@ __global__ void __launch_bounds__(EVAL_THREADS, 2) k_eval(stmf_problem P, int nb
         const int u = S.unit;
         __syncthreads();
         if (u >= total) break;
-        if (u < first_ulf) eval_urf_unit(P, S, u, nb_urf);
-        else eval_ulf_unit(P, S, u - first_ulf, nb_ulf);
+        if (u < first_ulf) eval_urf_unit<MODE>(P, S, u, nb_urf);
+        else eval_ulf_unit<MODE>(P, S, u - first_ulf, nb_ulf);
         __syncthreads();
     }
     if (threadIdx.x == 0) atomicMax(&P.ctl->ev_t1, global_ns());
@@ -691,6 +709,10 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nb_ulf, int
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = ctl->nc;
     for (int c = warp; c < nc; c += 32) {
+        if (P.cand[8 * c + 4]) {          // proved non-improving by the FP16 screen
+            if (lane == 0) { sf[c] = INFINITY; P.fc[c] = INFINITY; }
+            continue;
+        }
         const int type = P.cand[8 * c + 2];
         const int nb = type == 0 ? nb_ulf : nb_urf;
         const double *part = (type == 0 ? P.part_ulf : P.part_urf) + (size_t)c * nb;
@@ -814,7 +836,7 @@ __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
 {
     stmf_ctl *ctl = P.ctl;
     int *c0 = P.cand;
-    c0[0] = j; c0[1] = k; c0[2] = type; c0[3] = 0;
+    c0[0] = j; c0[1] = k; c0[2] = type; c0[3] = 0; c0[4] = 0;
     ctl->i = i;
     ctl->nc = 1;
     ctl->nu = type == 0 ? 1 : 0;
@@ -917,12 +939,32 @@ cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots)
 static inline int nb_ulf(const stmf_problem *P) { return (P->m + 3) / 4; }
 static inline int nb_urf(const stmf_problem *P) { return (P->n + 31) / 32; }
 
-cudaError_t launch_eval(cudaStream_t st, stmf_problem *P)
+cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode)
 {
     const int units = nb_ulf(P) + nb_urf(P);
     const int blocks = min(units, 2 * P->ctx->num_sms);
-    k_eval<<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
+    if (mode == 1) k_eval<1><<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
+    else if (mode == 2) k_eval<2><<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
+    else k_eval<0><<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
     return cudaGetLastError();
+}
+
+// One window of a row: candidates, seeds, evaluation, decision.  With FP16
+// screening the evaluation splits into phase 1 (every candidate's U'/V'),
+// the screen, and phase 2 over the candidates it kept.
+cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph)
+{
+    cudaError_t e = launch_window(st, P);
+    if (e == cudaSuccess) e = launch_seed(st, P, P->ctl_host->wmax);
+    if (P->precision == 1) {
+        if (e == cudaSuccess) e = launch_eval(st, P, 1);
+        if (e == cudaSuccess) e = launch_screen(st, P);
+        if (e == cudaSuccess) e = launch_eval(st, P, 2);
+    } else if (e == cudaSuccess) {
+        e = launch_eval(st, P, 0);
+    }
+    if (e == cudaSuccess) e = launch_select(st, P, in_graph, 0);
+    return e;
 }
 
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single)

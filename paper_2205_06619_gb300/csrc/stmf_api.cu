@@ -93,7 +93,8 @@ void problem_free(stmf_problem *P)
     void *ptrs[] = {P->R, P->RT, P->U, P->V, P->P1, P->P2, P->A, P->cmin1, P->cmin2, P->carg,
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
                     P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part_ulf, P->part_urf, P->fc,
-                    P->ctl, P->trace_dev, P->perm};
+                    P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
+                    P->scr_umax, P->scr_vmax};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
@@ -352,13 +353,8 @@ stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, b
     }, nullptr));
     CS(capture_into(ctx, cap, body_row, &nif, 1, [&](cudaStream_t c) { return launch_row_begin(c, P, 1); }, &rb));
     CS(add_conditional(ctx, body_row, &rb, 1, hw, cudaGraphCondTypeWhile, &wwin, &body_win));
-    CS(capture_into(ctx, cap, body_win, nullptr, 0, [&](cudaStream_t c) {
-        cudaError_t e = launch_window(c, P);
-        if (e == cudaSuccess) e = launch_seed(c, P, P->ctl_host->wmax);
-        if (e == cudaSuccess) e = launch_eval(c, P);
-        if (e == cudaSuccess) e = launch_select(c, P, 1, 0);
-        return e;
-    }, nullptr));
+    CS(capture_into(ctx, cap, body_win, nullptr, 0, [&](cudaStream_t c) { return launch_window_body(c, P, 1); },
+                    nullptr));
     return STMF_OK;
 }
 
@@ -399,10 +395,7 @@ stmf_status sweep_host(stmf_problem *P)
         }
         CK(launch_row_begin(st, P, 0));
         while (true) {
-            CK(launch_window(st, P));
-            CK(launch_seed(st, P, P->ctl_host->wmax));
-            CK(launch_eval(st, P));
-            CK(launch_select(st, P, 0, 0));
+            CK(launch_window_body(st, P, 0));
             s = read_ctl(P);
             if (s != STMF_OK) return s;
             if (P->ctl_host->row_done) break;
@@ -424,7 +417,7 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     stmf_options o;
     if (opts) o = *opts; else stmf_default_options(&o);
     if (o.window < 0 || o.window > STMF_WMAX) return fail(ctx, STMF_ERR_INVALID, "window outside [0, %d]", STMF_WMAX);
-    if (o.precision != 0) return fail(ctx, STMF_ERR_INVALID, "precision mode %d is not available", o.precision);
+    if (o.precision < 0 || o.precision > 1) return fail(ctx, STMF_ERR_INVALID, "precision mode %d unknown", o.precision);
     if (o.select < 0 || o.select > 1) return fail(ctx, STMF_ERR_INVALID, "select mode %d unknown", o.select);
     const int tr = m0 > n0;                 // Algorithm 3: a tall R is transposed
     const int m = tr ? n0 : m0, n = tr ? m0 : n0;
@@ -445,6 +438,26 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (s != STMF_OK) return s;
     P->transposed = tr; P->m0 = m0; P->n0 = n0;
     cudaStream_t st = ctx->stream;
+    if (o.precision == 1) {
+        // half planes and screen partials; the planes are written by every
+        // refresh from here on (the first one is in problem_init)
+        const size_t cells = (size_t)P->mp * P->np;
+        const size_t nblk = (size_t)(P->m + SCR_ROWS - 1) / SCR_ROWS;
+        cudaError_t ea = dalloc(&P->Rh, cells);
+        if (ea == cudaSuccess) ea = dalloc(&P->P1h, cells);
+        if (ea == cudaSuccess) ea = dalloc(&P->P2h, cells);
+        if (ea == cudaSuccess) ea = dalloc(&P->scr_sum, STMF_WMAX * nblk);
+        if (ea == cudaSuccess) ea = dalloc(&P->scr_cnt, STMF_WMAX * nblk);
+        if (ea == cudaSuccess) ea = dalloc(&P->scr_umax, STMF_WMAX);
+        if (ea == cudaSuccess) ea = dalloc(&P->scr_vmax, STMF_WMAX);
+        if (ea == cudaSuccess) ea = screen_prepare(P);
+        if (ea != cudaSuccess) {
+            problem_free(P);
+            cudaGetLastError();
+            return fail(ctx, STMF_ERR_OOM, "FP16 screening buffers: %s", cudaGetErrorString(ea));
+        }
+        P->precision = 1;
+    }
     int *d_bad = nullptr;
     cudaError_t e = cudaMalloc(&P->perm, sizeof(int) * m);
     if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
@@ -530,6 +543,7 @@ void fill_report(const stmf_problem *P, stmf_report *rep)
     rep->eval_launches = c.eval_launches;
     rep->eval_candidates = c.eval_cands;
     rep->seconds = P->seconds;
+    rep->candidates_screened = c.screened;
 }
 
 stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *trace_out, int64_t trace_cap)
@@ -611,10 +625,7 @@ stmf_status sweep_rows_host(stmf_problem *P, int rows)
         if (P->ctl_host->dirty_k != -2) CS(refresh(P));
         CK(launch_row_begin(st, P, 0));
         while (true) {
-            CK(launch_window(st, P));
-            CK(launch_seed(st, P, P->ctl_host->wmax));
-            CK(launch_eval(st, P));
-            CK(launch_select(st, P, 0, 0));
+            CK(launch_window_body(st, P, 0));
             CS(read_ctl(P));
             if (P->ctl_host->row_done) break;
         }
@@ -628,7 +639,7 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
 {
     stmf_options o;
     if (opts) o = *opts; else stmf_default_options(&o);
-    if (o.precision != 0) return fail(ctx, STMF_ERR_INVALID, "precision mode %d is not available", o.precision);
+    if (o.precision < 0 || o.precision > 1) return fail(ctx, STMF_ERR_INVALID, "precision mode %d unknown", o.precision);
     if (o.window < 0 || o.window > STMF_WMAX) return fail(ctx, STMF_ERR_INVALID, "window outside [0, %d]", STMF_WMAX);
     for (int q = 0; q < nprob; ++q) {
         const stmf_batch_problem &b = probs[q];
