@@ -52,12 +52,12 @@ ALU_PEAK_TOPS = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes (read + write) per k_eval launch from the ncu capture summarised in
 # profiles/k_eval_gene_1000x5000_r10.md (cold cache, gene workload); valid only
 # for the kernel source it was taken on
-EVAL_TRAFFIC = {"source_sha256_prefix": "3ec2fe87cea8704f", "bytes": 91.86e6, "workload": "gene"}
+EVAL_TRAFFIC = {"source_sha256_prefix": "none", "bytes": None, "workload": "gene"}
 
 
 def eval_traffic(workload_name):
     import hashlib
-    src = os.path.join(ROOT, "paper_2205_06619_gb300", "csrc", "kernels_update.cu")
+    src = os.path.join(ROOT, "paper_2205_06619_gb300", "csrc", "kernels_eval.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if sha != EVAL_TRAFFIC["source_sha256_prefix"] or workload_name != EVAL_TRAFFIC["workload"]:
         return None
@@ -249,6 +249,66 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    """Candidate screening in packed FP16 with FP32 re-check (precision 1) vs
+    the all-FP32 path (precision 0) on the 4000 x 20000 rank-20 workload, 50%
+    given.  Both runs start from the same Random Acol state and make the same
+    decisions; the final b-norm error of each is recomputed in FP64 by the
+    oracle from the returned factors (the CPU leg)."""
+    import torch
+    from paper_2205_06619_gb300 import api, synth
+    w = synth.workload_large(seed=args.seed)
+    R_np, M_np, r = w["R"], w["mask"], w["rank"]
+    Rg, Mw = torch.from_numpy(R_np).cuda(), api.pack_mask(M_np)
+    stream = api.context().stream
+    out = {}
+    with ClockSampler(0) as clocks:
+        for prec in (0, 1):
+            fz = api.Factorization(Rg, Mw, rank=r, seed=args.seed, precision=prec)
+            rep0 = fz.run(0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            rep1 = fz.run(args.steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            U, V = fz.result()
+            out[prec] = dict(seconds=a.elapsed_time(b) / 1e3, rep=rep1, rep0=rep0, U=U.cpu().numpy(),
+                             V=V.cpu().numpy())
+            fz.close()
+    same = bool(np.array_equal(out[0]["U"], out[1]["U"]) and np.array_equal(out[0]["V"], out[1]["V"]))
+    res = {}
+    for prec in (0, 1):
+        o = out[prec]
+        d = {k: o["rep"][k] - o["rep0"][k] for k in ("eval_ns", "eval_launches", "candidates_issued",
+                                                     "candidates_screened", "windows")}
+        res["fp32" if prec == 0 else "fp16_screen"] = {
+            "sweeps_per_s": args.steps / o["seconds"], "seconds": o["seconds"], "f_final": o["rep"]["f_final"],
+            "eval_us_per_window": d["eval_ns"] / 1e3 / max(d["eval_launches"], 1),
+            "candidates_issued": d["candidates_issued"], "candidates_screened": d["candidates_screened"],
+            "screened_fraction": d["candidates_screened"] / max(d["candidates_issued"], 1)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle  # CPU leg: FP64 error of the returned factors
+        t = time.perf_counter()
+        for prec, key in ((0, "fp32"), (1, "fp16_screen")):
+            f64 = oracle.error(R_np, M_np, out[prec]["U"].astype(np.float64), out[prec]["V"].astype(np.float64))
+            res[key]["f_oracle_fp64"] = f64
+            res[key]["rel_err_vs_oracle"] = abs(res[key]["f_final"] - f64) / f64
+        secs = time.perf_counter() - t
+        cpu = {"value": 2.0 / secs, "unit": "error evaluations/s", "cores": 1, "kind": "oracle",
+               "sample": "FP64 b-norm error of both returned factorizations (4000x20000, rank 20), %.1f s" % secs}
+    scr = res["fp16_screen"]
+    line = {"metric": METRIC, "value": scr["sweeps_per_s"], "unit": "sweeps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 0, "ms_per_step": 1e3 * out[1]["seconds"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 screen + f32 re-check", "data": "synthetic",
+            "config": {"workload": "precision: 4000x20000 rank-20, 50% given, U*,V* ~ U[0,1) + N(0,0.01)",
+                       "step": "one ByRow sweep from the Random Acol start", "l2": "inputs (1.3 GB) exceed L2"},
+            "identical_decisions": same, "speedup_vs_fp32": res["fp32"]["seconds"] / scr["seconds"],
+            "precision": res, "clocks": clocks.summary(), "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Learned initialisation vs Random Acol: sweeps and time to reach the
     plain method's final error on fresh matrices (same permutation for both)."""
@@ -319,7 +379,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5, help="timed sweeps")
     ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up sweeps")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gene", choices=["gene", "small", "large", "batch", "learned"])
+    ap.add_argument("--workload", default="gene", choices=["gene", "small", "large", "batch", "learned", "precision"])
     ap.add_argument("--learned-train", type=int, default=200)
     ap.add_argument("--learned-eval", type=int, default=16)
     ap.add_argument("--learned-m", type=int, default=200)
@@ -343,6 +403,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
 
     import torch
@@ -415,8 +478,16 @@ def main():
     d_eval_ns = rep1["eval_ns"] - rep0["eval_ns"]
     d_eval_n = rep1["eval_launches"] - rep0["eval_launches"]
     d_eval_c = rep1["eval_candidates"] - rep0["eval_candidates"]
+    d_res_ns = rep1["eval_res_ns"] - rep0["eval_res_ns"]
+    d_del_ns = rep1["eval_delta_ns"] - rep0["eval_delta_ns"]
+    # algorithmic ops per given entry and candidate: phase 1 (residuation)
+    # one sub + one min; phase 2 (error change) add, max, sub, sub
+    ach_res = (2.0 * n_obs * d_eval_c) / (d_res_ns * 1e-9) / 1e12 if d_res_ns else None
+    ach_del = (4.0 * n_obs * d_eval_c) / (d_del_ns * 1e-9) / 1e12 if d_del_ns else None
     achieved = (6.0 * n_obs * d_eval_c) / (d_eval_ns * 1e-9) / 1e12 if d_eval_ns else None
-    launches = 4 * d_win + args.steps * m_or + 5 * d_ref + args.steps
+    # per window: k_window, k_seed, k_res, k_delta, k_select; per row k_row_begin;
+    # per refresh k_stats, k_maxplus_planes, k_td_finalize, k_rank, k_scatter_f
+    launches = 5 * d_win + args.steps * m_or + 5 * d_ref + args.steps
 
     if rank_id != 0:
         if dist is not None:
@@ -446,13 +517,20 @@ def main():
                    "parallelism": "independent replicas" if world > 1 else "single GPU"},
         "gops": gops, "gops_frac_of_alu_peak": gops / (ALU_PEAK_TOPS * 1e3),
         "candidates_tried_per_sweep": d_tried / args.steps,
-        "roofline": {"kernel": "k_eval (window of F-ULF/F-URF candidates)", "bound": "alu",
-                     "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
-                     "frac": achieved / ALU_PEAK_TOPS if achieved else None,
+        "roofline": {"kernel": "k_delta (phase 2 of a window: error changes of all its candidates)",
+                     "bound": "alu", "achieved": ach_del, "peak": ALU_PEAK_TOPS, "unit": "Top/s",
+                     "frac": ach_del / ALU_PEAK_TOPS if ach_del else None,
                      "traffic": eval_traffic(args.workload), "traffic_unit": "bytes per launch",
-                     "launches": d_eval_n, "avg_launch_us": d_eval_ns / 1e3 / max(d_eval_n, 1),
+                     "launches": d_eval_n, "avg_launch_us": d_del_ns / 1e3 / max(d_eval_n, 1),
                      "candidates_per_launch": d_eval_c / max(d_eval_n, 1),
-                     "timing": "per-launch device time from %globaltimer (kernel runs inside a CUDA graph)"},
+                     "ops_per_given_entry_per_candidate": 4,
+                     "timing": "per-launch device time from %globaltimer (kernels run inside a CUDA graph)",
+                     "phase1_k_res": {"achieved": ach_res, "frac": ach_res / ALU_PEAK_TOPS if ach_res else None,
+                                      "avg_launch_us": d_res_ns / 1e3 / max(d_eval_n, 1),
+                                      "ops_per_given_entry_per_candidate": 2},
+                     "window_eval": {"achieved": achieved, "frac": achieved / ALU_PEAK_TOPS if achieved else None,
+                                     "avg_us": d_eval_ns / 1e3 / max(d_eval_n, 1),
+                                     "span": "k_res start to k_delta end, 6 ops per given entry per candidate"}},
         "e2e": {"value": (args.warmup + args.steps) * world / t_e2e, "unit": "sweeps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "job": "upload + init + %d sweeps + download, public API" % (args.warmup + args.steps)},

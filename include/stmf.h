@@ -101,12 +101,15 @@ typedef struct {
     int64_t refreshes;        /* product/statistics refreshes                        */
     int64_t windows;          /* device windows evaluated                            */
     int64_t trace_records;    /* trace records written                               */
-    int64_t eval_ns;          /* summed device durations of the window evaluations   */
+    int64_t eval_ns;          /* summed device durations of the window evaluations
+                                 (phase-1 start to phase-2 end, %globaltimer)       */
     int64_t eval_launches;    /* window evaluations timed                            */
     int64_t eval_candidates;  /* candidates those evaluations covered                */
     double seconds;           /* wall time of the sweep loop                         */
     int64_t candidates_screened; /* candidates the FP16 screen proved non-improving
                                     (precision 1; counted in candidates_issued)   */
+    int64_t eval_res_ns;      /* summed durations of the phase-1 (residuation) launches */
+    int64_t eval_delta_ns;    /* summed durations of the phase-2 (error change) launches */
 } stmf_report;
 
 /* Context: binds a device and a stream (cudaStream_t passed as void*; NULL =
@@ -290,8 +293,9 @@ void stmf_default_options(stmf_options *opts);
  * iterations of (FADD, FMNMX) pairs on every SM and returns, in *gops
  * (host), the measured giga-operations per second (FADD and FMNMX count one
  * each).  mode 0: 1:1 FADD/FMNMX; 1: FADD only; 2: FMNMX only;
- * 3: packed half2 HADD2/HMNMX2 (two operations per lane).  Uses the
- * context's stream and synchronizes it. */
+ * 3: packed half2 HADD2/HMNMX2 (two operations per lane); 4: packed
+ * FP32x2 adds only; 5: one packed FP32x2 add then two scalar FMNMX (1:1 mix
+ * with the additions packed).  Uses the context's stream and synchronizes it. */
 stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops);
 
 #ifdef __cplusplus

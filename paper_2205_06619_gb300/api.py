@@ -54,7 +54,7 @@ class Report(C.Structure):
                 ("candidates_issued", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
                 ("windows", C.c_int64), ("trace_records", C.c_int64), ("eval_ns", C.c_int64),
                 ("eval_launches", C.c_int64), ("eval_candidates", C.c_int64), ("seconds", C.c_double),
-                ("candidates_screened", C.c_int64)]
+                ("candidates_screened", C.c_int64), ("eval_res_ns", C.c_int64), ("eval_delta_ns", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -22,6 +22,7 @@
 
 #define STMF_PAD 256
 #define STMF_WMAX 64          // candidates per device window (upper bound)
+#define STMF_DELTA_BLOCKS_PER_SM 4   // resident blocks of the phase-2 kernel
 
 static inline int stmf_roundup(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -59,13 +60,17 @@ struct stmf_ctl {
     int nu, nv;        // F-ULF / F-URF candidates of the window
     int exhausted;     // 1 when the window reached the end of the row's candidates
     int eval_next;     // work queue of the window evaluation (next unit)
-    int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // window slots per type
+    int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // window slots per type, grouped by k
+    int alist[STMF_WMAX];  // all the window's slots to evaluate in phase 2, grouped by k
+    int na;
     long long tried;   // sequential-method candidates tried (cumulative)
     long long issued;  // candidates evaluated on the device (cumulative)
     long long accepted;
     long long refreshes;
     long long windows;
     unsigned long long ev_t0, ev_t1;   // earliest start / latest end of the running window evaluation
+    unsigned long long ev_r1, ev_d0;   // end of its phase-1 launch / start of its phase-2 launch
+    long long res_ns, delta_ns;        // summed durations of the phase-1 / phase-2 launches
     long long eval_ns;                 // summed durations of the window evaluations (%globaltimer)
     long long eval_launches;
     long long eval_cands;              // candidates those evaluations covered
@@ -100,8 +105,7 @@ struct stmf_problem {
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
-    double *part_ulf;  // STMF_WMAX x ceil(m/4) partial changes of the F-ULF units
-    double *part_urf;  // STMF_WMAX x ceil(n/32) partial changes of the F-URF units
+    double *part;      // STMF_WMAX x (phase-2 blocks) partial changes
     double *fc;        // STMF_WMAX candidate errors
     // FP16 screening (precision 1; all NULL otherwise)
     int precision;
@@ -160,6 +164,12 @@ cudaError_t launch_window(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots);
 cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode = 0);
 cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph);
+
+// kernels_eval.cu
+cudaError_t launch_res(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_delta(cudaStream_t st, stmf_problem *P);
+int delta_grid(const stmf_problem *P);
+int delta_depth(const stmf_problem *P);
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);
 cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P);

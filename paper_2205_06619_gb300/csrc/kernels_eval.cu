@@ -1,0 +1,259 @@
+// Evaluation of a window of F-ULF / F-URF candidates (Algorithms 1 and 2),
+// in two launches.
+//
+// Phase 1 (k_res) completes every candidate's factor pair:
+//   F-ULF slot c:  U'_sc = min over given t of (R_st - V'_ct)   (row residuation)
+//   F-URF slot c:  V'_ct = min over given s of (R_st - U'_sc)   (column residuation)
+// where the other factor (V'_c for F-ULF, U'_c for F-URF) is the seed that
+// k_seed wrote.  Phase 2 (k_delta) sums, for every candidate, the change of
+// the b-norm terms over all entries
+//   Delta_c = sum over given (s,t) of ( |R_st - max(E_st, U'_sc + V'_ct)| - |R_st - P1_st| ),
+//   E = max over l != k of (U_sl + V_lt) = (A == k ? P2 : P1),
+// per entry, so a candidate that changes nothing gives exactly 0.
+#include "common.cuh"
+
+namespace {
+
+constexpr unsigned FULLM = 0xffffffffu;
+constexpr int NCT = STMF_WMAX / 2;    // candidates of one type in a window
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Atomic minimum of a float slot that starts at +inf.  Non-negative floats
+// order like their bit patterns as signed integers, negative ones in reverse
+// as unsigned integers; -0 is first made +0 so that it orders as zero.
+__device__ __forceinline__ void atomic_min_float(float *addr, float v)
+{
+    v = v + 0.0f;
+    if (v >= 0.f) atomicMin(reinterpret_cast<int *>(addr), __float_as_int(v));
+    else atomicMax(reinterpret_cast<unsigned *>(addr), __float_as_uint(v));
+}
+
+// ------------------------------------------------------------------ phase 1
+// Task = (type, RES_THREADS rows of X, RES_CHUNK columns): type 0 runs over
+// the rows of R with the F-ULF candidates' V'_c, type 1 over the rows of R^T
+// with the F-URF candidates' U'_c.  The candidates' values of the chunk are
+// staged in shared memory and read as warp-wide broadcasts; each thread owns
+// one row and keeps the running minima of all the type's candidates in
+// registers (no cross-thread reduction).  Chunks combine through atomic
+// minima, which are exact in any order.  NaN entries (not given, padding)
+// drop out of fminf.
+constexpr int RES_THREADS = 128;
+constexpr int RES_CHUNK = 256;
+
+__global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0, int nch0, int nch1)
+{
+    __shared__ __align__(16) float sW[NCT][RES_CHUNK];
+    __shared__ int sslot[NCT];
+    const stmf_ctl *ctl = P.ctl;
+    const int tid = threadIdx.x;
+    // the window evaluation's span (this launch's start to the end of
+    // phase 2) is recorded with the global nanosecond timer: inside a CUDA
+    // graph no event can bracket single nodes
+    if (tid == 0) atomicMin(&P.ctl->ev_t0, global_ns());
+    int task = blockIdx.x;
+    const int type = task >= ntask0;
+    if (type) task -= ntask0;
+    const int cnt = type ? ctl->nv : ctl->nu;
+    if (cnt == 0) return;
+    const int nch = type ? nch1 : nch0;
+    const int rb = task / nch, c0 = (task % nch) * RES_CHUNK;
+    const float *X = type ? P.RT : P.R;
+    const size_t ldx = type ? P.mp : P.np;
+    const int nrows = type ? P.n : P.m;
+    const float *W = type ? P.Uc : P.Vc;
+    float *OUT = type ? P.Vc : P.Uc;
+    const size_t ldw = type ? P.mp : P.np;
+    const size_t ldo = type ? P.np : P.mp;
+
+    if (tid < cnt) sslot[tid] = type ? ctl->vlist[tid] : ctl->ulist[tid];
+    __syncthreads();
+    for (int e = tid; e < cnt * (RES_CHUNK / 4); e += RES_THREADS) {
+        const int c = e / (RES_CHUNK / 4), q = e % (RES_CHUNK / 4);
+        reinterpret_cast<float4 *>(sW[c])[q] = reinterpret_cast<const float4 *>(W + sslot[c] * ldw + c0)[q];
+    }
+    __syncthreads();
+    const int row = rb * RES_THREADS + tid;
+    if (row < nrows) {
+        float acc[NCT];
+#pragma unroll
+        for (int c = 0; c < NCT; ++c) acc[c] = INFINITY;
+        const float4 *x4 = reinterpret_cast<const float4 *>(X + row * ldx + c0);
+#pragma unroll 1
+        for (int q = 0; q < RES_CHUNK / 4; q += 2) {
+            const float4 a = x4[q], b = x4[q + 1];
+#pragma unroll
+            for (int c = 0; c < NCT; ++c) {
+                if (c < cnt) {
+                    const float4 w0 = reinterpret_cast<const float4 *>(sW[c])[q];
+                    const float4 w1 = reinterpret_cast<const float4 *>(sW[c])[q + 1];
+                    float m = acc[c];
+                    m = fminf(m, a.x - w0.x); m = fminf(m, a.y - w0.y);
+                    m = fminf(m, a.z - w0.z); m = fminf(m, a.w - w0.w);
+                    m = fminf(m, b.x - w1.x); m = fminf(m, b.y - w1.y);
+                    m = fminf(m, b.z - w1.z); m = fminf(m, b.w - w1.w);
+                    acc[c] = m;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NCT; ++c)
+            if (c < cnt && acc[c] < INFINITY) atomic_min_float(OUT + sslot[c] * ldo + row, acc[c]);
+    }
+    __syncthreads();
+    if (tid == 0) atomicMax(&P.ctl->ev_r1, global_ns());
+}
+
+// ------------------------------------------------------------------ phase 2
+// Tiles of 4 rows x DEL_COLS columns (a thread owns 4 rows x one float4
+// column) cover the matrix and are dealt to the blocks round-robin, so every
+// block's share is fixed and the sums are reproducible.  A thread keeps its
+// tile of -R, -|R - P1|, P1, P2 and A in registers and runs through all the
+// window's candidates (grouped by k, so E is rebuilt only when k changes);
+// V'_c is read from global memory two candidates ahead, U'_c of the tile's
+// rows from shared memory.
+constexpr int DEL_THREADS = 128;
+constexpr int DEL_COLS = 4 * DEL_THREADS;
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Change of the b-norm terms of a 4 x 4 tile for one candidate:
+//   sum over the tile of ( |R - max(E, u_i + v_j)| - t0 ),  t0 = |R - P1|,
+// where a NaN R (entry not given) gives 0 through fmaxf.  The tile holds -R
+// and -t0, so every addition is a packed FP32x2 add (two lanes of one
+// instruction, each rounded like a scalar add): per entry the terms are the
+// scalar ones, |P' - R| = |R - P'| exactly; the sum is a fixed tree of
+// depth 4.
+__device__ __forceinline__ float tile_change(const float (&nr)[4][4], const float (&nt0)[4][4],
+                                             const float (&E)[4][4], const float4 u, const float4 v)
+{
+    const float uu[4] = {u.x, u.y, u.z, u.w};
+    const float2 v01 = f2(v.x, v.y), v23 = f2(v.z, v.w);
+    float2 q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 ui = f2(uu[i], uu[i]);
+        const float2 x01 = __fadd2_rn(ui, v01), x23 = __fadd2_rn(ui, v23);
+        const float2 a01 = __fadd2_rn(f2(fmaxf(E[i][0], x01.x), fmaxf(E[i][1], x01.y)), f2(nr[i][0], nr[i][1]));
+        const float2 a23 = __fadd2_rn(f2(fmaxf(E[i][2], x23.x), fmaxf(E[i][3], x23.y)), f2(nr[i][2], nr[i][3]));
+        const float2 d01 = __fadd2_rn(f2(fmaxf(fabsf(a01.x), 0.f), fmaxf(fabsf(a01.y), 0.f)), f2(nt0[i][0], nt0[i][1]));
+        const float2 d23 = __fadd2_rn(f2(fmaxf(fabsf(a23.x), 0.f), fmaxf(fabsf(a23.y), 0.f)), f2(nt0[i][2], nt0[i][3]));
+        q[i] = __fadd2_rn(d01, d23);
+    }
+    const float2 s = __fadd2_rn(__fadd2_rn(q[0], q[1]), __fadd2_rn(q[2], q[3]));
+    return s.x + s.y;
+}
+
+__global__ void __launch_bounds__(DEL_THREADS, 4) k_delta(stmf_problem P, int ntiles, int nct)
+{
+    __shared__ float sacc[STMF_WMAX][DEL_THREADS];
+    __shared__ __align__(16) float su[STMF_WMAX][4];
+    __shared__ int sslot[STMF_WMAX], sk[STMF_WMAX];
+    const stmf_ctl *ctl = P.ctl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) atomicMin(&P.ctl->ev_d0, global_ns());
+    const int na = ctl->na;
+    if (tid < na) {
+        const int slot = ctl->alist[tid];
+        sslot[tid] = slot;
+        sk[tid] = P.cand[8 * slot + 1];
+    }
+    for (int c = 0; c < na; ++c) sacc[c][tid] = 0.f;
+    const int nf4 = P.np >> 2;
+    for (int tile = blockIdx.x; tile < ntiles && na > 0; tile += gridDim.x) {
+        const int s0 = (tile / nct) * 4;
+        const int f = (tile % nct) * DEL_THREADS + tid;
+        __syncthreads();
+        for (int e = tid; e < 4 * na; e += DEL_THREADS)
+            su[e >> 2][e & 3] = P.Uc[(size_t)sslot[e >> 2] * P.mp + s0 + (e & 3)];
+        __syncthreads();
+        if (f >= nf4) continue;
+
+        float nr[4][4], nt0[4][4], p1[4][4], p2[4][4], E[4][4];
+        uint32_t aw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const size_t o4 = (size_t)(s0 + i) * nf4 + f;
+            const float4 x = reinterpret_cast<const float4 *>(P.R)[o4];
+            const float4 y = reinterpret_cast<const float4 *>(P.P1)[o4];
+            const float4 z = reinterpret_cast<const float4 *>(P.P2)[o4];
+            aw[i] = reinterpret_cast<const uint32_t *>(P.A)[o4];
+            nr[i][0] = -x.x; nr[i][1] = -x.y; nr[i][2] = -x.z; nr[i][3] = -x.w;
+            nt0[i][0] = -fmaxf(fabsf(x.x - y.x), 0.f); nt0[i][1] = -fmaxf(fabsf(x.y - y.y), 0.f);
+            nt0[i][2] = -fmaxf(fabsf(x.z - y.z), 0.f); nt0[i][3] = -fmaxf(fabsf(x.w - y.w), 0.f);
+            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
+            p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
+        }
+        const float4 *Vc4 = reinterpret_cast<const float4 *>(P.Vc) + f;
+        const size_t ldv4 = (size_t)nf4;
+        float4 vn0 = Vc4[sslot[0] * ldv4];
+        float4 vn1 = na > 1 ? Vc4[sslot[1] * ldv4] : vn0;
+        int kcur = -1;
+#pragma unroll 1
+        for (int c = 0; c < na; ++c) {
+            const float4 v4 = vn0;
+            vn0 = vn1;
+            if (c + 2 < na) vn1 = Vc4[sslot[c + 2] * ldv4];
+            const int k = sk[c];
+            if (k != kcur) {
+                kcur = k;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj)
+                        E[i][jj] = ((aw[i] >> (8 * jj)) & 0xffu) == (uint32_t)k ? p2[i][jj] : p1[i][jj];
+            }
+            const float4 u4 = *reinterpret_cast<const float4 *>(su[c]);
+            sacc[c][tid] += tile_change(nr, nt0, E, u4, v4);
+        }
+    }
+    __syncthreads();
+    // block partial of every candidate, fixed order, in FP64
+    for (int c = warp; c < na; c += DEL_THREADS / 32) {
+        double x = 0.0;
+        for (int t = lane; t < DEL_THREADS; t += 32) x += (double)sacc[c][t];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULLM, x, o);
+        if (lane == 0) P.part[(size_t)sslot[c] * gridDim.x + blockIdx.x] = x;
+    }
+    if (tid == 0) atomicMax(&P.ctl->ev_t1, global_ns());
+}
+
+int res_chunks(int cols) { return (cols + RES_CHUNK - 1) / RES_CHUNK; }
+int res_blocks(int rows) { return (rows + RES_THREADS - 1) / RES_THREADS; }
+
+}  // namespace
+
+int delta_grid(const stmf_problem *P)
+{
+    const int ntiles = ((P->m + 3) / 4) * ((P->np + DEL_COLS - 1) / DEL_COLS);
+    return ntiles < STMF_DELTA_BLOCKS_PER_SM * P->ctx->num_sms ? ntiles : STMF_DELTA_BLOCKS_PER_SM * P->ctx->num_sms;
+}
+
+int delta_depth(const stmf_problem *P)
+{
+    const int ntiles = ((P->m + 3) / 4) * ((P->np + DEL_COLS - 1) / DEL_COLS);
+    const int g = delta_grid(P);
+    return 5 + (ntiles + g - 1) / g;      // tile tree (4) + one per tile a block takes
+}
+
+cudaError_t launch_res(cudaStream_t st, stmf_problem *P)
+{
+    const int nch0 = res_chunks(P->n), nch1 = res_chunks(P->m);
+    const int ntask0 = res_blocks(P->m) * nch0, ntask1 = res_blocks(P->n) * nch1;
+    k_res<<<ntask0 + ntask1, RES_THREADS, 0, st>>>(*P, ntask0, nch0, nch1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delta(cudaStream_t st, stmf_problem *P)
+{
+    const int nct = (P->np + DEL_COLS - 1) / DEL_COLS;
+    const int ntiles = ((P->m + 3) / 4) * nct;
+    k_delta<<<delta_grid(P), DEL_THREADS, 0, st>>>(*P, ntiles, nct);
+    return cudaGetLastError();
+}

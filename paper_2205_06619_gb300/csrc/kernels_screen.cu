@@ -246,6 +246,12 @@ __global__ void __launch_bounds__(1024) k_screen_select(stmf_problem P, int nblk
         const int slot = ctl->vlist[a];
         if (!P.cand[8 * slot + 4]) ctl->vlist[nv2++] = slot;
     }
+    int na2 = 0;
+    for (int a = 0; a < ctl->na; ++a) {
+        const int slot = ctl->alist[a];
+        if (!P.cand[8 * slot + 4]) ctl->alist[na2++] = slot;
+    }
+    ctl->na = na2;
     ctl->nu = nu2;
     ctl->nv = nv2;
     ctl->screened += dropped;
@@ -274,10 +280,9 @@ cudaError_t launch_screen(cudaStream_t st, stmf_problem *P)
     if (e != cudaSuccess) return e;
     // FP32 additions a term passes through: the screen's per-thread sums
     // (one per column-pair step, plus the pair sum) and the FP32 path's
-    // (4-level tile sum plus one per step of an F-ULF row block or an
-    // F-URF column strip)
+    // (tile tree plus one per tile of a phase-2 block)
     const double ds = 2.0 + (P->np / 2 + SCR_THREADS - 1) / SCR_THREADS;
-    const double d32 = 6.0 + (P->np + 1023) / 1024 + (P->mp + 127) / 128;
+    const double d32 = 1.0 + delta_depth(P);
     k_screen_select<<<1, 1024, 0, st>>>(*P, nblk, ds + d32);
     return cudaGetLastError();
 }

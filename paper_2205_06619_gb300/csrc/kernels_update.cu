@@ -300,8 +300,14 @@ __global__ void __launch_bounds__(1024) k_window(stmf_problem P)
             while (b >= 0 && sk[idx[b]] > sk[a]) { idx[b + 1] = idx[b]; --b; }
             idx[b + 1] = a;
         }
-        for (int a = 0; a < cnt; ++a) { ctl->ulist[a] = 2 * idx[a]; ctl->vlist[a] = 2 * idx[a] + 1; }
+        for (int a = 0; a < cnt; ++a) {
+            ctl->ulist[a] = 2 * idx[a];
+            ctl->vlist[a] = 2 * idx[a] + 1;
+            ctl->alist[2 * a] = 2 * idx[a];
+            ctl->alist[2 * a + 1] = 2 * idx[a] + 1;
+        }
         ctl->nc = 2 * cnt;
+        ctl->na = 2 * cnt;
         ctl->nu = cnt;
         ctl->nv = cnt;
         ctl->exhausted = spos >= P.n;
@@ -311,7 +317,9 @@ __global__ void __launch_bounds__(1024) k_window(stmf_problem P)
 }
 
 // Seeds: F-ULF slots get V'_k. from the column statistics, F-URF slots U'_.k
-// from the row statistics.  grid.y = slot, grid.x covers max(np, mp).
+// from the row statistics; the other factor of each slot (the residuation of
+// phase 1, combined with atomic minima) starts at +inf.  grid.y = slot,
+// grid.x covers max(np, mp).
 __global__ void k_seed(stmf_problem P)
 {
     const stmf_ctl *ctl = P.ctl;
@@ -321,6 +329,7 @@ __global__ void k_seed(stmf_problem P)
     const int j = cd[0], k = cd[1], type = cd[2], i = ctl->i;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (type == 0) {
+        if (x < P.mp) P.Uc[(size_t)c * P.mp + x] = INFINITY;
         if (x >= P.np) return;
         const float useed = P.R[(size_t)i * P.np + j] - P.V[(size_t)k * P.np + j];   // U''_ik
         float v = 0.f;
@@ -331,6 +340,7 @@ __global__ void k_seed(stmf_problem P)
         }
         P.Vc[(size_t)c * P.np + x] = v;
     } else {
+        if (x < P.np) P.Vc[(size_t)c * P.np + x] = INFINITY;
         if (x >= P.mp) return;
         const float vseed = P.R[(size_t)i * P.np + j] - P.U[(size_t)i * P.r + k];    // V''_kj
         float u = 0.f;
@@ -341,344 +351,6 @@ __global__ void k_seed(stmf_problem P)
         }
         P.Uc[(size_t)c * P.mp + x] = u;
     }
-}
-
-// Warp reduce-scatter of 32 values: afterwards lane L holds op over the warp
-// of value L.  31 shuffles instead of 32 x 5.
-template <bool MIN>
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane)
-{
-#pragma unroll
-    for (int lvl = 0; lvl < 5; ++lvl) {
-        const int o = 16 >> lvl;
-        const bool upper = lane & o;
-#pragma unroll
-        for (int q = 0; q < o; ++q) {
-            const float send = upper ? v[q] : v[q + o];
-            const float keep = upper ? v[q + o] : v[q];
-            const float recv = __shfl_xor_sync(FULL, send, o);
-            v[q] = MIN ? fminf(keep, recv) : keep + recv;
-        }
-    }
-    return v[0];
-}
-
-// Warp reduce-scatter of 16 values: afterwards lanes 2L and 2L+1 hold op over
-// the warp of value L.
-__device__ __forceinline__ float reduce_scatter16_min(float (&v)[16], int lane)
-{
-#pragma unroll
-    for (int lvl = 0; lvl < 4; ++lvl) {
-        const int o = 8 >> lvl;          // half of the live values
-        const int lo = 16 >> lvl;        // lane offset of this level
-        const bool upper = lane & lo;
-#pragma unroll
-        for (int q = 0; q < o; ++q) {
-            const float send = upper ? v[q] : v[q + o];
-            const float keep = upper ? v[q + o] : v[q];
-            v[q] = fminf(keep, __shfl_xor_sync(FULL, send, lo));
-        }
-    }
-    return fminf(v[0], __shfl_xor_sync(FULL, v[0], 1));
-}
-
-constexpr int CG = 4;          // candidates per phase-1 group (unrolled)
-constexpr int EVAL_THREADS = 256;
-
-struct EvalSmem {
-    float acc[STMF_WMAX / 2][EVAL_THREADS];     // per-thread partial changes, per candidate
-    float su[STMF_WMAX / 2][4];                 // U'_sk of the unit's 4 rows (F-ULF)
-    __align__(16) float sv[STMF_WMAX / 2][32];  // V'_kt of the unit's 32 columns (F-URF)
-    float red[8][32];
-    int sslot[STMF_WMAX / 2], sk[STMF_WMAX / 2];
-    int unit;
-};
-
-// E = max over l != k of (U_sl + V_lt) = (A == k ? P2 : P1) for a 4 x 4 tile.
-__device__ __forceinline__ void load_E(float (&E)[4][4], const float4 *p1, const float4 *p2,
-                                       const uint32_t *a, size_t stride4, int k)
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 x = p1[i * stride4], y = p2[i * stride4];
-        const uint32_t w = a[i * stride4];
-        E[i][0] = ((w & 0xff) == (uint32_t)k) ? y.x : x.x;
-        E[i][1] = (((w >> 8) & 0xff) == (uint32_t)k) ? y.y : x.y;
-        E[i][2] = (((w >> 16) & 0xff) == (uint32_t)k) ? y.z : x.z;
-        E[i][3] = ((w >> 24) == (uint32_t)k) ? y.w : x.w;
-    }
-}
-
-// Change of the b-norm terms of a 4 x 4 tile for one candidate:
-//   sum over the tile of ( |R - max(E, u_i + v_j)| - t0 ),  t0 = |R - P1|,
-// where a NaN R (entry not given) gives 0 through fmaxf.  Pairwise sums.
-__device__ __forceinline__ float tile_change(const float (&rv)[4][4], const float (&t0)[4][4],
-                                             const float (&E)[4][4], const float (&u)[4], const float (&v)[4])
-{
-    float q[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float d[4];
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-            d[jj] = fmaxf(fabsf(rv[i][jj] - fmaxf(E[i][jj], u[i] + v[jj])), 0.f) - t0[i][jj];
-        q[i] = (d[0] + d[1]) + (d[2] + d[3]);
-    }
-    return (q[0] + q[1]) + (q[2] + q[3]);
-}
-
-// Reduces the per-thread partials of every candidate of a unit (fixed order:
-// 32 consecutive threads in FP64 per lane group, then 8 lanes) into
-// part[slot * ldpart + unit].
-__device__ __forceinline__ void reduce_unit(EvalSmem &S, int nc, double *part, int ldpart, int unit)
-{
-    __syncthreads();
-    const int tid = threadIdx.x, cc = tid >> 3, sub = tid & 7;
-    double x = 0.0;
-    if (cc < nc)
-        for (int q = 0; q < 32; ++q) x += (double)S.acc[cc][sub * 32 + q];
-#pragma unroll
-    for (int o = 4; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-    if (cc < nc && sub == 0) part[(size_t)S.sslot[cc] * ldpart + unit] = x;
-}
-
-// F-ULF unit: 4 full rows.  Phase 1: U'_sk = min over t of (R_st - V'_kt) for
-// every F-ULF candidate.  Phase 2: the candidates' change of the error over
-// the 4 rows, accumulated per entry (a candidate that changes nothing gives
-// exactly 0).  MODE 0 runs both phases, MODE 1 phase 1 only, MODE 2 phase 2
-// only, with U' read back from Uc (the window's lists then hold the
-// candidates the FP16 screen kept).
-template <int MODE>
-__device__ __forceinline__ void eval_ulf_unit(const stmf_problem &P, EvalSmem &S, int b, int ldpart)
-{
-    const stmf_ctl *ctl = P.ctl;
-    const int nu = ctl->nu;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int s0 = b * 4;
-    const int nf4 = P.np >> 2;
-    if (tid < nu) {
-        const int slot = ctl->ulist[tid];
-        S.sslot[tid] = slot;
-        S.sk[tid] = P.cand[8 * slot + 1];
-    }
-    if (MODE != 1)
-        for (int cc = 0; cc < nu; ++cc) S.acc[cc][tid] = 0.f;
-    __syncthreads();
-    const float4 *R4 = reinterpret_cast<const float4 *>(P.R + (size_t)s0 * P.np);
-
-    if (MODE == 2) {
-        if (tid < 4 * nu) S.su[tid >> 2][tid & 3] = P.Uc[(size_t)S.sslot[tid >> 2] * P.mp + s0 + (tid & 3)];
-        __syncthreads();
-    }
-    // ---- phase 1
-    for (int g = 0; g < nu && MODE != 2; g += CG) {
-        float acc[4 * CG];
-#pragma unroll
-        for (int q = 0; q < 4 * CG; ++q) acc[q] = INFINITY;
-        for (int f = tid; f < nf4; f += EVAL_THREADS) {
-            float4 r4[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) r4[i] = R4[(size_t)i * nf4 + f];
-#pragma unroll
-            for (int cc = 0; cc < CG; ++cc) {
-                if (g + cc < nu) {
-                    const float4 v4 = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[g + cc] * P.np)[f];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        float a = acc[cc * 4 + i];
-                        a = fminf(a, r4[i].x - v4.x);
-                        a = fminf(a, r4[i].y - v4.y);
-                        a = fminf(a, r4[i].z - v4.z);
-                        a = fminf(a, r4[i].w - v4.w);
-                        acc[cc * 4 + i] = a;
-                    }
-                }
-            }
-        }
-        const float w = reduce_scatter16_min(acc, lane);
-        S.red[warp][lane] = w;
-        __syncthreads();
-        if (tid < 16) {
-            float x = S.red[0][2 * tid];
-#pragma unroll
-            for (int q = 1; q < 8; ++q) x = fminf(x, S.red[q][2 * tid]);
-            const int cc = tid >> 2, i = tid & 3;
-            if (g + cc < nu) {
-                S.su[g + cc][i] = x;
-                P.Uc[(size_t)S.sslot[g + cc] * P.mp + s0 + i] = x;
-            }
-        }
-        __syncthreads();
-    }
-
-    if (MODE == 1) return;
-    // ---- phase 2: a thread owns the 4 rows x 4 columns of one float4 column
-    const float4 *P14 = reinterpret_cast<const float4 *>(P.P1 + (size_t)s0 * P.np);
-    const float4 *P24 = reinterpret_cast<const float4 *>(P.P2 + (size_t)s0 * P.np);
-    const uint32_t *A4 = reinterpret_cast<const uint32_t *>(P.A + (size_t)s0 * P.np);
-    for (int f = tid; f < nf4; f += EVAL_THREADS) {
-        float rv[4][4], t0[4][4], E[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 x = R4[(size_t)i * nf4 + f], y = P14[(size_t)i * nf4 + f];
-            rv[i][0] = x.x; rv[i][1] = x.y; rv[i][2] = x.z; rv[i][3] = x.w;
-            t0[i][0] = fmaxf(fabsf(x.x - y.x), 0.f); t0[i][1] = fmaxf(fabsf(x.y - y.y), 0.f);
-            t0[i][2] = fmaxf(fabsf(x.z - y.z), 0.f); t0[i][3] = fmaxf(fabsf(x.w - y.w), 0.f);
-        }
-        int kcur = -1;
-        // the next candidate's V' columns are loaded one iteration ahead
-        float4 vnext = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[0] * P.np)[f];
-#pragma unroll 1
-        for (int cc = 0; cc < nu; ++cc) {
-            const float4 v4 = vnext;
-            if (cc + 1 < nu) vnext = reinterpret_cast<const float4 *>(P.Vc + (size_t)S.sslot[cc + 1] * P.np)[f];
-            const int k = S.sk[cc];
-            if (k != kcur) {
-                load_E(E, P14 + f, P24 + f, A4 + f, nf4, k);
-                kcur = k;
-            }
-            const float4 u4 = *reinterpret_cast<const float4 *>(&S.su[cc][0]);
-            const float u[4] = {u4.x, u4.y, u4.z, u4.w};
-            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-            S.acc[cc][tid] += tile_change(rv, t0, E, u, v);
-        }
-    }
-    reduce_unit(S, nu, P.part_ulf, ldpart, b);
-}
-
-// F-URF unit: a strip of 32 full columns.  Phase 1: V'_kt = min over s of
-// (R_st - U'_sk) from rows of RT (warp w owns columns 4w .. 4w+3).  Phase 2:
-// the candidates' change of the error over the strip.  MODE as for F-ULF
-// (MODE 2 reads V' back from Vc).
-template <int MODE>
-__device__ __forceinline__ void eval_urf_unit(const stmf_problem &P, EvalSmem &S, int b, int ldpart)
-{
-    const stmf_ctl *ctl = P.ctl;
-    const int nv = ctl->nv;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t0c = b * 32;
-    if (tid < nv) {
-        const int slot = ctl->vlist[tid];
-        S.sslot[tid] = slot;
-        S.sk[tid] = P.cand[8 * slot + 1];
-    }
-    if (MODE != 1)
-        for (int cc = 0; cc < nv; ++cc) S.acc[cc][tid] = 0.f;
-    __syncthreads();
-
-    if (MODE == 2) {
-        for (int e = tid; e < 32 * nv; e += EVAL_THREADS)
-            S.sv[e >> 5][e & 31] = P.Vc[(size_t)S.sslot[e >> 5] * P.np + t0c + (e & 31)];
-    }
-    // ---- phase 1
-    if (MODE != 2) {
-        const int nf4 = P.mp >> 2;
-        const float4 *X4 = reinterpret_cast<const float4 *>(P.RT + (size_t)(t0c + 4 * warp) * P.mp);
-        for (int g = 0; g < nv; g += CG) {
-            float acc[4 * CG];
-#pragma unroll
-            for (int q = 0; q < 4 * CG; ++q) acc[q] = INFINITY;
-            for (int f = lane; f < nf4; f += 32) {
-                float4 x4[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) x4[i] = X4[(size_t)i * nf4 + f];
-#pragma unroll
-                for (int cc = 0; cc < CG; ++cc) {
-                    if (g + cc < nv) {
-                        const float4 u4 = reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[g + cc] * P.mp)[f];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            float a = acc[cc * 4 + i];
-                            a = fminf(a, x4[i].x - u4.x);
-                            a = fminf(a, x4[i].y - u4.y);
-                            a = fminf(a, x4[i].z - u4.z);
-                            a = fminf(a, x4[i].w - u4.w);
-                            acc[cc * 4 + i] = a;
-                        }
-                    }
-                }
-            }
-            const float x = reduce_scatter16_min(acc, lane);
-            const int cc = lane >> 3, i = (lane >> 1) & 3;
-            if ((lane & 1) == 0 && g + cc < nv) {
-                S.sv[g + cc][4 * warp + i] = x;
-                P.Vc[(size_t)S.sslot[g + cc] * P.np + t0c + 4 * warp + i] = x;
-            }
-        }
-    }
-    __syncthreads();
-    if (MODE == 1) return;
-
-    // ---- phase 2: a thread owns 4 consecutive rows x 4 columns per step
-    const int cl = tid & 7, rl = tid >> 3;
-    const int tc = t0c + cl * 4;
-    const size_t st4 = (size_t)(P.np >> 2);
-    for (int sb = rl * 4; sb < P.m; sb += 128) {
-        const size_t off4 = ((size_t)sb * P.np + tc) >> 2;
-        const float4 *R4 = reinterpret_cast<const float4 *>(P.R) + off4;
-        const float4 *P14 = reinterpret_cast<const float4 *>(P.P1) + off4;
-        const float4 *P24 = reinterpret_cast<const float4 *>(P.P2) + off4;
-        const uint32_t *A4 = reinterpret_cast<const uint32_t *>(P.A) + off4;
-        float rv[4][4], t0[4][4], E[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 x = R4[i * st4], y = P14[i * st4];
-            rv[i][0] = x.x; rv[i][1] = x.y; rv[i][2] = x.z; rv[i][3] = x.w;
-            t0[i][0] = fmaxf(fabsf(x.x - y.x), 0.f); t0[i][1] = fmaxf(fabsf(x.y - y.y), 0.f);
-            t0[i][2] = fmaxf(fabsf(x.z - y.z), 0.f); t0[i][3] = fmaxf(fabsf(x.w - y.w), 0.f);
-        }
-        int kcur = -1;
-        // the next candidate's U' rows are loaded one iteration ahead
-        float4 unext = *reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[0] * P.mp + sb);
-#pragma unroll 1
-        for (int cc = 0; cc < nv; ++cc) {
-            const float4 u4 = unext;
-            if (cc + 1 < nv) unext = *reinterpret_cast<const float4 *>(P.Uc + (size_t)S.sslot[cc + 1] * P.mp + sb);
-            const int k = S.sk[cc];
-            if (k != kcur) {
-                load_E(E, P14, P24, A4, st4, k);
-                kcur = k;
-            }
-            const float4 v4 = *reinterpret_cast<const float4 *>(&S.sv[cc][cl * 4]);
-            const float u[4] = {u4.x, u4.y, u4.z, u4.w};
-            const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-            S.acc[cc][tid] += tile_change(rv, t0, E, u, v);
-        }
-    }
-    reduce_unit(S, nv, P.part_urf, ldpart, b);
-}
-
-// One launch evaluates the whole window with persistent blocks that take
-// units from a queue: the 32-column F-URF strips (the larger units) first,
-// then the 4-row F-ULF blocks.
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(EVAL_THREADS, 2) k_eval(stmf_problem P, int nb_ulf, int nb_urf)
-{
-    __shared__ EvalSmem S;
-    // the launch's duration (first block start to last block end) is
-    // recorded with the global nanosecond timer: the kernel runs inside a
-    // CUDA graph, where no event can bracket a single node
-    if (threadIdx.x == 0) atomicMin(&P.ctl->ev_t0, global_ns());
-    const int total = (P.ctl->nv ? nb_urf : 0) + (P.ctl->nu ? nb_ulf : 0);
-    const int first_ulf = P.ctl->nv ? nb_urf : 0;
-    while (true) {
-        if (threadIdx.x == 0) S.unit = atomicAdd(&P.ctl->eval_next, 1);
-        __syncthreads();
-        const int u = S.unit;
-        __syncthreads();
-        if (u >= total) break;
-        if (u < first_ulf) eval_urf_unit<MODE>(P, S, u, nb_urf);
-        else eval_ulf_unit<MODE>(P, S, u - first_ulf, nb_ulf);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicMax(&P.ctl->ev_t1, global_ns());
 }
 
 __device__ __forceinline__ void put_trace(stmf_ctl *ctl, int pos, int j, int k, int type, double f)
@@ -692,13 +364,13 @@ __device__ __forceinline__ void put_trace(stmf_ctl *ctl, int pos, int j, int k, 
     ctl->ntrace += 1;
 }
 
-// End of a window: sums the block partials of every candidate (fixed order)
+// End of a window: sums the phase-2 block partials of every candidate (fixed order)
 // into its change Delta = f' - f, keeps the first candidate in the paper's
 // order with Delta < 0 (select_mode 1: the smallest), commits it, writes the
 // trace record and advances the row.  In a graph it also sets the
 // conditions of the row loop: h_win (another window of this row), h_dirty
 // (refresh before the next row), h_row (another row in this sweep).
-__global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nb_ulf, int nb_urf, int in_graph, int single,
+__global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int in_graph, int single,
                                                 cudaGraphConditionalHandle h_row,
                                                 cudaGraphConditionalHandle h_dirty,
                                                 cudaGraphConditionalHandle h_win)
@@ -713,11 +385,9 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nb_ulf, int
             if (lane == 0) { sf[c] = INFINITY; P.fc[c] = INFINITY; }
             continue;
         }
-        const int type = P.cand[8 * c + 2];
-        const int nb = type == 0 ? nb_ulf : nb_urf;
-        const double *part = (type == 0 ? P.part_ulf : P.part_urf) + (size_t)c * nb;
+        const double *part = P.part + (size_t)c * nblk;
         double x = 0.0;
-        for (int b = lane; b < nb; b += 32) x += part[b];
+        for (int b = lane; b < nblk; b += 32) x += part[b];
 #pragma unroll
         for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
         if (lane == 0) { sf[c] = x; P.fc[c] = ctl->f + x; }
@@ -738,9 +408,13 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nb_ulf, int
             ctl->eval_ns += (long long)(ctl->ev_t1 - ctl->ev_t0);
             ctl->eval_launches += 1;
             ctl->eval_cands += nc;
+            if (ctl->ev_r1 > ctl->ev_t0) ctl->res_ns += (long long)(ctl->ev_r1 - ctl->ev_t0);
+            if (ctl->ev_t1 > ctl->ev_d0) ctl->delta_ns += (long long)(ctl->ev_t1 - ctl->ev_d0);
         }
         ctl->ev_t0 = ~0ull;
         ctl->ev_t1 = 0ull;
+        ctl->ev_r1 = 0ull;
+        ctl->ev_d0 = ~0ull;
         ctl->tried += (ctl->select_mode == 0 && kept >= 0) ? kept + 1 : nc;
         ctl->ncand_row += nc;
         ctl->kept = kept >= 0;
@@ -843,6 +517,8 @@ __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
     ctl->nv = type == 1 ? 1 : 0;
     ctl->ulist[0] = 0;
     ctl->vlist[0] = 0;
+    ctl->alist[0] = 0;
+    ctl->na = 1;
     ctl->exhausted = 1;
     ctl->ncand_row = 0;
     ctl->select_mode = 0;
@@ -936,17 +612,13 @@ cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots)
     return cudaGetLastError();
 }
 
-static inline int nb_ulf(const stmf_problem *P) { return (P->m + 3) / 4; }
-static inline int nb_urf(const stmf_problem *P) { return (P->n + 31) / 32; }
-
+// mode 0: both phases; 1: phase 1 (residuations); 2: phase 2 (error changes).
 cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode)
 {
-    const int units = nb_ulf(P) + nb_urf(P);
-    const int blocks = min(units, 2 * P->ctx->num_sms);
-    if (mode == 1) k_eval<1><<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
-    else if (mode == 2) k_eval<2><<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
-    else k_eval<0><<<blocks, EVAL_THREADS, 0, st>>>(*P, nb_ulf(P), nb_urf(P));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (mode != 2) e = launch_res(st, P);
+    if (e == cudaSuccess && mode != 1) e = launch_delta(st, P);
+    return e;
 }
 
 // One window of a row: candidates, seeds, evaluation, decision.  With FP16
@@ -969,7 +641,7 @@ cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph)
 
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single)
 {
-    k_select<<<1, 1024, 0, st>>>(*P, nb_ulf(P), nb_urf(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
+    k_select<<<1, 1024, 0, st>>>(*P, delta_grid(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
     return cudaGetLastError();
 }
 

@@ -92,7 +92,7 @@ void problem_free(stmf_problem *P)
     if (P->sweep_graph) cudaGraphDestroy(P->sweep_graph);
     void *ptrs[] = {P->R, P->RT, P->U, P->V, P->P1, P->P2, P->A, P->cmin1, P->cmin2, P->carg,
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
-                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part_ulf, P->part_urf, P->fc,
+                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
                     P->scr_umax, P->scr_vmax};
     for (void *q : ptrs)
@@ -129,7 +129,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     A(dalloc(&P->tdcol, np)); A(dalloc(&P->colhist, np * r)); A(dalloc(&P->rowhist, STMF_MAX_RANK));
     A(dalloc(&P->rank, np)); A(dalloc(&P->order, np)); A(dalloc(&P->cand, 8 * STMF_WMAX));
     A(dalloc(&P->Uc, (size_t)STMF_WMAX * mp)); A(dalloc(&P->Vc, (size_t)STMF_WMAX * np));
-    A(dalloc(&P->part_ulf, (mp / 4) * STMF_WMAX)); A(dalloc(&P->part_urf, (np / 32) * STMF_WMAX));
+    A(dalloc(&P->part, (size_t)STMF_DELTA_BLOCKS_PER_SM * ctx->num_sms * STMF_WMAX));
     A(dalloc(&P->fc, STMF_WMAX)); A(dalloc(&P->ctl, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&P->ctl_host, sizeof(stmf_ctl));
     if (e != cudaSuccess) {
@@ -146,6 +146,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     c.wmax = window;
     c.dirty_k = -1;
     c.ev_t0 = ~0ull;
+    c.ev_d0 = ~0ull;
     e = cudaMemsetAsync(P->U, 0, sizeof(float) * mp * r, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->V, 0, sizeof(float) * r * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P1, 0, sizeof(float) * mp * np, st);
@@ -544,6 +545,8 @@ void fill_report(const stmf_problem *P, stmf_report *rep)
     rep->eval_candidates = c.eval_cands;
     rep->seconds = P->seconds;
     rep->candidates_screened = c.screened;
+    rep->eval_res_ns = c.res_ns;
+    rep->eval_delta_ns = c.delta_ns;
 }
 
 stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *trace_out, int64_t trace_cap)
@@ -912,7 +915,7 @@ stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_pr
 
 stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops)
 {
-    if (!ctx || !gops || iters < 1 || mode < 0 || mode > 3) return fail(ctx, STMF_ERR_INVALID, "bad arguments");
+    if (!ctx || !gops || iters < 1 || mode < 0 || mode > 5) return fail(ctx, STMF_ERR_INVALID, "bad arguments");
     CK(cudaSetDevice(ctx->device));
     float *sink = nullptr;
     CK(cudaMalloc(&sink, 256 * sizeof(float)));
@@ -930,7 +933,7 @@ stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops)
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(sink);
-    const double lane_ops = (double)blocks * 256.0 * iters * 8.0 * 2.0 * (mode == 3 ? 2.0 : 1.0);
+    const double lane_ops = (double)blocks * 256.0 * iters * 8.0 * 2.0 * (mode >= 3 ? 2.0 : 1.0);
     *gops = lane_ops / (ms * 1e-3) / 1e9;
     return STMF_OK;
 }
