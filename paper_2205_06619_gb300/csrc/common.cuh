@@ -22,7 +22,7 @@
 
 #define STMF_PAD 256
 #define STMF_WMAX 64          // candidates per device window (upper bound)
-#define STMF_DELTA_BLOCKS_PER_SM 4   // resident blocks of the phase-2 kernel
+#define STMF_DELTA_MAX_BLOCKS_PER_SM 8   // capacity of the phase-2 partials, per SM
 
 static inline int stmf_roundup(int x, int a) { return (x + a - 1) / a * a; }
 

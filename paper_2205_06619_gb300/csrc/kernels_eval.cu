@@ -40,11 +40,45 @@ __device__ __forceinline__ void atomic_min_float(float *addr, float v)
 // with the F-URF candidates' U'_c.  The candidates' values of the chunk are
 // staged in shared memory and read as warp-wide broadcasts; each thread owns
 // one row and keeps the running minima of all the type's candidates in
-// registers (no cross-thread reduction).  Chunks combine through atomic
-// minima, which are exact in any order.  NaN entries (not given, padding)
-// drop out of fminf.
+// registers (no cross-thread reduction).  The candidate loop is unrolled for
+// a compile-time count NB >= cnt (4, 8, 16 or 32, picked per block) so the
+// minima of different candidates interleave; the slots above cnt compute on
+// whatever the staging area holds and are never stored.  Chunks combine
+// through atomic minima, which are exact in any order.  NaN entries (not
+// given, padding) drop out of fminf.
 constexpr int RES_THREADS = 128;
-constexpr int RES_CHUNK = 256;
+constexpr int RES_CHUNK = 128;
+
+__device__ __forceinline__ float min8(float4 a, float4 b, float4 w0, float4 w1)
+{
+    const float m0 = fminf(fminf(a.x - w0.x, a.y - w0.y), fminf(a.z - w0.z, a.w - w0.w));
+    const float m1 = fminf(fminf(b.x - w1.x, b.y - w1.y), fminf(b.z - w1.z, b.w - w1.w));
+    return fminf(m0, m1);
+}
+
+template <int NB>
+__device__ __forceinline__ void res_rows(const float4 *x4, const float (*sW)[RES_CHUNK], const int *sslot, int cnt,
+                                         float *OUT, size_t ldo, int row)
+{
+    float acc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc[c] = INFINITY;
+    float4 a = x4[0], b = x4[1];
+#pragma unroll 1
+    for (int q = 0; q < RES_CHUNK / 4; q += 2) {
+        const float4 ca = a, cb = b;
+        if (q + 2 < RES_CHUNK / 4) { a = x4[q + 2]; b = x4[q + 3]; }     // next 8 columns in flight
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+            const float4 w0 = reinterpret_cast<const float4 *>(sW[c])[q];
+            const float4 w1 = reinterpret_cast<const float4 *>(sW[c])[q + 1];
+            acc[c] = fminf(acc[c], min8(ca, cb, w0, w1));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+        if (c < cnt && acc[c] < INFINITY) atomic_min_float(OUT + sslot[c] * ldo + row, acc[c]);
+}
 
 __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0, int nch0, int nch1)
 {
@@ -80,30 +114,11 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
     __syncthreads();
     const int row = rb * RES_THREADS + tid;
     if (row < nrows) {
-        float acc[NCT];
-#pragma unroll
-        for (int c = 0; c < NCT; ++c) acc[c] = INFINITY;
         const float4 *x4 = reinterpret_cast<const float4 *>(X + row * ldx + c0);
-#pragma unroll 1
-        for (int q = 0; q < RES_CHUNK / 4; q += 2) {
-            const float4 a = x4[q], b = x4[q + 1];
-#pragma unroll
-            for (int c = 0; c < NCT; ++c) {
-                if (c < cnt) {
-                    const float4 w0 = reinterpret_cast<const float4 *>(sW[c])[q];
-                    const float4 w1 = reinterpret_cast<const float4 *>(sW[c])[q + 1];
-                    float m = acc[c];
-                    m = fminf(m, a.x - w0.x); m = fminf(m, a.y - w0.y);
-                    m = fminf(m, a.z - w0.z); m = fminf(m, a.w - w0.w);
-                    m = fminf(m, b.x - w1.x); m = fminf(m, b.y - w1.y);
-                    m = fminf(m, b.z - w1.z); m = fminf(m, b.w - w1.w);
-                    acc[c] = m;
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < NCT; ++c)
-            if (c < cnt && acc[c] < INFINITY) atomic_min_float(OUT + sslot[c] * ldo + row, acc[c]);
+        if (cnt <= 4) res_rows<4>(x4, sW, sslot, cnt, OUT, ldo, row);
+        else if (cnt <= 8) res_rows<8>(x4, sW, sslot, cnt, OUT, ldo, row);
+        else if (cnt <= 16) res_rows<16>(x4, sW, sslot, cnt, OUT, ldo, row);
+        else res_rows<32>(x4, sW, sslot, cnt, OUT, ldo, row);
     }
     __syncthreads();
     if (tid == 0) atomicMax(&P.ctl->ev_r1, global_ns());
@@ -119,6 +134,8 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
 // rows from shared memory.
 constexpr int DEL_THREADS = 128;
 constexpr int DEL_COLS = 4 * DEL_THREADS;
+constexpr int DEL_BLOCKS_PER_SM = 4;
+static_assert(DEL_BLOCKS_PER_SM <= STMF_DELTA_MAX_BLOCKS_PER_SM, "phase-2 partials buffer too small");
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
@@ -149,7 +166,7 @@ __device__ __forceinline__ float tile_change(const float (&nr)[4][4], const floa
     return s.x + s.y;
 }
 
-__global__ void __launch_bounds__(DEL_THREADS, 4) k_delta(stmf_problem P, int ntiles, int nct)
+__global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_problem P, int ntiles, int nct)
 {
     __shared__ float sacc[STMF_WMAX][DEL_THREADS];
     __shared__ __align__(16) float su[STMF_WMAX][4];
@@ -232,7 +249,8 @@ int res_blocks(int rows) { return (rows + RES_THREADS - 1) / RES_THREADS; }
 int delta_grid(const stmf_problem *P)
 {
     const int ntiles = ((P->m + 3) / 4) * ((P->np + DEL_COLS - 1) / DEL_COLS);
-    return ntiles < STMF_DELTA_BLOCKS_PER_SM * P->ctx->num_sms ? ntiles : STMF_DELTA_BLOCKS_PER_SM * P->ctx->num_sms;
+    const int cap = DEL_BLOCKS_PER_SM * P->ctx->num_sms;
+    return ntiles < cap ? ntiles : cap;
 }
 
 int delta_depth(const stmf_problem *P)
