@@ -52,7 +52,9 @@ ALU_PEAK_TOPS = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes (read + write) per k_eval launch from the ncu capture summarised in
 # profiles/k_eval_gene_1000x5000_r10.md (cold cache, gene workload); valid only
 # for the kernel source it was taken on
-EVAL_TRAFFIC = {"source_sha256_prefix": "none", "bytes": None, "workload": "gene"}
+# k_delta DRAM bytes per launch (read + write), ncu capture of the gene
+# workload (profiles/k_delta_gene_1000x5000_r10.md), valid for this source
+EVAL_TRAFFIC = {"source_sha256_prefix": "ebbaabe2edd4bdf5", "bytes": 68.23e6, "workload": "gene"}
 
 
 def eval_traffic(workload_name):
