@@ -47,7 +47,7 @@ struct stmf_ctl {
     int pos;           // next position in the column order
     int row_start;     // 1 before the first window of a row
     int wj;            // j-candidates of the next window (each gives F-ULF, F-URF)
-    int wj0;           // j-candidates of a row's first window
+    int wj0;           // j-candidates of a row's first window (what the previous row consumed)
     int wmax;          // candidates per window (upper bound, even)
     int nc;            // candidates in the current window
     int ncand_row;     // candidates of the row consumed so far
@@ -160,7 +160,6 @@ cudaError_t launch_acol(cudaStream_t st, const float *R, int ld, int m, int n, i
 cudaError_t launch_copy_rows(cudaStream_t st, const float *src, int lds, float *dst, int ldd,
                              int rows, int cols);
 cudaError_t launch_stats(cudaStream_t st, stmf_problem *P);
-cudaError_t launch_window(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots);
 cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode = 0);
 cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph);

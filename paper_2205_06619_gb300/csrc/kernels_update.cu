@@ -229,8 +229,10 @@ __global__ void __launch_bounds__(256) k_stats(stmf_problem P)
 // R_ij given; k_j = argmax_l (rowhist_i[l] + colhist[j][l]) (TD_A; the multiset
 // union adds multiplicities; smaller l on ties).  Each j gives F-ULF (slot 2a)
 // then F-URF (slot 2a+1), the order in which Algorithm 3 tries them.  At the
-// first window of a row the row histogram is rebuilt.
-__global__ void __launch_bounds__(1024) k_window(stmf_problem P)
+// first window of a row the row histogram is rebuilt.  Runs in a block of
+// 1024 threads: at the start of a row (k_row_begin) and after a window that
+// neither kept a candidate nor exhausted the row (k_select).
+__device__ __forceinline__ void build_window(const stmf_problem &P, bool row_start)
 {
     __shared__ int sh[STMF_MAX_RANK];
     __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2];
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(1024) k_window(stmf_problem P)
     stmf_ctl *ctl = P.ctl;
     const int i = ctl->i, tid = threadIdx.x, r = P.r;
     const float *Ri = P.R + (size_t)i * P.np;
-    if (ctl->row_start) {
+    if (row_start) {
         if (tid < r) sh[tid] = 0;
         __syncthreads();
         const uint8_t *Ai = P.A + (size_t)i * P.np;
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(1024) k_window(stmf_problem P)
         __syncthreads();
     } else {
         if (tid < r) sh[tid] = P.rowhist[tid];
+        __syncthreads();
     }
     if (tid < 32) {
         const int want = min(ctl->wj, ctl->wmax / 2);
@@ -380,17 +383,28 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
     stmf_ctl *ctl = P.ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = ctl->nc;
-    for (int c = warp; c < nc; c += 32) {
-        if (P.cand[8 * c + 4]) {          // proved non-improving by the FP16 screen
-            if (lane == 0) { sf[c] = INFINITY; P.fc[c] = INFINITY; }
-            continue;
-        }
-        const double *part = P.part + (size_t)c * nblk;
+    // 16 threads per candidate, four independent partial sums each (the
+    // loads of a thread are all in flight together); fixed order
+    {
+        const int c = tid >> 4, sub = tid & 15;
         double x = 0.0;
-        for (int b = lane; b < nblk; b += 32) x += part[b];
+        const bool live = c < nc && !P.cand[8 * c + 4];    // dropped: proved non-improving by the FP16 screen
+        if (live) {
+            const double *part = P.part + (size_t)c * nblk;
+            double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+            int b = sub;
+            for (; b + 48 < nblk; b += 64) {
+                x0 += part[b]; x1 += part[b + 16]; x2 += part[b + 32]; x3 += part[b + 48];
+            }
+            for (; b < nblk; b += 16) x0 += part[b];
+            x = (x0 + x1) + (x2 + x3);
+        }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-        if (lane == 0) { sf[c] = x; P.fc[c] = ctl->f + x; }
+        for (int o = 8; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        if (c < nc && sub == 0) {
+            sf[c] = live ? x : INFINITY;
+            P.fc[c] = live ? ctl->f + x : INFINITY;
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -439,7 +453,16 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
                 ctl->wj = min(ctl->wj * 2, ctl->wmax / 2);
                 ctl->row_done = 0;
             }
-            if (ctl->row_done) ctl->i += 1;
+            if (ctl->row_done) {
+                ctl->i += 1;
+                // the next row's first window covers as many columns as this
+                // row consumed (rounded up to a power of two): a window's
+                // size never changes the decision, only the work per launch
+                const int used = kept >= 0 ? P.cand[8 * kept + 3] + 1 : ctl->ncand_row / 2;
+                int w = 2;
+                while (w < used && w < ctl->wmax / 2) w *= 2;
+                ctl->wj0 = w;
+            }
             if (in_graph) {
                 cudaGraphSetConditional(h_win, ctl->row_done ? 0u : 1u);
                 if (ctl->row_done) {
@@ -456,19 +479,28 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         for (int s = tid; s < P.m; s += 1024) P.U[(size_t)s * P.r + k] = P.Uc[(size_t)kept * P.mp + s];
         for (int t = tid; t < P.n; t += 1024) P.V[(size_t)k * P.np + t] = P.Vc[(size_t)kept * P.np + t];
     }
+    if (!single) {
+        __syncthreads();
+        if (!ctl->row_done) build_window(P, false);
+    }
 }
 
-// Start of a row: row state reset; in a graph, opens the window loop.
-__global__ void k_row_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_win)
+// Start of a row: row state reset and the row's first window; in a graph,
+// opens the window loop.
+__global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_win)
 {
     stmf_ctl *ctl = P.ctl;
-    ctl->row_start = 1;
-    ctl->pos = 0;
-    ctl->ncand_row = 0;
-    ctl->wj = ctl->wj0;
-    ctl->kept = 0;
-    ctl->row_done = 0;
-    if (in_graph) cudaGraphSetConditional(h_win, 1u);
+    if (threadIdx.x == 0) {
+        ctl->row_start = 1;
+        ctl->pos = 0;
+        ctl->ncand_row = 0;
+        ctl->wj = ctl->wj0;
+        ctl->kept = 0;
+        ctl->row_done = 0;
+        if (in_graph) cudaGraphSetConditional(h_win, 1u);
+    }
+    __syncthreads();
+    build_window(P, true);
 }
 
 // Start of a sweep: row 0; in a graph, opens the row loop and asks for a
@@ -599,11 +631,6 @@ cudaError_t launch_stats(cudaStream_t st, stmf_problem *P)
     return cudaGetLastError();
 }
 
-cudaError_t launch_window(cudaStream_t st, stmf_problem *P)
-{
-    k_window<<<1, 1024, 0, st>>>(*P);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots)
 {
@@ -621,13 +648,13 @@ cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode)
     return e;
 }
 
-// One window of a row: candidates, seeds, evaluation, decision.  With FP16
-// screening the evaluation splits into phase 1 (every candidate's U'/V'),
-// the screen, and phase 2 over the candidates it kept.
+// One window of a row (its candidates were chosen by k_row_begin or by the
+// previous k_select): seeds, evaluation, decision and the next window.  With
+// FP16 screening the evaluation splits into phase 1 (every candidate's
+// U'/V'), the screen, and phase 2 over the candidates it kept.
 cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph)
 {
-    cudaError_t e = launch_window(st, P);
-    if (e == cudaSuccess) e = launch_seed(st, P, P->ctl_host->wmax);
+    cudaError_t e = launch_seed(st, P, P->ctl_host->wmax);
     if (P->precision == 1) {
         if (e == cudaSuccess) e = launch_eval(st, P, 1);
         if (e == cudaSuccess) e = launch_screen(st, P);
@@ -659,7 +686,7 @@ cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P)
 
 cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph)
 {
-    k_row_begin<<<1, 1, 0, st>>>(*P, in_graph, P->h_win);
+    k_row_begin<<<1, 1024, 0, st>>>(*P, in_graph, P->h_win);
     return cudaGetLastError();
 }
 
