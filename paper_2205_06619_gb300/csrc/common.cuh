@@ -26,6 +26,23 @@
 
 static inline int stmf_roundup(int x, int a) { return (x + a - 1) / a * a; }
 
+// Float-float (hi, lo) accumulation, about 48 significant bits, with FP32
+// operations only (FP64 is slow on this part).  Knuth's TwoSum on the high
+// parts, the low parts added to its error, then renormalised.
+struct stmf_ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ stmf_ff ff_add(stmf_ff a, stmf_ff b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
 struct stmf_ctx {
     int device;
     cudaStream_t stream;
@@ -105,14 +122,14 @@ struct stmf_problem {
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
-    double *part;      // STMF_WMAX x (phase-2 blocks) partial changes
+    float2 *part;      // STMF_WMAX x (phase-2 blocks) partial changes, float-float (hi, lo)
     double *fc;        // STMF_WMAX candidate errors
     // FP16 screening (precision 1; all NULL otherwise)
     int precision;
     __half *Rh, *P1h, *P2h;
     int scr_blocks;    // row blocks of the screen
-    double *scr_sum;   // STMF_WMAX x scr_blocks screened changes
-    double *scr_cnt;   // STMF_WMAX x scr_blocks counts of possibly changed given entries
+    float2 *scr_sum;   // STMF_WMAX x scr_blocks screened changes (float-float)
+    float2 *scr_cnt;   // STMF_WMAX x scr_blocks counts of possibly changed given entries (float-float)
     float *scr_umax;   // STMF_WMAX x scr_blocks max |U'_sk| over the block's rows
     float *scr_vmax;   // STMF_WMAX max |V'_kt| over t < n
     stmf_ctl *ctl;     // device control block

@@ -230,13 +230,14 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
         }
     }
     __syncthreads();
-    // block partial of every candidate, fixed order, in FP64
+    // block partial of every candidate, fixed order, float-float
     for (int c = warp; c < na; c += DEL_THREADS / 32) {
-        double x = 0.0;
-        for (int t = lane; t < DEL_THREADS; t += 32) x += (double)sacc[c][t];
+        stmf_ff x = {0.f, 0.f};
+        for (int t = lane; t < DEL_THREADS; t += 32) x = ff_add(x, {sacc[c][t], 0.f});
 #pragma unroll
-        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULLM, x, o);
-        if (lane == 0) P.part[(size_t)sslot[c] * gridDim.x + blockIdx.x] = x;
+        for (int o = 16; o; o >>= 1)
+            x = ff_add(x, {__shfl_xor_sync(FULLM, x.hi, o), __shfl_xor_sync(FULLM, x.lo, o)});
+        if (lane == 0) P.part[(size_t)sslot[c] * gridDim.x + blockIdx.x] = make_float2(x.hi, x.lo);
     }
     if (tid == 0) atomicMax(&P.ctl->ev_t1, global_ns());
 }

@@ -26,7 +26,9 @@
 //    <= (4.02 + 2.03 D_32) u M (D = the number of FP32 additions a term
 //    passes through).
 //  * Drop iff Delta_half > 1.01 |S| W, W the per-entry sum of the above; no
-//    dropping at all when M > 16384 (half overflow).
+//    dropping at all when M > 16384 (half overflow).  The block and grid sums
+//    of both paths are float-float (relative error below 2^-44 over their
+//    depth), far inside the 1% margin.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -181,20 +183,20 @@ __global__ void __launch_bounds__(SCR_THREADS) k_screen(stmf_problem P, int wmax
     }
     __syncthreads();
     for (int c = warp; c < ncl; c += SCR_THREADS / 32) {
-        double x = 0.0, y = 0.0;
+        stmf_ff x = {0.f, 0.f}, y = {0.f, 0.f};
         for (int t = lane; t < SCR_THREADS; t += 32) {
             const float2 a = sacc[c * SCR_THREADS + t];
-            x += a.x;
-            y += a.y;
+            x = ff_add(x, {a.x, 0.f});
+            y = ff_add(y, {a.y, 0.f});
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
-            x += __shfl_xor_sync(FULLM, x, o);
-            y += __shfl_xor_sync(FULLM, y, o);
+            x = ff_add(x, {__shfl_xor_sync(FULLM, x.hi, o), __shfl_xor_sync(FULLM, x.lo, o)});
+            y = ff_add(y, {__shfl_xor_sync(FULLM, y.hi, o), __shfl_xor_sync(FULLM, y.lo, o)});
         }
         if (lane == 0) {
-            P.scr_sum[(size_t)sslot[c] * nblk + b] = x;
-            P.scr_cnt[(size_t)sslot[c] * nblk + b] = y;
+            P.scr_sum[(size_t)sslot[c] * nblk + b] = make_float2(x.hi, x.lo);
+            P.scr_cnt[(size_t)sslot[c] * nblk + b] = make_float2(y.hi, y.lo);
         }
     }
 }
@@ -209,17 +211,21 @@ __global__ void __launch_bounds__(1024) k_screen_select(stmf_problem P, int nblk
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = ctl->nc;
     for (int c = warp; c < nc; c += 32) {
-        double x = 0.0, y = 0.0;
+        stmf_ff x = {0.f, 0.f}, y = {0.f, 0.f};
         for (int b = lane; b < nblk; b += 32) {
-            x += P.scr_sum[(size_t)c * nblk + b];
-            y += P.scr_cnt[(size_t)c * nblk + b];
+            const float2 p = P.scr_sum[(size_t)c * nblk + b], q = P.scr_cnt[(size_t)c * nblk + b];
+            x = ff_add(x, {p.x, p.y});
+            y = ff_add(y, {q.x, q.y});
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
-            x += __shfl_xor_sync(FULLM, x, o);
-            y += __shfl_xor_sync(FULLM, y, o);
+            x = ff_add(x, {__shfl_xor_sync(FULLM, x.hi, o), __shfl_xor_sync(FULLM, x.lo, o)});
+            y = ff_add(y, {__shfl_xor_sync(FULLM, y.hi, o), __shfl_xor_sync(FULLM, y.lo, o)});
         }
-        if (lane == 0) { sd[c] = x; sn[c] = y; }
+        if (lane == 0) {
+            sd[c] = (double)x.hi + (double)x.lo;
+            sn[c] = (double)y.hi + (double)y.lo;
+        }
     }
     __syncthreads();
     if (tid != 0) return;

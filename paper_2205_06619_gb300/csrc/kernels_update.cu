@@ -383,27 +383,30 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
     stmf_ctl *ctl = P.ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nc = ctl->nc;
-    // 16 threads per candidate, four independent partial sums each (the
+    // 16 threads per candidate, four independent float-float sums each (the
     // loads of a thread are all in flight together); fixed order
     {
         const int c = tid >> 4, sub = tid & 15;
-        double x = 0.0;
+        stmf_ff x = {0.f, 0.f};
         const bool live = c < nc && !P.cand[8 * c + 4];    // dropped: proved non-improving by the FP16 screen
         if (live) {
-            const double *part = P.part + (size_t)c * nblk;
-            double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+            const float2 *part = P.part + (size_t)c * nblk;
+            stmf_ff x0 = {0.f, 0.f}, x1 = x0, x2 = x0, x3 = x0;
             int b = sub;
             for (; b + 48 < nblk; b += 64) {
-                x0 += part[b]; x1 += part[b + 16]; x2 += part[b + 32]; x3 += part[b + 48];
+                const float2 p0 = part[b], p1 = part[b + 16], p2 = part[b + 32], p3 = part[b + 48];
+                x0 = ff_add(x0, {p0.x, p0.y}); x1 = ff_add(x1, {p1.x, p1.y});
+                x2 = ff_add(x2, {p2.x, p2.y}); x3 = ff_add(x3, {p3.x, p3.y});
             }
-            for (; b < nblk; b += 16) x0 += part[b];
-            x = (x0 + x1) + (x2 + x3);
+            for (; b < nblk; b += 16) x0 = ff_add(x0, {part[b].x, part[b].y});
+            x = ff_add(ff_add(x0, x1), ff_add(x2, x3));
         }
 #pragma unroll
-        for (int o = 8; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        for (int o = 8; o; o >>= 1) x = ff_add(x, {__shfl_xor_sync(FULL, x.hi, o), __shfl_xor_sync(FULL, x.lo, o)});
         if (c < nc && sub == 0) {
-            sf[c] = live ? x : INFINITY;
-            P.fc[c] = live ? ctl->f + x : INFINITY;
+            const double d = (double)x.hi + (double)x.lo;
+            sf[c] = live ? d : INFINITY;
+            P.fc[c] = live ? ctl->f + d : INFINITY;
         }
     }
     __syncthreads();

@@ -129,7 +129,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     A(dalloc(&P->tdcol, np)); A(dalloc(&P->colhist, np * r)); A(dalloc(&P->rowhist, STMF_MAX_RANK));
     A(dalloc(&P->rank, np)); A(dalloc(&P->order, np)); A(dalloc(&P->cand, 8 * STMF_WMAX));
     A(dalloc(&P->Uc, (size_t)STMF_WMAX * mp)); A(dalloc(&P->Vc, (size_t)STMF_WMAX * np));
-    A(dalloc(&P->part, (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * ctx->num_sms * STMF_WMAX));
+    A(dalloc(&P->part, (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * ctx->num_sms * STMF_WMAX));   // float2
     A(dalloc(&P->fc, STMF_WMAX)); A(dalloc(&P->ctl, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&P->ctl_host, sizeof(stmf_ctl));
     if (e != cudaSuccess) {
