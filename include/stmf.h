@@ -27,7 +27,9 @@
  *     stmf_status; STMF_ERR_INVALID is returned, with nothing launched, for a
  *     bad argument (size < 1, r outside [1, STMF_MAX_RANK], a too-small
  *     leading dimension, a NULL required pointer, an index out of range, a
- *     row or column with no given entry, a non-finite given entry).  The text
+ *     row or column with no given entry, a given entry that is not finite
+ *     or has magnitude 2^60 or more: the evaluation keeps entries that are
+ *     not given at a finite sentinel far above that range).  The text
  *     of the last error of a context is available from stmf_last_error().
  *     Device-side waits are bounded: a wait that runs out returns
  *     STMF_ERR_TIMEOUT and leaves the device usable.

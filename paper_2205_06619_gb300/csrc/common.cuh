@@ -22,6 +22,7 @@
 
 #define STMF_PAD 256
 #define STMF_WMAX 64          // candidates per device window (upper bound)
+#define STMF_R_LIMIT 1.152921504606846976e18f   // 2^60: given entries of R must be smaller in magnitude
 #define STMF_DELTA_MAX_BLOCKS_PER_SM 8   // capacity of the phase-2 partials, per SM
 
 static inline int stmf_roundup(int x, int a) { return (x + a - 1) / a * a; }

@@ -139,6 +139,11 @@ static_assert(DEL_BLOCKS_PER_SM <= STMF_DELTA_MAX_BLOCKS_PER_SM, "phase-2 partia
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// Entries not given (and padding) enter the tile as R = E = DEL_BIG with
+// t0 = 0: P' = max(DEL_BIG, x) = DEL_BIG for every finite x below it, so
+// their term |P' - R| - t0 is exactly 0 without a NaN test per candidate.
+constexpr float DEL_BIG = 8.5070592e37f;    // 2^126
+
 // Change of the b-norm terms of a 4 x 4 tile for one candidate:
 //   sum over the tile of ( |R - max(E, u_i + v_j)| - t0 ),  t0 = |R - P1|,
 // where a NaN R (entry not given) gives 0 through fmaxf.  The tile holds -R
@@ -158,8 +163,8 @@ __device__ __forceinline__ float tile_change(const float (&nr)[4][4], const floa
         const float2 x01 = __fadd2_rn(ui, v01), x23 = __fadd2_rn(ui, v23);
         const float2 a01 = __fadd2_rn(f2(fmaxf(E[i][0], x01.x), fmaxf(E[i][1], x01.y)), f2(nr[i][0], nr[i][1]));
         const float2 a23 = __fadd2_rn(f2(fmaxf(E[i][2], x23.x), fmaxf(E[i][3], x23.y)), f2(nr[i][2], nr[i][3]));
-        const float2 d01 = __fadd2_rn(f2(fmaxf(fabsf(a01.x), 0.f), fmaxf(fabsf(a01.y), 0.f)), f2(nt0[i][0], nt0[i][1]));
-        const float2 d23 = __fadd2_rn(f2(fmaxf(fabsf(a23.x), 0.f), fmaxf(fabsf(a23.y), 0.f)), f2(nt0[i][2], nt0[i][3]));
+        const float2 d01 = f2(fabsf(a01.x) + nt0[i][0], fabsf(a01.y) + nt0[i][1]);
+        const float2 d23 = f2(fabsf(a23.x) + nt0[i][2], fabsf(a23.y) + nt0[i][3]);
         q[i] = __fadd2_rn(d01, d23);
     }
     const float2 s = __fadd2_rn(__fadd2_rn(q[0], q[1]), __fadd2_rn(q[2], q[3]));
@@ -200,11 +205,15 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
             const float4 y = reinterpret_cast<const float4 *>(P.P1)[o4];
             const float4 z = reinterpret_cast<const float4 *>(P.P2)[o4];
             aw[i] = reinterpret_cast<const uint32_t *>(P.A)[o4];
-            nr[i][0] = -x.x; nr[i][1] = -x.y; nr[i][2] = -x.z; nr[i][3] = -x.w;
-            nt0[i][0] = -fmaxf(fabsf(x.x - y.x), 0.f); nt0[i][1] = -fmaxf(fabsf(x.y - y.y), 0.f);
-            nt0[i][2] = -fmaxf(fabsf(x.z - y.z), 0.f); nt0[i][3] = -fmaxf(fabsf(x.w - y.w), 0.f);
-            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
-            p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
+            const float xr[4] = {x.x, x.y, x.z, x.w}, yr[4] = {y.x, y.y, y.z, y.w}, zr[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const bool given = xr[jj] == xr[jj];
+                nr[i][jj] = given ? -xr[jj] : -DEL_BIG;
+                nt0[i][jj] = given ? -fabsf(xr[jj] - yr[jj]) : 0.f;
+                p1[i][jj] = given ? yr[jj] : DEL_BIG;
+                p2[i][jj] = given ? zr[jj] : DEL_BIG;
+            }
         }
         const float4 *Vc4 = reinterpret_cast<const float4 *>(P.Vc) + f;
         const size_t ldv4 = (size_t)nf4;

@@ -35,7 +35,7 @@ __global__ void k_pack(const float *__restrict__ R, int ldr, const uint32_t *__r
         const bool given = mask ? ((mask[(size_t)s * ldm + (t >> 5)] >> (t & 31)) & 1u) : true;
         if (given) {
             v = R[(size_t)s * ldr + t];
-            if (!isfinite(v)) { atomicOr(bad, 1); v = QNAN; }
+            if (!(fabsf(v) < STMF_R_LIMIT)) { atomicOr(bad, 1); v = QNAN; }   // not finite, or too large
         }
     }
     Rp[(size_t)s * ldp + t] = v;
@@ -57,7 +57,7 @@ __global__ void k_pack_oriented(const float *__restrict__ R, int ldr, const uint
         const bool given = mask ? ((mask[(size_t)a * ldm + (b >> 5)] >> (b & 31)) & 1u) : true;
         if (given) {
             v = R[(size_t)a * ldr + b];
-            if (!isfinite(v)) { atomicOr(bad, 1); v = QNAN; }
+            if (!(fabsf(v) < STMF_R_LIMIT)) { atomicOr(bad, 1); v = QNAN; }   // not finite, or too large
         }
     }
     Rp[(size_t)s * ldp + t] = v;
@@ -332,7 +332,7 @@ __global__ void k_seed(stmf_problem P)
     const int j = cd[0], k = cd[1], type = cd[2], i = ctl->i;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (type == 0) {
-        if (x < P.mp) P.Uc[(size_t)c * P.mp + x] = INFINITY;
+        if (x < P.mp) P.Uc[(size_t)c * P.mp + x] = x < P.m ? INFINITY : 0.f;
         if (x >= P.np) return;
         const float useed = P.R[(size_t)i * P.np + j] - P.V[(size_t)k * P.np + j];   // U''_ik
         float v = 0.f;
@@ -343,7 +343,7 @@ __global__ void k_seed(stmf_problem P)
         }
         P.Vc[(size_t)c * P.np + x] = v;
     } else {
-        if (x < P.np) P.Vc[(size_t)c * P.np + x] = INFINITY;
+        if (x < P.np) P.Vc[(size_t)c * P.np + x] = x < P.n ? INFINITY : 0.f;
         if (x >= P.mp) return;
         const float vseed = P.R[(size_t)i * P.np + j] - P.U[(size_t)i * P.r + k];    // V''_kj
         float u = 0.f;

@@ -470,7 +470,7 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (d_bad) cudaFree(d_bad);
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "pack: %s", cudaGetErrorString(e)); }
-    if (bad) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite"); }
+    if (bad) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite or has magnitude >= 2^60"); }
     s = problem_init(P, o.U0, o.acol_p, o.seed, o.picks);
     if (s != STMF_OK) { problem_free(P); return s; }
     e = cudaSuccess;
@@ -823,7 +823,7 @@ stmf_status stmf_problem_create(stmf_ctx *ctx, int m, int n, int r, const float 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (d_bad) cudaFree(d_bad);
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "pack: %s", cudaGetErrorString(e)); }
-    if (bad) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite"); }
+    if (bad) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite or has magnitude >= 2^60"); }
     s = problem_init(P, U0, o.acol_p, o.seed, o.picks);
     if (s != STMF_OK) { problem_free(P); return s; }
     s = read_ctl(P);
