@@ -35,19 +35,21 @@ __device__ __forceinline__ void atomic_min_float(float *addr, float v)
 }
 
 // ------------------------------------------------------------------ phase 1
-// Task = (type, RES_THREADS rows of X, RES_CHUNK columns): type 0 runs over
-// the rows of R with the F-ULF candidates' V'_c, type 1 over the rows of R^T
-// with the F-URF candidates' U'_c.  The candidates' values of the chunk are
-// staged in shared memory and read as warp-wide broadcasts; each thread owns
-// one row and keeps the running minima of all the type's candidates in
-// registers (no cross-thread reduction).  The candidate loop is unrolled for
+// Task = (type, RES_THREADS x RES_RPT rows of X, RES_CHUNK columns): type 0
+// runs over the rows of R with the F-ULF candidates' V'_c, type 1 over the
+// rows of R^T with the F-URF candidates' U'_c.  The candidates' values of the
+// chunk are staged in shared memory and read as warp-wide broadcasts; each
+// thread owns two rows (every broadcast feeds both) and keeps their running
+// minima of all the type's candidates in registers (no cross-thread
+// reduction).  The candidate loop is unrolled for
 // a compile-time count NB >= cnt (4, 8, 16 or 32, picked per block) so the
 // minima of different candidates interleave; the slots above cnt compute on
 // whatever the staging area holds and are never stored.  Chunks combine
 // through atomic minima, which are exact in any order.  NaN entries (not
 // given, padding) drop out of fminf.
 constexpr int RES_THREADS = 128;
-constexpr int RES_CHUNK = 128;
+constexpr int RES_CHUNK = 64;
+constexpr int RES_RPT = 2;           // rows per thread
 
 __device__ __forceinline__ float min8(float4 a, float4 b, float4 w0, float4 w1)
 {
@@ -57,27 +59,29 @@ __device__ __forceinline__ float min8(float4 a, float4 b, float4 w0, float4 w1)
 }
 
 template <int NB>
-__device__ __forceinline__ void res_rows(const float4 *x4, const float (*sW)[RES_CHUNK], const int *sslot, int cnt,
-                                         float *OUT, size_t ldo, int row)
+__device__ __forceinline__ void res_rows(const float4 *x4a, const float4 *x4b, bool has_b, const float (*sW)[RES_CHUNK],
+                                         const int *sslot, int cnt, float *OUT, size_t ldo, int row)
 {
-    float acc[NB];
+    float acc[NB], accb[NB];
 #pragma unroll
-    for (int c = 0; c < NB; ++c) acc[c] = INFINITY;
-    float4 a = x4[0], b = x4[1];
+    for (int c = 0; c < NB; ++c) { acc[c] = INFINITY; accb[c] = INFINITY; }
 #pragma unroll 1
     for (int q = 0; q < RES_CHUNK / 4; q += 2) {
-        const float4 ca = a, cb = b;
-        if (q + 2 < RES_CHUNK / 4) { a = x4[q + 2]; b = x4[q + 3]; }     // next 8 columns in flight
+        const float4 a = x4a[q], b = x4a[q + 1];
+        const float4 a2 = x4b[q], b2 = x4b[q + 1];
 #pragma unroll
         for (int c = 0; c < NB; ++c) {
             const float4 w0 = reinterpret_cast<const float4 *>(sW[c])[q];
             const float4 w1 = reinterpret_cast<const float4 *>(sW[c])[q + 1];
-            acc[c] = fminf(acc[c], min8(ca, cb, w0, w1));
+            acc[c] = fminf(acc[c], min8(a, b, w0, w1));
+            accb[c] = fminf(accb[c], min8(a2, b2, w0, w1));
         }
     }
 #pragma unroll
-    for (int c = 0; c < NB; ++c)
+    for (int c = 0; c < NB; ++c) {
         if (c < cnt && acc[c] < INFINITY) atomic_min_float(OUT + sslot[c] * ldo + row, acc[c]);
+        if (has_b && c < cnt && accb[c] < INFINITY) atomic_min_float(OUT + sslot[c] * ldo + row + RES_THREADS, accb[c]);
+    }
 }
 
 __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0, int nch0, int nch1)
@@ -112,13 +116,15 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
         reinterpret_cast<float4 *>(sW[c])[q] = reinterpret_cast<const float4 *>(W + sslot[c] * ldw + c0)[q];
     }
     __syncthreads();
-    const int row = rb * RES_THREADS + tid;
+    const int row = rb * RES_THREADS * RES_RPT + tid;
     if (row < nrows) {
+        const bool has_b = row + RES_THREADS < nrows;
         const float4 *x4 = reinterpret_cast<const float4 *>(X + row * ldx + c0);
-        if (cnt <= 4) res_rows<4>(x4, sW, sslot, cnt, OUT, ldo, row);
-        else if (cnt <= 8) res_rows<8>(x4, sW, sslot, cnt, OUT, ldo, row);
-        else if (cnt <= 16) res_rows<16>(x4, sW, sslot, cnt, OUT, ldo, row);
-        else res_rows<32>(x4, sW, sslot, cnt, OUT, ldo, row);
+        const float4 *x4b = has_b ? reinterpret_cast<const float4 *>(X + (row + RES_THREADS) * ldx + c0) : x4;
+        if (cnt <= 4) res_rows<4>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
+        else if (cnt <= 8) res_rows<8>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
+        else if (cnt <= 16) res_rows<16>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
+        else res_rows<32>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
     }
     __syncthreads();
     if (tid == 0) atomicMax(&P.ctl->ev_r1, global_ns());
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
 }
 
 int res_chunks(int cols) { return (cols + RES_CHUNK - 1) / RES_CHUNK; }
-int res_blocks(int rows) { return (rows + RES_THREADS - 1) / RES_THREADS; }
+int res_blocks(int rows) { return (rows + RES_THREADS * RES_RPT - 1) / (RES_THREADS * RES_RPT); }
 
 }  // namespace
 
