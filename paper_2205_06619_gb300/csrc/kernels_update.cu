@@ -225,6 +225,30 @@ __global__ void __launch_bounds__(256) k_stats(stmf_problem P)
 
 // --------------------------------------------------------------- row loop
 
+// The single-block kernels of the row loop (k_row_begin, k_select) work on a
+// shared-memory copy of the control block: one coalesced load at the start
+// and one store at the end replace the chain of dependent global
+// read-modify-writes of its many fields.  No other kernel of the problem
+// runs while they do.
+constexpr int CTL_WORDS = (int)(sizeof(stmf_ctl) / sizeof(unsigned));
+static_assert(sizeof(stmf_ctl) % sizeof(unsigned) == 0, "control block is not a whole number of words");
+
+__device__ __forceinline__ void ctl_load(stmf_ctl &dst, const stmf_ctl *src)
+{
+    const unsigned *s = reinterpret_cast<const unsigned *>(src);
+    unsigned *d = reinterpret_cast<unsigned *>(&dst);
+    for (int w = threadIdx.x; w < CTL_WORDS; w += blockDim.x) d[w] = s[w];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
+{
+    __syncthreads();
+    const unsigned *s = reinterpret_cast<const unsigned *>(&src);
+    unsigned *d = reinterpret_cast<unsigned *>(dst);
+    for (int w = threadIdx.x; w < CTL_WORDS; w += blockDim.x) d[w] = s[w];
+}
+
 // Window of candidates (Algorithm 3): the next wj columns j of the order with
 // R_ij given; k_j = argmax_l (rowhist_i[l] + colhist[j][l]) (TD_A; the multiset
 // union adds multiplicities; smaller l on ties).  Each j gives F-ULF (slot 2a)
@@ -232,12 +256,11 @@ __global__ void __launch_bounds__(256) k_stats(stmf_problem P)
 // first window of a row the row histogram is rebuilt.  Runs in a block of
 // 1024 threads: at the start of a row (k_row_begin) and after a window that
 // neither kept a candidate nor exhausted the row (k_select).
-__device__ __forceinline__ void build_window(const stmf_problem &P, bool row_start)
+__device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ctl, bool row_start)
 {
     __shared__ int sh[STMF_MAX_RANK];
     __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2];
     __shared__ int scount, spos;
-    stmf_ctl *ctl = P.ctl;
     const int i = ctl->i, tid = threadIdx.x, r = P.r;
     const float *Ri = P.R + (size_t)i * P.np;
     if (row_start) {
@@ -380,8 +403,10 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
 {
     __shared__ double sf[STMF_WMAX];
     __shared__ int skept;
-    stmf_ctl *ctl = P.ctl;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ stmf_ctl sctl;
+    ctl_load(sctl, P.ctl);
+    stmf_ctl *ctl = &sctl;
+    const int tid = threadIdx.x;
     const int nc = ctl->nc;
     // 16 threads per candidate, four independent float-float sums each (the
     // loads of a thread are all in flight together); fixed order
@@ -484,15 +509,18 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
     }
     if (!single) {
         __syncthreads();
-        if (!ctl->row_done) build_window(P, false);
+        if (!ctl->row_done) build_window(P, ctl, false);
     }
+    ctl_store(P.ctl, sctl);
 }
 
 // Start of a row: row state reset and the row's first window; in a graph,
 // opens the window loop.
 __global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_win)
 {
-    stmf_ctl *ctl = P.ctl;
+    __shared__ stmf_ctl sctl;
+    ctl_load(sctl, P.ctl);
+    stmf_ctl *ctl = &sctl;
     if (threadIdx.x == 0) {
         ctl->row_start = 1;
         ctl->pos = 0;
@@ -503,7 +531,8 @@ __global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph
         if (in_graph) cudaGraphSetConditional(h_win, 1u);
     }
     __syncthreads();
-    build_window(P, true);
+    build_window(P, ctl, true);
+    ctl_store(P.ctl, sctl);
 }
 
 // Start of a sweep: row 0; in a graph, opens the row loop and asks for a
