@@ -10,7 +10,8 @@
 //   RT   np x mp  transpose of R (column passes of F-URF read rows of RT).
 //   U    mp x r   row-major (rows >= m are 0).
 //   V    r x np   row-major (columns >= n are 0).
-//   P1, P2 mp x np fp32, A mp x np uint8: top-2 planes of U (x) V.
+//   P1, P2 mp x np fp32, A mp x np uint8: top-2 planes of U (x) V at given
+//                 entries; P1 = P2 = STMF_SENTINEL elsewhere.
 //   Rh, P1h, P2h mp x np fp16 (precision 1 only): R, P1, P2 rounded to
 //                 nearest half at given entries, a quiet NaN elsewhere.
 #pragma once
@@ -23,6 +24,9 @@
 #define STMF_PAD 256
 #define STMF_WMAX 64          // candidates per device window (upper bound)
 #define STMF_R_LIMIT 1.152921504606846976e18f   // 2^60: given entries of R must be smaller in magnitude
+// P1 and P2 planes hold this value where R is not given (and in padding):
+// every error change the evaluation forms there is exactly 0 (see k_delta).
+#define STMF_SENTINEL 8.5070592e37f                 // 2^126
 #define STMF_DELTA_MAX_BLOCKS_PER_SM 8   // capacity of the phase-2 partials, per SM
 
 static inline int stmf_roundup(int x, int a) { return (x + a - 1) / a * a; }

@@ -134,31 +134,31 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
 // Tiles of 4 rows x DEL_COLS columns (a thread owns 4 rows x one float4
 // column) cover the matrix and are dealt to the blocks round-robin, so every
 // block's share is fixed and the sums are reproducible.  A thread keeps its
-// tile of -R, -|R - P1|, P1, P2 and A in registers and runs through all the
-// window's candidates (grouped by k, so E is rebuilt only when k changes);
-// V'_c is read from global memory two candidates ahead, U'_c of the tile's
-// rows from shared memory.
+// tile of P1, P2 and A in registers and runs through all the window's
+// candidates (grouped by k, so E is rebuilt only when k changes); V'_c is
+// read from global memory two candidates ahead, U'_c of the tile's rows from
+// shared memory.
 constexpr int DEL_THREADS = 128;
 constexpr int DEL_COLS = 4 * DEL_THREADS;
-constexpr int DEL_BLOCKS_PER_SM = 4;
+constexpr int DEL_BLOCKS_PER_SM = 5;
 static_assert(DEL_BLOCKS_PER_SM <= STMF_DELTA_MAX_BLOCKS_PER_SM, "phase-2 partials buffer too small");
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Entries not given (and padding) enter the tile as R = E = DEL_BIG with
-// t0 = 0: P' = max(DEL_BIG, x) = DEL_BIG for every finite x below it, so
-// their term |P' - R| - t0 is exactly 0 without a NaN test per candidate.
-constexpr float DEL_BIG = 8.5070592e37f;    // 2^126
 
-// Change of the b-norm terms of a 4 x 4 tile for one candidate:
-//   sum over the tile of ( |R - max(E, u_i + v_j)| - t0 ),  t0 = |R - P1|,
-// where a NaN R (entry not given) gives 0 through fmaxf.  The tile holds -R
-// and -t0, so every addition is a packed FP32x2 add (two lanes of one
-// instruction, each rounded like a scalar add): per entry the terms are the
-// scalar ones, |P' - R| = |R - P'| exactly; the sum is a fixed tree of
-// depth 4.
-__device__ __forceinline__ float tile_change(const float (&nr)[4][4], const float (&nt0)[4][4],
-                                             const float (&E)[4][4], const float4 u, const float4 v)
+// Change of the b-norm terms of a 4 x 4 tile for one candidate.  Every
+// factorization the method holds satisfies U (x) V <= R on the given entries
+// (Acol and both updates end with a residuation), and so does every
+// candidate's U' (x) V'.  With P1 <= R and P' <= R the term
+// |R - P'| - |R - P1| is P1 - P', P' = max(E, u_i + v_j): R is not needed.
+// (FP32 rounding can put a value an ulp above R; the term then differs from
+// the literal one by a few ulps, far inside the error tolerance.)  Entries
+// not given hold P1 = P2 = STMF_SENTINEL, so P' = STMF_SENTINEL (every
+// finite x is far below it) and the term is exactly 0,
+// as it is for every entry a candidate leaves unchanged.  Packed FP32x2
+// additions; the tile sum is a fixed tree of depth 4.
+__device__ __forceinline__ float tile_change(const float (&p1)[4][4], const float (&E)[4][4], const float4 u,
+                                             const float4 v)
 {
     const float uu[4] = {u.x, u.y, u.z, u.w};
     const float2 v01 = f2(v.x, v.y), v23 = f2(v.z, v.w);
@@ -167,10 +167,10 @@ __device__ __forceinline__ float tile_change(const float (&nr)[4][4], const floa
     for (int i = 0; i < 4; ++i) {
         const float2 ui = f2(uu[i], uu[i]);
         const float2 x01 = __fadd2_rn(ui, v01), x23 = __fadd2_rn(ui, v23);
-        const float2 a01 = __fadd2_rn(f2(fmaxf(E[i][0], x01.x), fmaxf(E[i][1], x01.y)), f2(nr[i][0], nr[i][1]));
-        const float2 a23 = __fadd2_rn(f2(fmaxf(E[i][2], x23.x), fmaxf(E[i][3], x23.y)), f2(nr[i][2], nr[i][3]));
-        const float2 d01 = f2(fabsf(a01.x) + nt0[i][0], fabsf(a01.y) + nt0[i][1]);
-        const float2 d23 = f2(fabsf(a23.x) + nt0[i][2], fabsf(a23.y) + nt0[i][3]);
+        const float2 n01 = f2(-fmaxf(E[i][0], x01.x), -fmaxf(E[i][1], x01.y));
+        const float2 n23 = f2(-fmaxf(E[i][2], x23.x), -fmaxf(E[i][3], x23.y));
+        const float2 d01 = __fadd2_rn(f2(p1[i][0], p1[i][1]), n01);
+        const float2 d23 = __fadd2_rn(f2(p1[i][2], p1[i][3]), n23);
         q[i] = __fadd2_rn(d01, d23);
     }
     const float2 s = __fadd2_rn(__fadd2_rn(q[0], q[1]), __fadd2_rn(q[2], q[3]));
@@ -202,24 +202,16 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
         __syncthreads();
         if (f >= nf4) continue;
 
-        float nr[4][4], nt0[4][4], p1[4][4], p2[4][4], E[4][4];
+        float p1[4][4], p2[4][4], E[4][4];
         uint32_t aw[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const size_t o4 = (size_t)(s0 + i) * nf4 + f;
-            const float4 x = reinterpret_cast<const float4 *>(P.R)[o4];
             const float4 y = reinterpret_cast<const float4 *>(P.P1)[o4];
             const float4 z = reinterpret_cast<const float4 *>(P.P2)[o4];
             aw[i] = reinterpret_cast<const uint32_t *>(P.A)[o4];
-            const float xr[4] = {x.x, x.y, x.z, x.w}, yr[4] = {y.x, y.y, y.z, y.w}, zr[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const bool given = xr[jj] == xr[jj];
-                nr[i][jj] = given ? -xr[jj] : -DEL_BIG;
-                nt0[i][jj] = given ? -fabsf(xr[jj] - yr[jj]) : 0.f;
-                p1[i][jj] = given ? yr[jj] : DEL_BIG;
-                p2[i][jj] = given ? zr[jj] : DEL_BIG;
-            }
+            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
+            p2[i][0] = z.x; p2[i][1] = z.y; p2[i][2] = z.z; p2[i][3] = z.w;
         }
         const float4 *Vc4 = reinterpret_cast<const float4 *>(P.Vc) + f;
         const size_t ldv4 = (size_t)nf4;
@@ -241,7 +233,7 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
                         E[i][jj] = ((aw[i] >> (8 * jj)) & 0xffu) == (uint32_t)k ? p2[i][jj] : p1[i][jj];
             }
             const float4 u4 = *reinterpret_cast<const float4 *>(su[c]);
-            sacc[c][tid] += tile_change(nr, nt0, E, u4, v4);
+            sacc[c][tid] += tile_change(p1, E, u4, v4);
         }
     }
     __syncthreads();

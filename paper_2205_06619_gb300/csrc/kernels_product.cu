@@ -219,13 +219,20 @@ k_maxplus_planes(int m, int n, int r, const float *__restrict__ U, const float *
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const size_t off = (size_t)(row0 + rg * 4 + i) * ld + c;
-            *reinterpret_cast<float4 *>(P1 + off) = make_float4(p1[i][0], p1[i][1], p1[i][2], p1[i][3]);
-            *reinterpret_cast<float4 *>(P2 + off) = make_float4(p2[i][0], p2[i][1], p2[i][2], p2[i][3]);
+            const float4 r4 = *reinterpret_cast<const float4 *>(R + off);
+            const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
+            float q1[4], q2[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const bool given = rv[jj] == rv[jj];
+                q1[jj] = given ? p1[i][jj] : STMF_SENTINEL;
+                q2[jj] = given ? p2[i][jj] : STMF_SENTINEL;
+            }
+            *reinterpret_cast<float4 *>(P1 + off) = make_float4(q1[0], q1[1], q1[2], q1[3]);
+            *reinterpret_cast<float4 *>(P2 + off) = make_float4(q2[0], q2[1], q2[2], q2[3]);
             const uint32_t packed = (uint32_t)am[i][0] | ((uint32_t)am[i][1] << 8) |
                                     ((uint32_t)am[i][2] << 16) | ((uint32_t)am[i][3] << 24);
             *reinterpret_cast<uint32_t *>(A + off) = packed;
-            const float4 r4 = *reinterpret_cast<const float4 *>(R + off);
-            const float rv[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
                 if (rv[jj] == rv[jj]) {   // given entry (not NaN)

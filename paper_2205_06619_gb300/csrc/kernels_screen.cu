@@ -24,7 +24,9 @@
 //    sum of 8 rows adds <= 6.05 u_h M, the FP32 accumulation of the screen
 //    <= 2.03 D_s u M and the FP32 path's own term and sum errors
 //    <= (4.02 + 2.03 D_32) u M (D = the number of FP32 additions a term
-//    passes through).
+//    passes through).  The FP32 path forms its terms as P1 - P' (exact
+//    when P1, P' <= R, which residuation keeps up to rounding): a value at
+//    most 3 u M above R moves a term by at most 12 u M more.
 //  * Drop iff Delta_half > 1.01 |S| W, W the per-entry sum of the above; no
 //    dropping at all when M > 16384 (half overflow).  The block and grid sums
 //    of both paths are float-float (relative error below 2^-44 over their
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(1024) k_screen_select(stmf_problem P, int nblk
     __syncthreads();
     if (tid != 0) return;
     const double uh = 1.0 / 2048.0, u32 = 1.0 / 16777216.0;
-    const double coef = (6.01 + 6.05) * uh + (4.02 + 2.03 * depth) * u32;
+    const double coef = (6.01 + 6.05) * uh + (4.02 + 12.0 + 2.03 * depth) * u32;
     const double mr = (double)__uint_as_float(ctl->scr_mr), mp = (double)__uint_as_float(ctl->scr_mp);
     int dropped = 0;
     for (int c = 0; c < nc; ++c) {
