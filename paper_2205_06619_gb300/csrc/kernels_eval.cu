@@ -48,7 +48,7 @@ __device__ __forceinline__ void atomic_min_float(float *addr, float v)
 // through atomic minima, which are exact in any order.  NaN entries (not
 // given, padding) drop out of fminf.
 constexpr int RES_THREADS = 128;
-constexpr int RES_CHUNK = 64;
+constexpr int RES_CHUNK_MAX = 128;   // columns per task: a multiple of 8 up to this, chosen per launch
 constexpr int RES_RPT = 2;           // rows per thread
 
 __device__ __forceinline__ float min8(float4 a, float4 b, float4 w0, float4 w1)
@@ -59,14 +59,15 @@ __device__ __forceinline__ float min8(float4 a, float4 b, float4 w0, float4 w1)
 }
 
 template <int NB>
-__device__ __forceinline__ void res_rows(const float4 *x4a, const float4 *x4b, bool has_b, const float (*sW)[RES_CHUNK],
-                                         const int *sslot, int cnt, float *OUT, size_t ldo, int row)
+__device__ __forceinline__ void res_rows(const float4 *x4a, const float4 *x4b, bool has_b,
+                                         const float (*sW)[RES_CHUNK_MAX], int nq, const int *sslot, int cnt,
+                                         float *OUT, size_t ldo, int row)
 {
     float acc[NB], accb[NB];
 #pragma unroll
     for (int c = 0; c < NB; ++c) { acc[c] = INFINITY; accb[c] = INFINITY; }
 #pragma unroll 1
-    for (int q = 0; q < RES_CHUNK / 4; q += 2) {
+    for (int q = 0; q < nq; q += 2) {
         const float4 a = x4a[q], b = x4a[q + 1];
         const float4 a2 = x4b[q], b2 = x4b[q + 1];
 #pragma unroll
@@ -84,9 +85,9 @@ __device__ __forceinline__ void res_rows(const float4 *x4a, const float4 *x4b, b
     }
 }
 
-__global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0, int nch0, int nch1)
+__global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0, int nch0, int nch1, int chunk)
 {
-    __shared__ __align__(16) float sW[NCT][RES_CHUNK];
+    __shared__ __align__(16) float sW[NCT][RES_CHUNK_MAX];
     __shared__ int sslot[NCT];
     const stmf_ctl *ctl = P.ctl;
     const int tid = threadIdx.x;
@@ -100,9 +101,10 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
     const int cnt = type ? ctl->nv : ctl->nu;
     if (cnt == 0) return;
     const int nch = type ? nch1 : nch0;
-    const int rb = task / nch, c0 = (task % nch) * RES_CHUNK;
+    const int rb = task / nch, c0 = (task % nch) * chunk;
     const float *X = type ? P.RT : P.R;
     const size_t ldx = type ? P.mp : P.np;
+    const int nq = min(chunk, (int)ldx - c0) >> 2;      // float4 columns of this task (rows are padded to 256)
     const int nrows = type ? P.n : P.m;
     const float *W = type ? P.Uc : P.Vc;
     float *OUT = type ? P.Vc : P.Uc;
@@ -111,8 +113,8 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
 
     if (tid < cnt) sslot[tid] = type ? ctl->vlist[tid] : ctl->ulist[tid];
     __syncthreads();
-    for (int e = tid; e < cnt * (RES_CHUNK / 4); e += RES_THREADS) {
-        const int c = e / (RES_CHUNK / 4), q = e % (RES_CHUNK / 4);
+    for (int e = tid; e < cnt * nq; e += RES_THREADS) {
+        const int c = e / nq, q = e % nq;
         reinterpret_cast<float4 *>(sW[c])[q] = reinterpret_cast<const float4 *>(W + sslot[c] * ldw + c0)[q];
     }
     __syncthreads();
@@ -121,10 +123,10 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
         const bool has_b = row + RES_THREADS < nrows;
         const float4 *x4 = reinterpret_cast<const float4 *>(X + row * ldx + c0);
         const float4 *x4b = has_b ? reinterpret_cast<const float4 *>(X + (row + RES_THREADS) * ldx + c0) : x4;
-        if (cnt <= 4) res_rows<4>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
-        else if (cnt <= 8) res_rows<8>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
-        else if (cnt <= 16) res_rows<16>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
-        else res_rows<32>(x4, x4b, has_b, sW, sslot, cnt, OUT, ldo, row);
+        if (cnt <= 4) res_rows<4>(x4, x4b, has_b, sW, nq, sslot, cnt, OUT, ldo, row);
+        else if (cnt <= 8) res_rows<8>(x4, x4b, has_b, sW, nq, sslot, cnt, OUT, ldo, row);
+        else if (cnt <= 16) res_rows<16>(x4, x4b, has_b, sW, nq, sslot, cnt, OUT, ldo, row);
+        else res_rows<32>(x4, x4b, has_b, sW, nq, sslot, cnt, OUT, ldo, row);
     }
     __syncthreads();
     if (tid == 0) atomicMax(&P.ctl->ev_r1, global_ns());
@@ -249,8 +251,27 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
     if (tid == 0) atomicMax(&P.ctl->ev_t1, global_ns());
 }
 
-int res_chunks(int cols) { return (cols + RES_CHUNK - 1) / RES_CHUNK; }
 int res_blocks(int rows) { return (rows + RES_THREADS * RES_RPT - 1) / (RES_THREADS * RES_RPT); }
+
+// Phase-1 tasks all have the same size, so a launch takes as many waves as
+// the tasks need slots; the column chunk (a multiple of 8 up to 128) is the
+// one that minimises waves x chunk.
+int res_chunk(const stmf_problem *P)
+{
+    static int per_sm = 0;
+    if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_res, RES_THREADS, 0) != cudaSuccess)
+        per_sm = 1;
+    const long long slots = (long long)per_sm * P->ctx->num_sms;
+    int best = RES_CHUNK_MAX;
+    long long best_cost = -1;
+    for (int c = 32; c <= RES_CHUNK_MAX; c += 8) {
+        const long long tasks = (long long)res_blocks(P->m) * ((P->n + c - 1) / c) +
+                                (long long)res_blocks(P->n) * ((P->m + c - 1) / c);
+        const long long cost = (tasks + slots - 1) / slots * c;
+        if (best_cost < 0 || cost <= best_cost) { best_cost = cost; best = c; }
+    }
+    return best;
+}
 
 }  // namespace
 
@@ -270,9 +291,10 @@ int delta_depth(const stmf_problem *P)
 
 cudaError_t launch_res(cudaStream_t st, stmf_problem *P)
 {
-    const int nch0 = res_chunks(P->n), nch1 = res_chunks(P->m);
+    const int chunk = res_chunk(P);
+    const int nch0 = (P->n + chunk - 1) / chunk, nch1 = (P->m + chunk - 1) / chunk;
     const int ntask0 = res_blocks(P->m) * nch0, ntask1 = res_blocks(P->n) * nch1;
-    k_res<<<ntask0 + ntask1, RES_THREADS, 0, st>>>(*P, ntask0, nch0, nch1);
+    k_res<<<ntask0 + ntask1, RES_THREADS, 0, st>>>(*P, ntask0, nch0, nch1, chunk);
     return cudaGetLastError();
 }
 
