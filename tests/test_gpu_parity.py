@@ -167,6 +167,23 @@ def test_problem_rejects_empty_column():
         api().Problem(tg(R), api().pack_mask(M), rank=2)
 
 
+def test_rejects_given_entries_beyond_the_magnitude_limit():
+    """Given entries must be finite and below 2^60 in magnitude (entries that
+    are not given sit at a sentinel of 2^126 in the evaluation's planes)."""
+    R = np.ones((6, 8), np.float32)
+    M = np.ones((6, 8), bool)
+    R[2, 3] = 2.0 ** 61
+    with pytest.raises(api().StmfError, match="2\\^60"):
+        api().factorize(tg(R), api().pack_mask(M), rank=2)
+    with pytest.raises(api().StmfError, match="2\\^60"):
+        api().Problem(tg(R), api().pack_mask(M), rank=2)
+    M[2, 3] = False                       # not given: its value is never read
+    api().factorize(tg(R), api().pack_mask(M), rank=2, sweeps=1)
+    R[2, 3] = 2.0 ** 59
+    M[2, 3] = True
+    api().factorize(tg(R), api().pack_mask(M), rank=2, sweeps=1)
+
+
 # ------------------------------------------------------------ factorize
 
 @pytest.mark.parametrize("shape,transposed", [((40, 70), False), ((70, 40), True)])
