@@ -67,7 +67,6 @@ struct stmf_ctl {
     int m;             // rows per sweep
     int sweep;         // sweep index (for the trace)
     int pos;           // next position in the column order
-    int row_start;     // 1 before the first window of a row
     int wj;            // j-candidates of the next window (each gives F-ULF, F-URF)
     int wj0;           // j-candidates of a row's first window (what the previous row consumed)
     int wmax;          // candidates per window (upper bound, even)
@@ -81,7 +80,6 @@ struct stmf_ctl {
     int err;           // device-detected error code (0 = none)
     int nu, nv;        // F-ULF / F-URF candidates of the window
     int exhausted;     // 1 when the window reached the end of the row's candidates
-    int eval_next;     // work queue of the window evaluation (next unit)
     int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // window slots per type, grouped by k
     int alist[STMF_WMAX];  // all the window's slots to evaluate in phase 2, grouped by k
     int na;

@@ -263,7 +263,6 @@ __global__ void __launch_bounds__(1024) k_screen_select(stmf_problem P, int nblk
     ctl->nu = nu2;
     ctl->nv = nv2;
     ctl->screened += dropped;
-    ctl->eval_next = 0;
 }
 
 size_t screen_smem(int wmax) { return sizeof(float2) * (size_t)wmax * SCR_THREADS; }

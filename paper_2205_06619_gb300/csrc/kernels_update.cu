@@ -1,21 +1,21 @@
 // Kernels of the F-ULF / F-URF updates (Algorithms 1 and 2) and of the ByRow
-// row loop of Algorithm 3, for a window of candidates evaluated at once.
+// row loop of Algorithm 3, apart from the window evaluation itself
+// (kernels_eval.cu): packing, initialisation, the residuation statistics,
+// the candidate window, the seeds, the decision and the row-loop control.
 //
 // F-ULF(i,j,k) on the state (U, V):
 //   seed   U''_ik = R_ij - V_kj
 //   V'_kt  = min over given s of (R_st - U''_sk)
 //          = min( R_it - U''_ik ,  min over s != i of (R_st - U_sk) )
 //            -- O(n) from the column statistics (min1, argmin, min2) of k
-//   U'_sk  = min over given t of (R_st - V'_kt)            (row pass)
+//   U'_sk  = min over given t of (R_st - V'_kt)            (row pass, phase 1)
 //   f'     = sum over given (s,t) of |R_st - max(E_st, U'_sk + V'_kt)|
 //            with E = max over l != k of (U_sl + V_lt) = (A == k ? P2 : P1)
+//            (phase 2, as the change f' - f summed per entry)
 // F-URF is the mirror image (row statistics, then a column pass over RT).
 //
-// Every value of a candidate's U', V' and every term of f' is computed with
-// the same FP32 operations as the plain definition, so they are bit-identical
-// to it.  The error is accumulated as the change f' - f (per-entry differences
-// of the FP32 terms) in FP32 partials of 8 entries, FP32 warp trees and FP64
-// across warps and blocks, all in a fixed order; f' = f + (f' - f).
+// The seeds and the residuations are computed with the same FP32 operations
+// as the plain definition, so a candidate's U', V' are bit-identical to it.
 #include "common.cuh"
 
 #define QNAN __int_as_float(0x7fffffff)
@@ -271,7 +271,7 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
             if (Ri[t] == Ri[t]) atomicAdd(&sh[Ai[t]], 1);
         __syncthreads();
         if (tid < r) P.rowhist[tid] = sh[tid];
-        if (tid == 0) { ctl->pos = 0; ctl->ncand_row = 0; ctl->row_start = 0; }
+        if (tid == 0) { ctl->pos = 0; ctl->ncand_row = 0; }
         __syncthreads();
     } else {
         if (tid < r) sh[tid] = P.rowhist[tid];
@@ -338,7 +338,6 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         ctl->nv = cnt;
         ctl->exhausted = spos >= P.n;
         ctl->pos = spos;
-        ctl->eval_next = 0;
     }
 }
 
@@ -522,7 +521,6 @@ __global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph
     ctl_load(sctl, P.ctl);
     stmf_ctl *ctl = &sctl;
     if (threadIdx.x == 0) {
-        ctl->row_start = 1;
         ctl->pos = 0;
         ctl->ncand_row = 0;
         ctl->wj = ctl->wj0;
@@ -586,7 +584,6 @@ __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
     ctl->exhausted = 1;
     ctl->ncand_row = 0;
     ctl->select_mode = 0;
-    ctl->eval_next = 0;
 }
 
 // Unconditional commit of slot 0 (commit_if_decreases = 0).
