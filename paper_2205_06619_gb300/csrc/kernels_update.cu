@@ -302,19 +302,28 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
     }
     __syncthreads();
     const int cnt = scount;
-    if (tid < cnt) {
-        const int j = sj[tid];
-        int best = 0, bestc = -1;
-        for (int l = 0; l < r; ++l) {
-            const int c = sh[l] + P.colhist[(size_t)j * r + l];
-            if (c > bestc) { bestc = c; best = l; }
+    {
+        // warp a takes column a of the window; lane l loads component l's
+        // count, and the warp keeps the largest (the smaller l on ties)
+        const int a = tid >> 5, l = tid & 31;
+        if (a < cnt) {
+            const int j = sj[a];
+            int c = l < r ? sh[l] + P.colhist[(size_t)j * r + l] : -1;
+            int bl = l;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const int oc = __shfl_xor_sync(FULL, c, o), ol = __shfl_xor_sync(FULL, bl, o);
+                if (oc > c || (oc == c && ol < bl)) { c = oc; bl = ol; }
+            }
+            if (l == 0) {
+                sk[a] = bl;
+                const int base = ctl->ncand_row / 2;
+                int *c0 = P.cand + 8 * (2 * a);
+                c0[0] = j; c0[1] = bl; c0[2] = 0; c0[3] = base + a; c0[4] = 0;
+                int *c1 = P.cand + 8 * (2 * a + 1);
+                c1[0] = j; c1[1] = bl; c1[2] = 1; c1[3] = base + a; c1[4] = 0;
+            }
         }
-        sk[tid] = best;
-        const int base = ctl->ncand_row / 2;
-        int *c0 = P.cand + 8 * (2 * tid);
-        c0[0] = j; c0[1] = best; c0[2] = 0; c0[3] = base + tid; c0[4] = 0;
-        int *c1 = P.cand + 8 * (2 * tid + 1);
-        c1[0] = j; c1[1] = best; c1[2] = 1; c1[3] = base + tid; c1[4] = 0;
     }
     __syncthreads();
     if (tid == 0) {
@@ -434,15 +443,33 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         }
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid < 32) {
+        // the first improving candidate (select_mode 0) or the smallest
+        // change, the earlier one on ties (select_mode 1), over nc <= 64
+        const int lane = tid;
         int kept = -1;
-        for (int c = 0; c < nc; ++c) {
-            if (sf[c] < 0.0) {
-                if (ctl->select_mode == 0) { kept = c; break; }
-                if (kept < 0 || sf[c] < sf[kept]) kept = c;
+        if (ctl->select_mode == 0) {
+            const unsigned b0 = __ballot_sync(FULL, lane < nc && sf[lane] < 0.0);
+            const unsigned b1 = __ballot_sync(FULL, lane + 32 < nc && sf[lane + 32] < 0.0);
+            kept = b0 ? __ffs(b0) - 1 : (b1 ? 32 + __ffs(b1) - 1 : -1);
+        } else {
+            double bv = INFINITY;
+            int bi = -1;
+            for (int c = lane; c < nc; c += 32)
+                if (sf[c] < 0.0 && (bi < 0 || sf[c] < bv)) { bv = sf[c]; bi = c; }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double ov = __shfl_xor_sync(FULL, bv, o);
+                const int oi = __shfl_xor_sync(FULL, bi, o);
+                if (oi >= 0 && (bi < 0 || ov < bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
             }
+            kept = bi;
         }
-        skept = kept;
+        if (lane == 0) skept = kept;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int kept = skept;
         ctl->issued += nc;
         ctl->windows += 1;
         if (ctl->ev_t1 > ctl->ev_t0) {
