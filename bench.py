@@ -487,9 +487,10 @@ def main():
     ach_res = (2.0 * n_obs * d_eval_c) / (d_res_ns * 1e-9) / 1e12 if d_res_ns else None
     ach_del = (4.0 * n_obs * d_eval_c) / (d_del_ns * 1e-9) / 1e12 if d_del_ns else None
     achieved = (6.0 * n_obs * d_eval_c) / (d_eval_ns * 1e-9) / 1e12 if d_eval_ns else None
-    # per window: k_window, k_seed, k_res, k_delta, k_select; per row k_row_begin;
-    # per refresh k_stats, k_maxplus_planes, k_td_finalize, k_rank, k_scatter_f
-    launches = 5 * d_win + args.steps * m_or + 5 * d_ref + args.steps
+    # per window: k_seed, k_res, k_delta, k_select (which also picks the next
+    # window); per row k_row_begin; per refresh k_stats, k_maxplus_planes,
+    # k_td_finalize, k_rank, k_scatter_f; per sweep k_sweep_begin
+    launches = 4 * d_win + args.steps * m_or + 5 * d_ref + args.steps
 
     if rank_id != 0:
         if dist is not None:
