@@ -35,18 +35,18 @@ __device__ __forceinline__ void atomic_min_float(float *addr, float v)
 }
 
 // ------------------------------------------------------------------ phase 1
-// Task = (type, RES_THREADS x RES_RPT rows of X, RES_CHUNK columns): type 0
+// Task = (type, RES_THREADS x RES_RPT rows of X, a chunk of columns): type 0
 // runs over the rows of R with the F-ULF candidates' V'_c, type 1 over the
 // rows of R^T with the F-URF candidates' U'_c.  The candidates' values of the
 // chunk are staged in shared memory and read as warp-wide broadcasts; each
 // thread owns two rows (every broadcast feeds both) and keeps their running
 // minima of all the type's candidates in registers (no cross-thread
-// reduction).  The candidate loop is unrolled for
-// a compile-time count NB >= cnt (4, 8, 16 or 32, picked per block) so the
-// minima of different candidates interleave; the slots above cnt compute on
-// whatever the staging area holds and are never stored.  Chunks combine
-// through atomic minima, which are exact in any order.  NaN entries (not
-// given, padding) drop out of fminf.
+// reduction).  The candidate loop is unrolled for a compile-time count
+// NB >= cnt (4, 8, 16 or 32, picked per block) so the minima of different
+// candidates interleave; the slots above cnt compute on whatever the staging
+// area holds and are never stored.  Chunks combine through atomic minima,
+// which are exact in any order.  NaN entries (not given, padding) drop out of
+// fminf.
 constexpr int RES_THREADS = 128;
 constexpr int RES_CHUNK_MAX = 128;   // columns per task: a multiple of 8 up to this, chosen per launch
 constexpr int RES_RPT = 2;           // rows per thread
