@@ -57,6 +57,7 @@ typedef enum {
 
 typedef struct stmf_ctx stmf_ctx;         /* device, stream, error text       */
 typedef struct stmf_problem stmf_problem; /* R, mask, U, V, planes, stats    */
+typedef struct stmf_mlp stmf_mlp;         /* learned-initialisation network  */
 
 /* Options of the factorization (Algorithm 3 and its readings). */
 typedef struct {
@@ -84,6 +85,11 @@ typedef struct {
                             (m x r, ld r); replaces Random Acol                          */
     int32_t *trace;      /* HOST, nullable: one record of STMF_TRACE_INTS per row visit */
     int64_t trace_cap;   /* capacity of trace in records                               */
+    const stmf_mlp *mlp; /* nullable: learned initialisation (an addition to the paper).
+                            U0 of the oriented, permuted problem = MLP(row sketch) +
+                            row median, computed on the device; the network's rank
+                            must be r, it must belong to the same context, and the
+                            oriented n must be <= 12288.  U0, if given, wins.      */
 } stmf_options;
 
 /* A trace record: sweep, row (oriented, permuted index), position of the kept
@@ -259,12 +265,10 @@ stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_pr
  * by a 32-quantile sketch of its given entries centred on the row median; an
  * MLP 32 -> 128 -> 128 -> r (ReLU, BF16 weights, FP32 accumulation) maps the
  * sketch to the row of U minus its median.  Random Acol stays the fallback. */
-typedef struct stmf_mlp stmf_mlp;
-
 /* sketch[s*32 + q] = v[floor((q+0.5)*c/32)] - median_s and median[s] =
  * v[floor(c/2)], where v are the c given entries of row s sorted ascending
  * (nearest-rank quantiles).  R, mask, sketch (m x 32), median (m) device;
- * n <= 12288. */
+ * n <= 12288.  mask NULL: the given entries are those of R that are not NaN. */
 stmf_status stmf_row_sketch(stmf_ctx *ctx, int m, int n, const float *R, int ldr, const uint32_t *mask,
                             int ldm_words, float *sketch, float *median);
 /* Number of parameters of the MLP for rank r (-1 if r is out of range).
@@ -288,8 +292,11 @@ stmf_status stmf_mlp_gradient(stmf_mlp *mlp, int B, const float *X, const float 
 stmf_status stmf_mlp_train_step(stmf_mlp *mlp, int B, const float *X, const float *T, float lr, double *loss);
 
 /* Fills *opts with the defaults (sweeps 1, eps 0, library window, first
- * improving, FP32, acol_p 5, seed 0, no explicit draws, no trace). */
+ * improving, FP32, acol_p 5, seed 0, no explicit draws, no trace, no MLP). */
 void stmf_default_options(stmf_options *opts);
+/* sizeof of the ABI's structs as this library was compiled (host pointers,
+ * each nullable), so that a binding can check its own layouts. */
+void stmf_struct_sizes(size_t *options, size_t *report, size_t *batch_problem);
 
 /* FP32 add+max issue-rate microbenchmark: runs `iters` dependent-chain
  * iterations of (FADD, FMNMX) pairs on every SM and returns, in *gops

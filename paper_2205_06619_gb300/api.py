@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "OOM", 4: "TIMEOUT", 5: "INTERNAL
 EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", "stmf_maxplus",
            "stmf_selection_stats", "stmf_problem_create", "stmf_problem_destroy", "stmf_update_U",
            "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_factorize_begin",
-           "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_peak_addmax",
+           "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_struct_sizes",
+           "stmf_peak_addmax",
            "stmf_selection_stats_noalloc", "stmf_factorize_batched", "stmf_row_sketch", "stmf_mlp_param_count",
            "stmf_mlp_create", "stmf_mlp_destroy", "stmf_mlp_get_params", "stmf_mlp_forward", "stmf_mlp_gradient",
            "stmf_mlp_train_step"]
@@ -39,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("eps", C.c_double), ("window", C.c_int), ("select", C.c_int),
                 ("precision", C.c_int), ("acol_p", C.c_int), ("seed", C.c_uint64),
                 ("perm", C.c_void_p), ("picks", C.c_void_p), ("U0", C.c_void_p),
-                ("trace", C.c_void_p), ("trace_cap", C.c_int64)]
+                ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("mlp", C.c_void_p)]
 
 
 class BatchProblem(C.Structure):
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True):
     L.stmf_mlp_train_step.argtypes = [P, i, P, P, C.c_float, C.POINTER(d)]
     L.stmf_default_options.argtypes = [C.POINTER(Options)]
     L.stmf_default_options.restype = None
+    L.stmf_struct_sizes.argtypes = [C.POINTER(C.c_size_t)] * 3
+    L.stmf_struct_sizes.restype = None
     L.stmf_peak_addmax.argtypes = [P, i, i, C.POINTER(d)]
     for name in EXPORTS:
         if name not in ("stmf_destroy", "stmf_last_error", "stmf_problem_destroy", "stmf_default_options",
@@ -256,7 +259,7 @@ def selection_stats_noalloc(R, U, V, mask_words=None, td_col=None, colhist=None)
 
 
 def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=0, perm=None, picks=None,
-             U0=None, trace=None):
+             U0=None, trace=None, mlp=None):
     o = Options()
     load().stmf_default_options(C.byref(o))
     o.sweeps, o.eps, o.window, o.select, o.precision, o.acol_p, o.seed = (
@@ -270,6 +273,8 @@ def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=
         _check_f32(U0, "U0"); keep.append(U0); o.U0 = U0.data_ptr()
     if trace is not None:
         keep.append(trace); o.trace = trace.ctypes.data; o.trace_cap = trace.shape[0]
+    if mlp is not None:
+        keep.append(mlp); o.mlp = mlp.h.value
     return o, keep
 
 
@@ -332,8 +337,9 @@ def decode_trace(trace: np.ndarray):
 
 
 def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5,
-              seed=0, perm=None, picks=None, U0=None, trace_cap=0):
+              seed=0, perm=None, picks=None, U0=None, trace_cap=0, mlp=None):
     """FastSTMF (Algorithm 3) on the device.  R: float32 CUDA (m x n).
+    mlp: an MLP (learned initialisation on the device) or None (Random Acol).
 
     Returns (U m x r, V r x n, report dict, trace list or None)."""
     torch = _torch()
@@ -341,7 +347,7 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     m, n = R.shape
     ctx = context()
     trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
-    o, keep = _options(sweeps, eps, window, select, precision, acol_p, seed, perm, picks, U0, trace)
+    o, keep = _options(sweeps, eps, window, select, precision, acol_p, seed, perm, picks, U0, trace, mlp)
     U = torch.empty((m, rank), device=R.device, dtype=torch.float32)
     V = torch.empty((rank, n), device=R.device, dtype=torch.float32)
     rep = Report()
@@ -354,7 +360,7 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     return U, V, rep.as_dict(), tr
 
 
-def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0):
+def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0, mlp=None):
     """Many independent problems in one device launch (stmf_factorize_batched).
 
     problems: list of dicts with R (float32 CUDA m x n), mask_words (or None),
@@ -377,7 +383,7 @@ def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0):
                               0 if mw is None else mw.shape[1], U.data_ptr(), V.data_ptr(), pr.get("seed", 0),
                               pr.get("sweeps", 1))
         outs.append((U, V))
-    o, keep = _options(0, eps, window, select, precision)
+    o, keep = _options(0, eps, window, select, precision, mlp=mlp)
     reps = (Report * max(n, 1))()
     tuned = (C.c_int * max(n, 1))()
     ctx.check(load().stmf_factorize_batched(ctx.h, n, arr, C.byref(o), reps, tuned))
@@ -456,12 +462,13 @@ class Factorization:
     orientation; ``report`` holds the cumulative counters."""
 
     def __init__(self, R, mask_words=None, rank=3, window=0, select=0, precision=0, acol_p=5, seed=0,
-                 perm=None, picks=None, U0=None, trace_cap=0):
+                 perm=None, picks=None, U0=None, trace_cap=0, mlp=None):
         _check_f32(R, "R")
         self.ctx = context()
         self.m, self.n, self.r = R.shape[0], R.shape[1], rank
         self.trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
-        o, self._keep = _options(0, 0.0, window, select, precision, acol_p, seed, perm, picks, U0, self.trace)
+        o, self._keep = _options(0, 0.0, window, select, precision, acol_p, seed, perm, picks, U0, self.trace,
+                                 mlp)
         h = C.c_void_p()
         ldm = mask_words.shape[1] if mask_words is not None else 0
         self.ctx.check(load().stmf_factorize_begin(self.ctx.h, self.m, self.n, rank, _ptr(R), R.stride(0),

@@ -203,5 +203,9 @@ constexpr int SCR_THREADS = 128;
 cudaError_t screen_prepare(stmf_problem *P);
 cudaError_t launch_screen(cudaStream_t st, stmf_problem *P);
 
+// mlp.cu
+stmf_status mlp_predict_rows(stmf_ctx *ctx, stmf_mlp *M, int m, int n, const float *R, int ldr, float *U0);
+int mlp_rank(const stmf_mlp *M);
+
 // peak.cu
 cudaError_t launch_peak(cudaStream_t st, int mode, int iters, int blocks, float *sink);

@@ -35,10 +35,11 @@ __global__ void __launch_bounds__(1024) k_row_sketch(const float *__restrict__ R
     __syncthreads();
     // compact the given entries (order irrelevant: they are sorted next)
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const bool given = mask ? ((mask[(size_t)s * ldm + (t >> 5)] >> (t & 31)) & 1u) : true;
+        const float v = R[(size_t)s * ldr + t];
+        const bool given = mask ? ((mask[(size_t)s * ldm + (t >> 5)] >> (t & 31)) & 1u) : v == v;
         if (given) {
             const int p = atomicAdd(&scnt, 1);
-            sv[p] = R[(size_t)s * ldr + t];
+            sv[p] = v;
         }
     }
     __syncthreads();
@@ -244,7 +245,52 @@ void launch_fwd(stmf_mlp *M, int B, const float *X, float *H1, float *H2, float 
     k_mlp_fwd<<<(B + 31) / 32, HID, 0, M->ctx->stream>>>(B, M->r, X, W1, b1, W2, b2, W3, b3, H1, H2, Y);
 }
 
+// U0[s][l] = Y[s][l] + median[s]
+__global__ void k_add_median(const float *__restrict__ Y, const float *__restrict__ med, int m, int r,
+                             float *__restrict__ U0)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m * r) U0[e] = Y[e] + med[e / r];
+}
+
 }  // namespace
+
+// Learned initial rows of a problem (the addition to Algorithm 3's Random
+// Acol start): U0[s] = MLP(sketch of row s) + median of row s, with the row's
+// given entries those of R that are not NaN.  Runs on ctx's stream, which must
+// be the MLP's.
+stmf_status mlp_predict_rows(stmf_ctx *ctx, stmf_mlp *M, int m, int n, const float *R, int ldr, float *U0)
+{
+    if (M->ctx != ctx) return mfail(ctx, STMF_ERR_INVALID, "the MLP was created on another context");
+    if (n > 12288) return mfail(ctx, STMF_ERR_INVALID, "learned initialisation needs n <= 12288 (row sketch)");
+    float *buf = nullptr;
+    const size_t nsk = (size_t)m * SK, nmd = (size_t)m, ny = (size_t)m * M->r;
+    cudaError_t e = cudaMalloc(&buf, sizeof(float) * (nsk + nmd + ny));
+    if (e != cudaSuccess) return mfail(ctx, STMF_ERR_OOM, cudaGetErrorString(e));
+    float *sk = buf, *md = buf + nsk, *Y = md + nmd;
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    const size_t smem = sizeof(float) * np2;
+    if (smem > 48 * 1024)
+        e = cudaFuncSetAttribute(k_row_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        k_row_sketch<<<m, 1024, smem, ctx->stream>>>(R, ldr, nullptr, 0, m, n, np2, sk, md);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        launch_fwd(M, m, sk, nullptr, nullptr, Y);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_add_median<<<(unsigned)((ny + 255) / 256), 256, 0, ctx->stream>>>(Y, md, m, M->r, U0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    return e == cudaSuccess ? STMF_OK : mfail(ctx, STMF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int mlp_rank(const stmf_mlp *M) { return M->r; }
 
 extern "C" {
 

@@ -471,7 +471,20 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (d_bad) cudaFree(d_bad);
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "pack: %s", cudaGetErrorString(e)); }
     if (bad) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "a given entry of R is not finite or has magnitude >= 2^60"); }
-    s = problem_init(P, o.U0, o.acol_p, o.seed, o.picks);
+    float *U0_learned = nullptr;
+    if (o.mlp && !o.U0) {
+        stmf_mlp *net = const_cast<stmf_mlp *>(o.mlp);
+        if (mlp_rank(net) != r) { problem_free(P); return fail(ctx, STMF_ERR_INVALID, "the MLP's rank is not r"); }
+        if (cudaMalloc(&U0_learned, sizeof(float) * (size_t)m * r) != cudaSuccess) {
+            problem_free(P);
+            cudaGetLastError();
+            return fail(ctx, STMF_ERR_OOM, "learned initialisation buffer");
+        }
+        s = mlp_predict_rows(ctx, net, m, n, P->R, P->np, U0_learned);
+        if (s != STMF_OK) { cudaFree(U0_learned); problem_free(P); return s; }
+    }
+    s = problem_init(P, o.U0 ? o.U0 : U0_learned, o.acol_p, o.seed, o.picks);
+    if (U0_learned) cudaFree(U0_learned);
     if (s != STMF_OK) { problem_free(P); return s; }
     e = cudaSuccess;
     if (o.trace && o.trace_cap > 0) {
@@ -702,6 +715,13 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
 }  // namespace
 
 extern "C" {
+
+void stmf_struct_sizes(size_t *options, size_t *report, size_t *batch_problem)
+{
+    if (options) *options = sizeof(stmf_options);
+    if (report) *report = sizeof(stmf_report);
+    if (batch_problem) *batch_problem = sizeof(stmf_batch_problem);
+}
 
 void stmf_default_options(stmf_options *o)
 {

@@ -41,7 +41,17 @@ def test_default_options_without_gpu():
     lib = api.load()
     o = api.Options()
     lib.stmf_default_options(ctypes.byref(o))
-    assert o.sweeps == 1 and o.acol_p == 5 and o.window == 0 and o.seed == 0 and not o.trace
+    assert o.sweeps == 1 and o.acol_p == 5 and o.window == 0 and o.seed == 0 and not o.trace and not o.mlp
+
+
+def test_struct_layouts_match_the_library():
+    """The binding's ctypes structs have the sizes the library was built with."""
+    from paper_2205_06619_gb300 import api
+    lib = api.load()
+    sizes = [ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()]
+    lib.stmf_struct_sizes(*[ctypes.byref(x) for x in sizes])
+    assert [x.value for x in sizes] == [ctypes.sizeof(api.Options), ctypes.sizeof(api.Report),
+                                        ctypes.sizeof(api.BatchProblem)]
 
 
 def test_invalid_arguments_fail_without_launch():

@@ -107,3 +107,27 @@ def test_learned_start_against_untrained_and_acol():
         for name in ("trained", "untrained", "acol"):
             assert np.isfinite(r[name]) and r[name] > 0
         assert r["trained_1"] < r["trained"] and r["untrained_1"] < r["untrained"]
+
+
+def test_learned_start_inside_the_library_equals_the_binding_path():
+    """stmf_options.mlp: the library computes U0 = MLP(row sketch) + median on
+    the oriented, permuted problem; the result equals passing the same start
+    as U0 from the binding (rows permuted by the caller)."""
+    from paper_2205_06619_gb300 import api
+    X, T = learned_init.training_set(count=8, m=60, n=300, rank=5, sweeps=2, seed=5)
+    net, _ = learned_init.train(X, T, rank=5, epochs=5, batch=64, lr=2e-3)
+    R, M = learned_init.gene_like(50, 240, seed=7)
+    Rg, Mw = torch.from_numpy(R).cuda(), api.pack_mask(M)
+    perm = np.random.default_rng(3).permutation(50).astype(np.int32)
+    U0 = learned_init.predict_U(net, Rg, Mw)[torch.from_numpy(perm.astype(np.int64)).cuda()].contiguous()
+    a = api.factorize(Rg, Mw, rank=5, sweeps=2, perm=perm, U0=U0, trace_cap=200)
+    b = api.factorize(Rg, Mw, rank=5, sweeps=2, perm=perm, mlp=net, trace_cap=200)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert a[2]["f_init"] == b[2]["f_init"] and a[3] == b[3]
+    with pytest.raises(api.StmfError, match="rank"):
+        api.factorize(Rg, Mw, rank=4, sweeps=1, mlp=net)
+    # the batched form takes the network for every problem
+    probs = [dict(R=Rg, mask_words=Mw, rank=5, sweeps=1, seed=q) for q in range(2)]
+    outs, _ = api.factorize_batched(probs, window=8, mlp=net)
+    for U, V, rep in outs:
+        assert torch.isfinite(U).all() and rep["f_final"] <= rep["f_init"]
