@@ -188,6 +188,7 @@ cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph);
 cudaError_t launch_res(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_delta(cudaStream_t st, stmf_problem *P);
 int delta_grid(const stmf_problem *P);
+int delta_parts(const stmf_problem *P);   // phase-2 partials per candidate
 int delta_depth(const stmf_problem *P);
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);

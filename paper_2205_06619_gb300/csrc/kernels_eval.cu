@@ -282,6 +282,8 @@ int delta_grid(const stmf_problem *P)
     return ntiles < cap ? ntiles : cap;
 }
 
+int delta_parts(const stmf_problem *P) { return delta_grid(P); }
+
 int delta_depth(const stmf_problem *P)
 {
     const int ntiles = ((P->m + 3) / 4) * ((P->np + DEL_COLS - 1) / DEL_COLS);

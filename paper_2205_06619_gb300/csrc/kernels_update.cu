@@ -724,7 +724,7 @@ cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph)
 
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single)
 {
-    k_select<<<1, 1024, 0, st>>>(*P, delta_grid(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
+    k_select<<<1, 1024, 0, st>>>(*P, delta_parts(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
     return cudaGetLastError();
 }
 
