@@ -85,6 +85,11 @@ typedef struct {
                             (m x r, ld r); replaces Random Acol                          */
     int32_t *trace;      /* HOST, nullable: one record of STMF_TRACE_INTS per row visit */
     int64_t trace_cap;   /* capacity of trace in records                               */
+    const float *V0;     /* DEVICE, nullable, needs U0: V of the oriented problem (r x n,
+                            ld n) used as given instead of the residuation of U0.
+                            With the U0, V0 and perm of a saved state, a new run
+                            continues exactly as the interrupted one would have
+                            (checkpoint / resume between sweeps).                  */
     const stmf_mlp *mlp; /* nullable: learned initialisation (an addition to the paper).
                             U0 of the oriented, permuted problem = MLP(row sketch) +
                             row median, computed on the device; the network's rank

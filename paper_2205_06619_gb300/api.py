@@ -40,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("eps", C.c_double), ("window", C.c_int), ("select", C.c_int),
                 ("precision", C.c_int), ("acol_p", C.c_int), ("seed", C.c_uint64),
                 ("perm", C.c_void_p), ("picks", C.c_void_p), ("U0", C.c_void_p),
-                ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("mlp", C.c_void_p)]
+                ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("V0", C.c_void_p), ("mlp", C.c_void_p)]
 
 
 class BatchProblem(C.Structure):
@@ -259,7 +259,7 @@ def selection_stats_noalloc(R, U, V, mask_words=None, td_col=None, colhist=None)
 
 
 def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=0, perm=None, picks=None,
-             U0=None, trace=None, mlp=None):
+             U0=None, trace=None, mlp=None, V0=None):
     o = Options()
     load().stmf_default_options(C.byref(o))
     o.sweeps, o.eps, o.window, o.select, o.precision, o.acol_p, o.seed = (
@@ -275,6 +275,8 @@ def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=
         keep.append(trace); o.trace = trace.ctypes.data; o.trace_cap = trace.shape[0]
     if mlp is not None:
         keep.append(mlp); o.mlp = mlp.h.value
+    if V0 is not None:
+        _check_f32(V0, "V0"); keep.append(V0); o.V0 = V0.data_ptr()
     return o, keep
 
 
@@ -336,8 +338,26 @@ def decode_trace(trace: np.ndarray):
     return out
 
 
+def sweep_log(trace):
+    """Per-sweep summary of trace records (one JSON-ready dict per sweep, in
+    sweep order): rows visited, updates kept, the b-norm error after the
+    sweep, and the mean position of the kept candidates in their rows'
+    candidate order."""
+    acc = {}
+    for (sw, row, pos, j, k, typ, f) in trace:
+        d = acc.setdefault(sw, {"sweep": sw, "rows": 0, "accepted": 0, "f": f, "pos_sum": 0})
+        d["rows"] += 1
+        d["f"] = f
+        if pos >= 0:
+            d["accepted"] += 1
+            d["pos_sum"] += pos
+    return [{"sweep": d["sweep"], "rows": d["rows"], "accepted": d["accepted"], "f": d["f"],
+             "mean_kept_position": d["pos_sum"] / d["accepted"] if d["accepted"] else None}
+            for _, d in sorted(acc.items())]
+
+
 def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5,
-              seed=0, perm=None, picks=None, U0=None, trace_cap=0, mlp=None):
+              seed=0, perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None):
     """FastSTMF (Algorithm 3) on the device.  R: float32 CUDA (m x n).
     mlp: an MLP (learned initialisation on the device) or None (Random Acol).
 
@@ -347,7 +367,7 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     m, n = R.shape
     ctx = context()
     trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
-    o, keep = _options(sweeps, eps, window, select, precision, acol_p, seed, perm, picks, U0, trace, mlp)
+    o, keep = _options(sweeps, eps, window, select, precision, acol_p, seed, perm, picks, U0, trace, mlp, V0)
     U = torch.empty((m, rank), device=R.device, dtype=torch.float32)
     V = torch.empty((rank, n), device=R.device, dtype=torch.float32)
     rep = Report()
@@ -462,13 +482,13 @@ class Factorization:
     orientation; ``report`` holds the cumulative counters."""
 
     def __init__(self, R, mask_words=None, rank=3, window=0, select=0, precision=0, acol_p=5, seed=0,
-                 perm=None, picks=None, U0=None, trace_cap=0, mlp=None):
+                 perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None):
         _check_f32(R, "R")
         self.ctx = context()
         self.m, self.n, self.r = R.shape[0], R.shape[1], rank
         self.trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
         o, self._keep = _options(0, 0.0, window, select, precision, acol_p, seed, perm, picks, U0, self.trace,
-                                 mlp)
+                                 mlp, V0)
         h = C.c_void_p()
         ldm = mask_words.shape[1] if mask_words is not None else 0
         self.ctx.check(load().stmf_factorize_begin(self.ctx.h, self.m, self.n, rank, _ptr(R), R.stride(0),

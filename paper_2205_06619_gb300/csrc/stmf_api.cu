@@ -10,6 +10,8 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace {
@@ -79,9 +81,29 @@ stmf_status fail(stmf_ctx *ctx, stmf_status st, const char *fmt, ...)
             return fail(c, STMF_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));               \
     } while (0)
 
+// NVTX ranges (header-only NVTX 3) around the host driver's phases, so a
+// timeline tool shows preparation, sweeps, the batched launch and tuning.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// Host-side fault injection for tests: with STMF_TEST_FAIL_ALLOC=N in the
+// environment, the N-th device allocation of every problem reports
+// cudaErrorMemoryAllocation (nothing is allocated), so the error paths can be
+// exercised without exhausting or faulting a GPU.
+int g_alloc_index = 0;
+
 template <class T>
 cudaError_t dalloc(T **p, size_t count)
 {
+    const char *inj = getenv("STMF_TEST_FAIL_ALLOC");
+    if (inj && ++g_alloc_index == atoi(inj)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
 }
 
@@ -110,6 +132,7 @@ cudaError_t set_ctl(stmf_problem *P, T stmf_ctl::*field, T value)
 
 stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_problem **out)
 {
+    g_alloc_index = 0;
     stmf_problem *P = new stmf_problem();
     memset(P, 0, sizeof(*P));
     P->ctx = ctx;
@@ -169,7 +192,8 @@ stmf_status refresh(stmf_problem *P)
 }
 
 // After R is packed: checks, RT, U, V = (-U)^T (x)* R, statistics, planes, f.
-stmf_status problem_init(stmf_problem *P, const float *U0, int acol_p, uint64_t seed, const int32_t *picks_in)
+stmf_status problem_init(stmf_problem *P, const float *U0, int acol_p, uint64_t seed, const int32_t *picks_in,
+                         const float *V0 = nullptr)
 {
     stmf_ctx *ctx = P->ctx;
     cudaStream_t st = ctx->stream;
@@ -204,12 +228,17 @@ stmf_status problem_init(stmf_problem *P, const float *U0, int acol_p, uint64_t 
         CK(cudaStreamSynchronize(st));
         cudaFree(d_picks);
     }
-    // V = (-U)^T (x)* R: the column minima of component l are the min1 of its
-    // column statistics.
     CK(set_ctl(P, &stmf_ctl::dirty_k, -1));
-    CK(launch_stats(st, P));
-    CK(launch_copy_rows(st, P->cmin1, P->np, P->V, P->np, P->r, P->n));
-    stmf_status s = refresh(P);        // row statistics of the new V, planes, f
+    if (V0) {
+        // a saved state (checkpoint): V as given, no residuation
+        CK(launch_copy_rows(st, V0, P->n, P->V, P->np, P->r, P->n));
+    } else {
+        // V = (-U)^T (x)* R: the column minima of component l are the min1 of
+        // its column statistics.
+        CK(launch_stats(st, P));
+        CK(launch_copy_rows(st, P->cmin1, P->np, P->V, P->np, P->r, P->n));
+    }
+    stmf_status s = refresh(P);        // statistics of the new (U, V), planes, f
     if (s != STMF_OK) return s;
     return STMF_OK;
 }
@@ -420,6 +449,7 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (o.window < 0 || o.window > STMF_WMAX) return fail(ctx, STMF_ERR_INVALID, "window outside [0, %d]", STMF_WMAX);
     if (o.precision < 0 || o.precision > 1) return fail(ctx, STMF_ERR_INVALID, "precision mode %d unknown", o.precision);
     if (o.select < 0 || o.select > 1) return fail(ctx, STMF_ERR_INVALID, "select mode %d unknown", o.select);
+    if (o.V0 && !o.U0) return fail(ctx, STMF_ERR_INVALID, "V0 needs U0");
     const int tr = m0 > n0;                 // Algorithm 3: a tall R is transposed
     const int m = tr ? n0 : m0, n = tr ? m0 : n0;
     std::vector<int> perm;
@@ -483,7 +513,7 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
         s = mlp_predict_rows(ctx, net, m, n, P->R, P->np, U0_learned);
         if (s != STMF_OK) { cudaFree(U0_learned); problem_free(P); return s; }
     }
-    s = problem_init(P, o.U0 ? o.U0 : U0_learned, o.acol_p, o.seed, o.picks);
+    s = problem_init(P, o.U0 ? o.U0 : U0_learned, o.acol_p, o.seed, o.picks, o.U0 ? o.V0 : nullptr);
     if (U0_learned) cudaFree(U0_learned);
     if (s != STMF_OK) { problem_free(P); return s; }
     e = cudaSuccess;
@@ -512,6 +542,7 @@ stmf_status fastmf_run(stmf_problem *P, int sweeps, double eps)
     }
     auto t0 = std::chrono::steady_clock::now();
     for (int sw = 0; sw < sweeps; ++sw) {
+        NvtxRange range("stmf sweep");
         const double f_prev = P->ctl_host->f;
         CK(set_ctl(P, &stmf_ctl::sweep, P->sweeps_done));
         if (graph) {
@@ -613,6 +644,7 @@ stmf_status tune_window(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_
     for (int w : trial) {
         stmf_options o = base;
         o.window = w; o.trace = nullptr; o.trace_cap = 0; o.perm = nullptr; o.picks = nullptr; o.U0 = nullptr;
+        o.V0 = nullptr;
         o.seed = bp.seed;
         stmf_problem *P = nullptr;
         CS(fastmf_begin(ctx, bp.m, bp.n, bp.r, bp.R, bp.ldr, bp.mask, bp.ldm_words, &o, &P));
@@ -677,6 +709,7 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
         const stmf_batch_problem &b = probs[q];
         stmf_options po = o;
         po.window = win[q]; po.seed = b.seed; po.perm = nullptr; po.picks = nullptr; po.U0 = nullptr;
+        po.V0 = nullptr;
         po.trace = nullptr; po.trace_cap = 0;
         CS(fastmf_begin(ctx, b.m, b.n, b.r, b.R, b.ldr, b.mask, b.ldm_words, &po, &Ps[q]));
         CK(set_ctl(Ps[q], &stmf_ctl::sweep_target, b.sweeps));
@@ -915,7 +948,11 @@ stmf_status stmf_factorize(stmf_ctx *ctx, int m0, int n0, int r, const float *R,
     if (opts) o = *opts; else stmf_default_options(&o);
     if (o.sweeps < 0) return fail(ctx, STMF_ERR_INVALID, "sweeps < 0");
     stmf_problem *P = nullptr;
-    stmf_status s = fastmf_begin(ctx, m0, n0, r, R, ldr, mask, ldm_words, &o, &P);
+    stmf_status s;
+    {
+        NvtxRange range("stmf prepare (orientation, init, planes)");
+        s = fastmf_begin(ctx, m0, n0, r, R, ldr, mask, ldm_words, &o, &P);
+    }
     if (s != STMF_OK) return s;
     s = fastmf_run(P, o.sweeps, o.eps);
     if (s == STMF_OK) s = fastmf_end(P, U_out, V_out, o.trace, o.trace_cap);
@@ -930,6 +967,7 @@ stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_pr
     if (!ctx) return STMF_ERR_INVALID;
     if (nprob < 0 || (nprob > 0 && !probs)) return fail(ctx, STMF_ERR_INVALID, "bad problem list");
     if (nprob == 0) return STMF_OK;
+    NvtxRange range("stmf batched factorization");
     return batched(ctx, nprob, probs, opts, reports, tuned_windows);
 }
 

@@ -85,3 +85,12 @@ def test_mask_packing_layout():
     for s in range(5):
         for t in range(70):
             assert bool((W[s, t // 32] >> (t % 32)) & 1) == M[s, t]
+
+
+def test_sweep_log_summarises_trace_records():
+    from paper_2205_06619_gb300 import api
+    trace = [(0, 3, 2, 7, 1, 0, 10.0), (0, 1, -1, -1, -1, -1, 10.0), (0, 0, 4, 2, 0, 1, 8.5),
+             (1, 3, -1, -1, -1, -1, 8.5), (1, 1, 0, 5, 1, 0, 8.0), (1, 0, -1, -1, -1, -1, 8.0)]
+    log = api.sweep_log(trace)
+    assert log == [{"sweep": 0, "rows": 3, "accepted": 2, "f": 8.5, "mean_kept_position": 3.0},
+                   {"sweep": 1, "rows": 3, "accepted": 1, "f": 8.0, "mean_kept_position": 0.0}]

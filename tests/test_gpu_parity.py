@@ -264,3 +264,47 @@ def test_graph_and_host_driven_loops_agree(monkeypatch):
     b = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=2, seed=2, trace_cap=200)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     assert [t[:6] for t in a[3]] == [t[:6] for t in b[3]]
+
+
+# ------------------------------------------------------ checkpoint / faults
+
+def test_resume_from_saved_state_equals_the_uninterrupted_run():
+    """Checkpoint / resume: the factors and permutation after sweep 1, passed
+    back as U0, V0 and perm, continue exactly as the uninterrupted run."""
+    R, M, _, _ = synth.uniform_planted(40, 90, 4, 0.01, 0.8, seed=12)
+    Rg, Mw = tg(R), api().pack_mask(M)
+    perm = np.random.default_rng(5).permutation(40).astype(np.int32)
+    full = api().factorize(Rg, Mw, rank=4, sweeps=3, seed=1, perm=perm, trace_cap=500)
+    fz = api().Factorization(Rg, Mw, rank=4, seed=1, perm=perm)
+    fz.run(1)
+    U1, V1 = fz.result()
+    fz.close()
+    U0 = U1[torch.from_numpy(perm.astype(np.int64)).cuda()].contiguous()    # oriented, permuted rows
+    res = api().factorize(Rg, Mw, rank=4, sweeps=2, perm=perm, U0=U0, V0=V1.contiguous(), trace_cap=500)
+    assert torch.equal(res[0], full[0]) and torch.equal(res[1], full[1])
+    assert res[2]["f_final"] == full[2]["f_final"]
+    later = [t[1:] for t in full[3] if t[0] >= 1]
+    assert [t[1:] for t in res[3]] == later
+    with pytest.raises(api().StmfError, match="V0 needs U0"):
+        api().factorize(Rg, Mw, rank=4, sweeps=1, V0=V1.contiguous())
+
+
+def test_injected_allocation_failures_leave_the_context_usable(monkeypatch):
+    """Host-side fault injection (STMF_TEST_FAIL_ALLOC=N fails the N-th device
+    allocation of a problem): the call returns STMF_ERR_OOM, frees what it had
+    allocated and the next call works."""
+    R, M, _, _ = synth.uniform_planted(30, 50, 3, 0.01, 0.8, seed=2)
+    Rg, Mw = tg(R), api().pack_mask(M)
+    ref = api().factorize(Rg, Mw, rank=3, sweeps=1, seed=0)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for n in (1, 2, 7, 13, 20):
+        monkeypatch.setenv("STMF_TEST_FAIL_ALLOC", str(n))
+        with pytest.raises(api().StmfError) as ei:
+            api().factorize(Rg, Mw, rank=3, sweeps=1, seed=0)
+        assert ei.value.status == 3          # STMF_ERR_OOM
+    monkeypatch.delenv("STMF_TEST_FAIL_ALLOC")
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < 64 * 1024 * 1024
+    again = api().factorize(Rg, Mw, rank=3, sweeps=1, seed=0)
+    assert torch.equal(again[0], ref[0]) and torch.equal(again[1], ref[1])
