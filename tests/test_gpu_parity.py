@@ -242,6 +242,20 @@ def test_factorize_ragged_and_degenerate_shapes():
         assert np.array_equal(V.cpu().numpy().astype(np.float64), out["V"]), (m, n, r)
 
 
+@pytest.mark.parametrize("obs,r", [(0.05, 3), (0.5, 20), (1.0, 32)])
+def test_factorize_density_and_rank_extremes_replay(obs, r):
+    """Sparse (5% given), half and fully given matrices at ranks 3, 20 and 32,
+    with n not a multiple of 32: decisions replayed against the oracle."""
+    from tests.replay import replay
+    R, M, _, _ = synth.uniform_planted(45, 301, r, 0.01, obs, seed=int(obs * 100) + r)
+    U, V, rep, trace = api().factorize(tg(R), api().pack_mask(M), rank=r, sweeps=2, seed=3, trace_cap=500)
+    out = replay(R, M, r, trace, seed=3)
+    assert np.array_equal(U.cpu().numpy().astype(np.float64), out["U"])
+    assert np.array_equal(V.cpu().numpy().astype(np.float64), out["V"])
+    assert rel(rep["f_final"], out["f"]) <= TOL
+    assert len(out["divergences"]) <= 1
+
+
 def test_factorize_in_pieces_equals_one_call():
     """Sweeps run in pieces on a live problem give the same run as one call."""
     R, M, _, _ = synth.uniform_planted(30, 64, 3, 0.01, 0.8, seed=31)
