@@ -363,19 +363,19 @@ stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, b
 
     cudaGraph_t target = g;
     if (job) {
-        cudaGraphNode_t jb, wsw;
+        cudaGraphNode_t jb = nullptr, wsw = nullptr;
         CS(capture_into(ctx, cap, g, nullptr, 0, [&](cudaStream_t c) { return launch_job_begin(c, P); }, &jb));
         CS(add_conditional(ctx, g, &jb, 1, hs, cudaGraphCondTypeWhile, &wsw, &target));
     }
-    cudaGraphNode_t sb, wrow;
+    cudaGraphNode_t sb = nullptr, wrow = nullptr;
     CS(capture_into(ctx, cap, target, nullptr, 0, [&](cudaStream_t c) { return launch_sweep_begin(c, P, 1); }, &sb));
-    cudaGraph_t body_row;
+    cudaGraph_t body_row = nullptr;
     CS(add_conditional(ctx, target, &sb, 1, hr, cudaGraphCondTypeWhile, &wrow, &body_row));
     if (job)
         CS(capture_into(ctx, cap, target, &wrow, 1, [&](cudaStream_t c) { return launch_sweep_end(c, P); }, nullptr));
 
-    cudaGraphNode_t nif, rb, wwin;
-    cudaGraph_t body_ref, body_win;
+    cudaGraphNode_t nif = nullptr, rb = nullptr, wwin = nullptr;
+    cudaGraph_t body_ref = nullptr, body_win = nullptr;
     CS(add_conditional(ctx, body_row, nullptr, 0, hd, cudaGraphCondTypeIf, &nif, &body_ref));
     CS(capture_into(ctx, cap, body_ref, nullptr, 0, [&](cudaStream_t c) {
         cudaError_t e = launch_stats(c, P);
