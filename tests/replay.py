@@ -8,7 +8,6 @@ the error before the row (a near-tie with "f decreases").  The oracle then
 adopts the GPU's decision (it applies the same F-ULF / F-URF itself, which in
 FP32 mode reproduces the GPU's factors bit for bit) and continues.
 """
-import numpy as np
 
 import oracle as orc
 

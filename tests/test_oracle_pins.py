@@ -10,7 +10,6 @@ import itertools
 import os
 
 import numpy as np
-import pytest
 
 from paper_2205_06619_gb300 import synth
 

@@ -12,7 +12,6 @@ oracle's own F-ULF / F-URF candidates (no GPU code is involved).
    {x_h >= E_h}.
 """
 import numpy as np
-import pytest
 
 from paper_2205_06619_gb300 import synth
 
