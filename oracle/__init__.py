@@ -27,6 +27,8 @@ _SRC = os.path.join(_HERE, "stmf_oracle.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 
 MODES = {"fp64": 0, "fp32": 1}
+# selections of (j, k) within a row (Section "The ByRow strategy")
+SELECTIONS = {"TD_A": 0, "TD_B": 1, "TD": 2, "SEQ": 3}
 
 _lib = None
 
@@ -67,12 +69,18 @@ def lib():
         L.orc_row_order.argtypes = [i, i, i, i, P, P, P, P, i, P, P]
         L.orc_row_step.restype = i
         L.orc_row_step.argtypes = [i, i, i, i, P, P, P, P, i, P, P, P]
+        L.orc_row_order_sel.restype = i
+        L.orc_row_order_sel.argtypes = [i, i, i, i, i, P, P, P, P, i, P, P]
+        L.orc_row_step_sel.restype = i
+        L.orc_row_step_sel.argtypes = [i, i, i, i, i, P, P, P, P, i, P, P, P]
         L.orc_acol_init.argtypes = [i, i, i, i, P, P, P, i, P]
         L.orc_prepare.restype = i
         L.orc_prepare.argtypes = [i, i, i, i, P, P, P, P, i, u64, P, P, P, P, P, P, P]
         L.orc_finish.argtypes = [i, i, i, i, P, P, P, P, P]
         L.orc_factorize.restype = i
         L.orc_factorize.argtypes = [i, i, i, i, P, P, i, d, P, P, i, u64, P, P, P, P, P, i64, P]
+        L.orc_factorize_sel.restype = i
+        L.orc_factorize_sel.argtypes = [i, i, i, i, i, P, P, i, d, P, P, i, u64, P, P, P, P, P, i64, P]
         _lib = L
     return _lib
 
@@ -174,17 +182,26 @@ def row_stats(R, M, U, V, i, mode="fp32"):
     return td, ch, rh
 
 
-def row_order(R, M, U, V, i, mode="fp32"):
+def _sel(selection):
+    if selection not in SELECTIONS:
+        raise ValueError("selection must be one of %s" % sorted(SELECTIONS))
+    return SELECTIONS[selection]
+
+
+def row_order(R, M, U, V, i, mode="fp32", selection="TD_A"):
+    """The (j, k) pairs of row i in the order the selection tries them."""
     R, M, U, V = _d(R), _m(M), _d(U), _d(V)
     m, n = R.shape
     r = U.shape[1]
-    js = np.empty(n, np.int32); ks = np.empty(n, np.int32)
-    c = lib().orc_row_order(_mode(mode), m, n, r, _p(R), _p(M), _p(U), _p(V), i, _p(js), _p(ks))
+    cap = n * r if selection == "SEQ" else n
+    js = np.empty(cap, np.int32); ks = np.empty(cap, np.int32)
+    c = lib().orc_row_order_sel(_mode(mode), _sel(selection), m, n, r, _p(R), _p(M), _p(U), _p(V), i,
+                                _p(js), _p(ks))
     return js[:c].copy(), ks[:c].copy()
 
 
-def row_step(R, M, U, V, i, f, mode="fp32"):
-    """One ByRow/TD_A row step in place on U, V (float64 arrays).
+def row_step(R, M, U, V, i, f, mode="fp32", selection="TD_A"):
+    """One ByRow row step in place on U, V (float64 arrays).
 
     Returns (kept, f_new, (pos, j, k, type), tried)."""
     R, M = _d(R), _m(M)
@@ -194,8 +211,8 @@ def row_step(R, M, U, V, i, f, mode="fp32"):
     fb = C.c_double(f)
     out = np.full(4, -1, np.int32)
     tried = C.c_int64(0)
-    kept = lib().orc_row_step(_mode(mode), m, n, r, _p(R), _p(M), _p(U), _p(V), i,
-                              C.byref(fb), _p(out), C.byref(tried))
+    kept = lib().orc_row_step_sel(_mode(mode), _sel(selection), m, n, r, _p(R), _p(M), _p(U), _p(V), i,
+                                  C.byref(fb), _p(out), C.byref(tried))
     return bool(kept), fb.value, tuple(int(x) for x in out), tried.value
 
 
@@ -238,8 +255,10 @@ def finish(m0, n0, transposed, Ui, Vi, perm):
 
 
 def factorize(R0, M0, r, sweeps, eps=0.0, perm=None, picks=None, p=5, seed=0, U0=None,
-              mode="fp32", trace_cap=0):
-    """FastSTMF (Algorithm 3).  Returns dict(U, V, f_hist, sweeps, tried, kept, trace)."""
+              mode="fp32", trace_cap=0, selection="TD_A"):
+    """FastSTMF (Algorithm 3) with the row's selection of (j, k) (TD_A as
+    published; TD_B, TD, SEQ of Section "The ByRow strategy").
+    Returns dict(U, V, f_hist, sweeps, tried, kept, trace)."""
     R0, M0 = _d(R0), _m(M0)
     m0, n0 = R0.shape
     p = min(p, max(m0, n0))  # the oriented matrix is wide: n = max(m0, n0)
@@ -250,9 +269,9 @@ def factorize(R0, M0, r, sweeps, eps=0.0, perm=None, picks=None, p=5, seed=0, U0
     perm = None if perm is None else np.ascontiguousarray(perm, np.int32)
     picks = None if picks is None else np.ascontiguousarray(picks, np.int32)
     U0 = None if U0 is None else _d(U0)
-    empty = lib().orc_factorize(_mode(mode), m0, n0, r, _p(R0), _p(M0), sweeps, eps, _p(perm), _p(picks),
-                                p, seed, _p(U0), _p(U), _p(V), _p(f_hist),
-                                _p(trace) if trace_cap else None, trace_cap, _p(counters))
+    empty = lib().orc_factorize_sel(_mode(mode), _sel(selection), m0, n0, r, _p(R0), _p(M0), sweeps, eps,
+                                    _p(perm), _p(picks), p, seed, _p(U0), _p(U), _p(V), _p(f_hist),
+                                    _p(trace) if trace_cap else None, trace_cap, _p(counters))
     if empty:
         raise ValueError("oracle: %d rows/columns without a given entry" % empty)
     done = int(counters[0])

@@ -32,6 +32,12 @@
 #define ORC_FP64 0
 #define ORC_FP32 1
 
+/* selections of (j, k) within a row (Section "The ByRow strategy") */
+#define ORC_SEL_TD_A 0
+#define ORC_SEL_TD_B 1
+#define ORC_SEL_TD 2
+#define ORC_SEL_SEQ 3
+
 static double rnd(int mode, double x) { return mode == ORC_FP32 ? (double)(float)x : x; }
 static double add_(int mode, double a, double b) { return rnd(mode, a + b); }
 static double sub_(int mode, double a, double b) { return rnd(mode, a - b); }
@@ -249,60 +255,127 @@ void orc_row_stats(int mode, int m, int n, int r, const double *R, const uint8_t
     free(A);
 }
 
-/* Candidate order for row i (Algorithm 3): the columns j, sorted by
- * td_col[j] in decreasing order, each with
- *   k_j = argmax_l count_l({f(i,t)}_t  union  {f(t,j)}_t).
- * Readings: only j with R_ij given are candidates (F-ULF needs R_ij);
- * the multiset union adds multiplicities; equal td_col keep the smaller j
- * first; equal counts keep the smaller l.  Returns the number of
- * candidates; js/ks receive them in order.                                  */
-int orc_row_order(int mode, int m, int n, int r, const double *R, const uint8_t *M,
-                  const double *U, const double *V, int i, int32_t *js, int32_t *ks)
+/* Selections of (j, k) for a fixed row i (Section "The ByRow strategy"):
+ *   ORC_SEL_TD_A  columns by err = td_col descending; k = the component that
+ *                 occurs most often in {f(i,t)}_t  union  {f(t,j)}_t
+ *                 (Algorithm 3, the method's default);
+ *   ORC_SEL_TD_B  columns as TD_A; k from the worst entry of row i and of
+ *                 column j:  j0 = argmax_t td(i,t), i0 = argmax_s td(s,j),
+ *                 k = f(i,j0) if (U(x)V)_{i j0} >= (U(x)V)_{i0 j}, else f(i0,j);
+ *   ORC_SEL_TD    columns by their own tropical distance td(i,j) descending;
+ *                 k = f(i,j);
+ *   ORC_SEL_SEQ   columns in increasing j and, for each, k = 0, 1, ..., r-1.
+ * f(s,t) = smallest l attaining max_l (U_sl + V_lt) (Section "The ByRow
+ * strategy").  Readings: only j with R_ij given are candidates; td and the
+ * multisets run over given entries only; every sort is stable on an
+ * increasing list (equal keys keep the smaller index first); every argmax
+ * keeps the smaller index on ties; TD_B's argmaxes are taken over the
+ * entry-wise td of row i and of column j (as printed, err of ByRow is td_col
+ * and does not depend on the row, so its argmax over rows would be
+ * degenerate).  Returns the number of (j, k) pairs; js/ks (capacity n, or
+ * n * r for SEQ) receive them in order.  Each pair is tried as F-ULF, then
+ * F-URF.                                                                     */
+int orc_row_order_sel(int mode, int sel, int m, int n, int r, const double *R, const uint8_t *M,
+                      const double *U, const double *V, int i, int32_t *js, int32_t *ks)
 {
-    double *td_col = (double *)malloc(sizeof(double) * (size_t)n);
-    int32_t *colhist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * r);
-    int32_t *rowhist = (int32_t *)malloc(sizeof(int32_t) * (size_t)r);
-    orc_row_stats(mode, m, n, r, R, M, U, V, i, td_col, colhist, rowhist);
+    double *P1 = (double *)malloc(sizeof(double) * (size_t)m * n);
+    int32_t *A = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    double *td = (double *)malloc(sizeof(double) * (size_t)m * n);
+    orc_maxplus(mode, m, n, r, U, V, P1, A, NULL);
+    for (size_t e = 0; e < (size_t)m * n; ++e) td[e] = M[e] ? fabs(sub_(mode, R[e], P1[e])) : 0.0;
+    const double *tdi = td + (size_t)i * n;
     int cnt = 0;
+    if (sel == ORC_SEL_SEQ) {
+        for (int j = 0; j < n; ++j)
+            if (M[(size_t)i * n + j])
+                for (int k = 0; k < r; ++k) { js[cnt] = j; ks[cnt] = k; ++cnt; }
+        free(P1); free(A); free(td);
+        return cnt;
+    }
     for (int j = 0; j < n; ++j)
         if (M[(size_t)i * n + j]) js[cnt++] = j;
-    /* insertion sort, descending td_col; strict comparison keeps equal keys in
-     * increasing j (a stable sort of an increasing list)                    */
-    for (int a = 1; a < cnt; ++a) {
+    if (sel == ORC_SEL_TD) {
+        for (int a = 1; a < cnt; ++a) {            /* stable insertion sort, td(i,j) descending */
+            int32_t x = js[a];
+            int b = a - 1;
+            while (b >= 0 && tdi[js[b]] < tdi[x]) { js[b + 1] = js[b]; --b; }
+            js[b + 1] = x;
+        }
+        for (int a = 0; a < cnt; ++a) ks[a] = A[(size_t)i * n + js[a]];
+        free(P1); free(A); free(td);
+        return cnt;
+    }
+    /* TD_A and TD_B: td_col over given entries, summed in row order */
+    double *td_col = (double *)calloc((size_t)n, sizeof(double));
+    for (int s = 0; s < m; ++s)
+        for (int t = 0; t < n; ++t)
+            if (M[(size_t)s * n + t]) td_col[t] += td[(size_t)s * n + t];
+    for (int a = 1; a < cnt; ++a) {                /* stable insertion sort, td_col descending */
         int32_t x = js[a];
         int b = a - 1;
         while (b >= 0 && td_col[js[b]] < td_col[x]) { js[b + 1] = js[b]; --b; }
         js[b + 1] = x;
     }
-    for (int a = 0; a < cnt; ++a) {
-        int j = js[a], best = 0;
-        int32_t bestc = -1;
-        for (int l = 0; l < r; ++l) {
-            int32_t c = rowhist[l] + colhist[(size_t)j * r + l];
-            if (c > bestc) { bestc = c; best = l; }
+    if (sel == ORC_SEL_TD_A) {
+        int32_t *colhist = (int32_t *)calloc((size_t)n * r, sizeof(int32_t));
+        int32_t *rowhist = (int32_t *)calloc((size_t)r, sizeof(int32_t));
+        for (int s = 0; s < m; ++s)
+            for (int t = 0; t < n; ++t) {
+                size_t e = (size_t)s * n + t;
+                if (!M[e]) continue;
+                colhist[(size_t)t * r + A[e]] += 1;
+                if (s == i) rowhist[A[e]] += 1;
+            }
+        for (int a = 0; a < cnt; ++a) {
+            int j = js[a], best = 0;
+            int32_t bestc = -1;
+            for (int l = 0; l < r; ++l) {
+                int32_t c = rowhist[l] + colhist[(size_t)j * r + l];
+                if (c > bestc) { bestc = c; best = l; }
+            }
+            ks[a] = best;
         }
-        ks[a] = best;
+        free(colhist); free(rowhist);
+    } else {                                       /* TD_B */
+        int j0 = -1;
+        for (int t = 0; t < n; ++t)
+            if (M[(size_t)i * n + t] && (j0 < 0 || tdi[t] > tdi[j0])) j0 = t;
+        for (int a = 0; a < cnt; ++a) {
+            int j = js[a], i0 = -1;
+            for (int s = 0; s < m; ++s)
+                if (M[(size_t)s * n + j] && (i0 < 0 || td[(size_t)s * n + j] > td[(size_t)i0 * n + j])) i0 = s;
+            ks[a] = P1[(size_t)i * n + j0] >= P1[(size_t)i0 * n + j] ? A[(size_t)i * n + j0]
+                                                                      : A[(size_t)i0 * n + j];
+        }
     }
-    free(td_col); free(colhist); free(rowhist);
+    free(td_col); free(P1); free(A); free(td);
     return cnt;
 }
 
-/* One ByRow step on row i (Algorithm 3, body of the row loop).
- * Reading of the garbled nesting: for each j in order, try F-ULF(i,j,k_j);
- * if the error decreased keep it and end the row, else revert and try
- * F-URF(i,j,k_j) the same way, else revert and go to the next j.
- * "Decreases" is strict: f' < f.  On return *f holds the current error;
- * out = {position in order, j, k, type (0 = F-ULF, 1 = F-URF)} of the kept
- * update; *tried counts the candidates evaluated (both types count).
- * Returns 1 if an update was kept, 0 if the row is left unchanged.         */
-int orc_row_step(int mode, int m, int n, int r, const double *R, const uint8_t *M,
-                 double *U, double *V, int i, double *f, int32_t *out, int64_t *tried)
+/* Candidate order for row i of Algorithm 3 (TD_A).                          */
+int orc_row_order(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                  const double *U, const double *V, int i, int32_t *js, int32_t *ks)
 {
-    int32_t *js = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    return orc_row_order_sel(mode, ORC_SEL_TD_A, m, n, r, R, M, U, V, i, js, ks);
+}
+
+/* One ByRow step on row i (Algorithm 3, body of the row loop) with the
+ * selection sel.  Reading of the garbled nesting: for each (j, k) in order,
+ * try F-ULF(i,j,k); if the error decreased keep it and end the row, else
+ * revert and try F-URF(i,j,k) the same way, else revert and go to the next
+ * pair.  "Decreases" is strict: f' < f.  On return *f holds the current
+ * error; out = {position in order, j, k, type (0 = F-ULF, 1 = F-URF)} of the
+ * kept update; *tried counts the candidates evaluated (both types count).
+ * Returns 1 if an update was kept, 0 if the row is left unchanged.         */
+int orc_row_step_sel(int mode, int sel, int m, int n, int r, const double *R, const uint8_t *M,
+                     double *U, double *V, int i, double *f, int32_t *out, int64_t *tried)
+{
+    const size_t cap = (size_t)n * (sel == ORC_SEL_SEQ ? r : 1);
+    int32_t *js = (int32_t *)malloc(sizeof(int32_t) * cap);
+    int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * cap);
     double *ucol = (double *)malloc(sizeof(double) * (size_t)m);
     double *vrow = (double *)malloc(sizeof(double) * (size_t)n);
-    int cnt = orc_row_order(mode, m, n, r, R, M, U, V, i, js, ks);
+    int cnt = orc_row_order_sel(mode, sel, m, n, r, R, M, U, V, i, js, ks);
     int kept = 0;
     for (int a = 0; a < cnt && !kept; ++a) {
         int j = js[a], k = ks[a];
@@ -325,6 +398,12 @@ int orc_row_step(int mode, int m, int n, int r, const double *R, const uint8_t *
     if (!kept && out) { out[0] = -1; out[1] = -1; out[2] = -1; out[3] = -1; }
     free(js); free(ks); free(ucol); free(vrow);
     return kept;
+}
+
+int orc_row_step(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                 double *U, double *V, int i, double *f, int32_t *out, int64_t *tried)
+{
+    return orc_row_step_sel(mode, ORC_SEL_TD_A, m, n, r, R, M, U, V, i, f, out, tried);
 }
 
 /* Random Acol initialisation of U (Section "Comparison of strategies"):
@@ -416,7 +495,8 @@ void orc_finish(int m0, int n0, int r, int transposed, const double *Ui, const d
     }
 }
 
-/* FastSTMF, Algorithm 3 (STMF_ByRow_RandPerm_TD_A_W).
+/* FastSTMF, Algorithm 3 (STMF_ByRow_RandPerm_TD_A_W), with the row's
+ * selection sel (ORC_SEL_*; TD_A is the published method).
  * Sweeps over all rows; stops after `sweeps` sweeps, or earlier when
  * eps > 0 and the error changed by less than eps over a sweep (Section
  * "Comparison of strategies": convergence when the change in error is below
@@ -427,10 +507,10 @@ void orc_finish(int m0, int n0, int r, int transposed, const double *Ui, const d
  * counters (nullable) = {sweeps done, candidates tried, updates kept,
  * trace records written}.  Returns the number of empty rows + columns found
  * (0 on success; the run is skipped otherwise).                             */
-int orc_factorize(int mode, int m0, int n0, int r, const double *R0, const uint8_t *M0,
-                  int sweeps, double eps, const int32_t *perm_in, const int32_t *picks_in,
-                  int p, uint64_t seed, const double *U0, double *U_out, double *V_out,
-                  double *f_hist, int32_t *trace, int64_t trace_cap, int64_t *counters)
+int orc_factorize_sel(int mode, int sel, int m0, int n0, int r, const double *R0, const uint8_t *M0,
+                      int sweeps, double eps, const int32_t *perm_in, const int32_t *picks_in,
+                      int p, uint64_t seed, const double *U0, double *U_out, double *V_out,
+                      double *f_hist, int32_t *trace, int64_t trace_cap, int64_t *counters)
 {
     int tr = m0 > n0;
     int m = tr ? n0 : m0, n = tr ? m0 : n0;
@@ -451,7 +531,7 @@ int orc_factorize(int mode, int m0, int n0, int r, const double *R0, const uint8
             double f_prev = f;
             for (int i = 0; i < m; ++i) {
                 int32_t out[4];
-                kept += orc_row_step(mode, m, n, r, Ri, Mi, Ui, Vi, i, &f, out, &tried);
+                kept += orc_row_step_sel(mode, sel, m, n, r, Ri, Mi, Ui, Vi, i, &f, out, &tried);
                 if (trace && nrec < trace_cap) {
                     int32_t *rec = trace + 6 * nrec;
                     rec[0] = sw; rec[1] = i; rec[2] = out[0]; rec[3] = out[1];
@@ -468,4 +548,14 @@ int orc_factorize(int mode, int m0, int n0, int r, const double *R0, const uint8
     if (counters) { counters[0] = done; counters[1] = tried; counters[2] = kept; counters[3] = nrec; }
     free(Ri); free(Mi); free(Ui); free(Vi); free(perm);
     return empty;
+}
+
+/* Algorithm 3 with the TD_A selection (the method as published).           */
+int orc_factorize(int mode, int m0, int n0, int r, const double *R0, const uint8_t *M0,
+                  int sweeps, double eps, const int32_t *perm_in, const int32_t *picks_in,
+                  int p, uint64_t seed, const double *U0, double *U_out, double *V_out,
+                  double *f_hist, int32_t *trace, int64_t trace_cap, int64_t *counters)
+{
+    return orc_factorize_sel(mode, ORC_SEL_TD_A, m0, n0, r, R0, M0, sweeps, eps, perm_in, picks_in, p, seed,
+                             U0, U_out, V_out, f_hist, trace, trace_cap, counters);
 }
