@@ -311,6 +311,64 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def run_selection(args):
+    """The four selections of (j, k) within a row (Section "The ByRow
+    strategy": TD_A as published, TD_B, TD, SEQ) on the gene-expression
+    workload: sweeps/s over sweeps W..W+K-1 of one run each (CUDA events on
+    the library's stream), with the error reached and the candidates tried.
+    CPU leg: the oracle computing the same row's (j, k) order for each
+    selection from the library's final state."""
+    import torch
+    from paper_2205_06619_gb300 import api, synth
+    w = synth.workload_gene(seed=args.seed)
+    R_np, M_np, r = w["R"], w["mask"], w["rank"]
+    Rg, Mw = torch.from_numpy(R_np).cuda(), api.pack_mask(M_np)
+    stream = api.context().stream
+    res, last = {}, None
+    with ClockSampler(0) as clocks:
+        for sel in ("TD_A", "TD_B", "TD", "SEQ"):
+            fz = api.Factorization(Rg, Mw, rank=r, seed=args.seed, selection=sel)
+            fz.run(args.warmup)
+            rep0 = fz.run(0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            rep1 = fz.run(args.steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            secs = a.elapsed_time(b) / 1e3
+            d = {k: rep1[k] - rep0[k] for k in ("candidates_tried", "candidates_issued", "accepted", "windows",
+                                                "refreshes")}
+            res[sel] = {"sweeps_per_s": args.steps / secs, "f_start": rep0["f_final"], "f_end": rep1["f_final"],
+                        "f_init": rep1["f_init"],
+                        "per_sweep": {k: v / args.steps for k, v in d.items()}}
+            if sel == "TD_A":
+                last = fz.result()
+            fz.close()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle   # CPU leg: the oracle's row orders from the library's TD_A state
+        U, V = (x.cpu().numpy().astype(np.float64) for x in last)
+        st = oracle.prepare(R_np, M_np, r, seed=args.seed)
+        # the factors come back in the caller's frame; the oracle's frame is oriented and permuted
+        Ui = U[st["perm"]]
+        t = time.perf_counter()
+        for sel in ("TD_A", "TD_B", "TD", "SEQ"):
+            oracle.row_order(st["R"], st["M"], Ui, V, 0, selection=sel)
+        secs = time.perf_counter() - t
+        cpu = {"value": 4.0 / secs, "unit": "row orders/s", "cores": 1, "kind": "oracle",
+               "sample": "the (j, k) order of row 0 for each of the 4 selections at 1000x5000, %.1f s" % secs}
+    a_ = res["TD_A"]
+    line = {"metric": METRIC, "value": a_["sweeps_per_s"], "unit": "sweeps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / a_["sweeps_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "selection: gene-expression 1000x5000 rank-10, 80% given, each selection of "
+                                   "(j, k) from the same Random Acol start",
+                       "step": "one ByRow sweep (sweeps W..W+K-1 of each run)", "l2": "not flushed"},
+            "selections": res, "clocks": clocks.summary(), "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Learned initialisation vs Random Acol: sweeps and time to reach the
     plain method's final error on fresh matrices (same permutation for both)."""
@@ -381,7 +439,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5, help="timed sweeps")
     ap.add_argument("--warmup", type=int, default=3, help="untimed warm-up sweeps")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gene", choices=["gene", "small", "large", "batch", "learned", "precision"])
+    ap.add_argument("--workload", default="gene",
+                    choices=["gene", "small", "large", "batch", "learned", "precision", "selection"])
     ap.add_argument("--learned-train", type=int, default=200)
     ap.add_argument("--learned-eval", type=int, default=16)
     ap.add_argument("--learned-m", type=int, default=200)
@@ -405,6 +464,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args)
+        return
+    if args.workload == "selection":
+        run_selection(args)
         return
     if args.workload == "precision":
         run_precision(args)

@@ -59,6 +59,23 @@ typedef struct stmf_ctx stmf_ctx;         /* device, stream, error text       */
 typedef struct stmf_problem stmf_problem; /* R, mask, U, V, planes, stats    */
 typedef struct stmf_mlp stmf_mlp;         /* learned-initialisation network  */
 
+/* Selections of (j, k) within a row (Section "The ByRow strategy").  Every
+ * selection tries its (j, k) pairs in order, F-ULF then F-URF for each, and
+ * keeps the first candidate that lowers the error; only given entries R_ij
+ * are candidates; sorts keep the smaller index first on equal keys, and
+ * every argmax the smaller index on ties.
+ *   TD_A: columns by td_col descending; k = the component occurring most
+ *         often in f(i, .) and f(., j) together (Algorithm 3, the default).
+ *   TD_B: columns as TD_A; j0 = argmax_t td(i,t), i0 = argmax_s td(s,j);
+ *         k = f(i,j0) if (U(x)V)_{i j0} >= (U(x)V)_{i0 j}, else f(i0,j).
+ *         (Reading: the argmaxes run over the entry-wise td of row i and of
+ *         column j; td_col itself does not depend on the row.)
+ *   TD:   columns by their own td(i,j) descending; k = f(i,j).
+ *   SEQ:  columns in increasing j, each with k = 0, 1, ..., r-1.
+ * td(s,t) = |R_st - (U(x)V)_st| over given entries; f(s,t) = the smallest
+ * l attaining (U(x)V)_st. */
+enum { STMF_SEL_TD_A = 0, STMF_SEL_TD_B = 1, STMF_SEL_TD = 2, STMF_SEL_SEQ = 3 };
+
 /* Options of the factorization (Algorithm 3 and its readings). */
 typedef struct {
     int sweeps;          /* passes over all rows (the loop "while not converged") */
@@ -95,6 +112,10 @@ typedef struct {
                             row median, computed on the device; the network's rank
                             must be r, it must belong to the same context, and the
                             oriented n must be <= 12288.  U0, if given, wins.      */
+    int selection;       /* STMF_SEL_*: how a row picks its (j, k) pairs; 0 = TD_A.
+                            TD keeps a per-row column order (three extra launches
+                            per row); TD_B a per-column argmax (one extra launch
+                            per refresh).                                          */
 } stmf_options;
 
 /* A trace record: sweep, row (oriented, permuted index), position of the kept

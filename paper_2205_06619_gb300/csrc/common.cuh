@@ -48,6 +48,17 @@ __device__ __forceinline__ stmf_ff ff_add(stmf_ff a, stmf_ff b)
     return {h, e - (h - s)};
 }
 
+// Argmax key of the TD_B / TD selections: the largest td first, then the
+// smaller index.  td >= 0, so its float bits order like its value.
+__device__ __forceinline__ unsigned long long td_argmax_key(float td, int idx)
+{
+    return ((unsigned long long)__float_as_uint(td) << 32) | (unsigned)(0xffffffffu - (unsigned)idx);
+}
+__device__ __forceinline__ int td_argmax_index(unsigned long long key)
+{
+    return (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+}
+
 struct stmf_ctx {
     int device;
     cudaStream_t stream;
@@ -105,6 +116,7 @@ struct stmf_ctl {
     unsigned scr_mr;   // running max of |R| over given entries (float bits)
     unsigned scr_mp;   // running max of the finite |P1|, |P2| over given entries (float bits)
     long long screened;// candidates the screen proved non-improving (cumulative)
+    int tdb_j0;        // TD_B: column of the largest td(i, t) of the current row
 };
 
 struct stmf_problem {
@@ -122,6 +134,13 @@ struct stmf_problem {
     int *rowhist;      // r
     int *rank;         // np
     int *order;        // np: columns by decreasing td_col, ties to smaller j
+    // selection of (j, k) within a row (STMF_SEL_*); the buffers of the
+    // selections other than TD_A are NULL unless that selection is used
+    int sel;
+    double *rowkey;    // np: TD keys td(i, t) of the current row (0 where not given)
+    int *rowrank;      // np
+    int *roworder;     // np: TD order of the current row (decreasing td(i, t), ties to smaller t)
+    int *colarg;       // np: TD_B i0 of column t: the row of the largest td(s, t), the smaller s on ties
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
@@ -163,6 +182,7 @@ int planes_nparts(int m);
 cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int *chpart, int nparts,
                                 int ldpart, int n, int r, double *tdcol, int *colhist);
 cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_row_order(cudaStream_t st, stmf_problem *P);
 
 // kernels_update.cu
 cudaError_t launch_pack(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm,

@@ -357,7 +357,70 @@ __global__ void __launch_bounds__(1024) k_scatter_f(const double *__restrict__ t
     }
 }
 
+// TD selection (Section "The ByRow strategy"): the key of column t for row
+// i = ctl->i is its tropical distance td(i,t) = |R_it - P1_it| where R_it is
+// given, else 0 (the window skips those columns).  Ranked like the column
+// order: decreasing key, equal keys keep the smaller t first, so the given
+// columns come out in the selection's order.
+__global__ void k_row_keys(const float *__restrict__ R, const float *__restrict__ P1, int np, int n,
+                           const stmf_ctl *__restrict__ ctl, double *__restrict__ key, int *__restrict__ rank)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const size_t e = (size_t)ctl->i * np + t;
+    const float x = R[e];
+    key[t] = x == x ? (double)fabsf(x - P1[e]) : 0.0;
+    rank[t] = 0;
+}
+
+__global__ void k_row_scatter(const int *__restrict__ rank, int n, int *__restrict__ order)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) order[rank[t]] = t;
+}
+
+// TD_B selection (Section "The ByRow strategy"): i0 of every column t, the
+// row of the largest td(s,t) over given s (the smaller s on ties).  A block
+// covers 32 columns; its 32 warps stride over the rows, each warp reading 32
+// consecutive columns of one row.
+__global__ void __launch_bounds__(1024) k_col_tdmax(const float *__restrict__ R, const float *__restrict__ P1,
+                                                    int np, int m, int n, int *__restrict__ colarg)
+{
+    __shared__ unsigned long long red[32][33];
+    const int c = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + c;
+    unsigned long long best = 0ull;
+    if (t < n)
+        for (int s = q; s < m; s += 32) {
+            const size_t e = (size_t)s * np + t;
+            const float x = R[e];
+            if (x == x) {
+                const unsigned long long k = td_argmax_key(fabsf(x - P1[e]), s);
+                best = k > best ? k : best;
+            }
+        }
+    red[q][c] = best;
+    __syncthreads();
+    if (q == 0 && t < n) {
+        for (int z = 1; z < 32; ++z) best = red[z][c] > best ? red[z][c] : best;
+        colarg[t] = best ? td_argmax_index(best) : 0;   // every column has a given entry (checked at set-up)
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_row_order(cudaStream_t st, stmf_problem *P)
+{
+    const int nb = (P->n + 255) / 256;
+    k_row_keys<<<nb, 256, 0, st>>>(P->R, P->P1, P->np, P->n, P->ctl, P->rowkey, P->rowrank);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid((P->n + 255) / 256, (P->n + RANK_CHUNK - 1) / RANK_CHUNK);
+    k_rank<<<grid, 256, 0, st>>>(P->rowkey, P->n, P->rowrank);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_row_scatter<<<nb, 256, 0, st>>>(P->rowrank, P->n, P->roworder);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_maxplus(cudaStream_t st, int m, int n, int r, const float *U, int ldu,
                            const float *V, int ldv, const uint32_t *mask, int ldm,
@@ -397,7 +460,8 @@ cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int
     return cudaGetLastError();
 }
 
-// Product planes, statistics, column order and error of a problem.
+// Product planes, statistics, column order and error of a problem (and, for
+// the TD_B selection, every column's i0).
 cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P)
 {
     cudaError_t e = launch_planes(st, P, P->chpart);
@@ -409,5 +473,7 @@ cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P)
     k_rank<<<grid, 256, 0, st>>>(P->tdcol, P->n, P->rank);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scatter_f<<<1, 1024, 0, st>>>(P->tdcol, P->rank, P->n, P->order, P->ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (P->sel == STMF_SEL_TD_B) k_col_tdmax<<<(P->n + 31) / 32, 1024, 0, st>>>(P->R, P->P1, P->np, P->m, P->n, P->colarg);
     return cudaGetLastError();
 }

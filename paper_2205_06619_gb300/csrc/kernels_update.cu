@@ -249,31 +249,62 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
     for (int w = threadIdx.x; w < CTL_WORDS; w += blockDim.x) d[w] = s[w];
 }
 
-// Window of candidates (Algorithm 3): the next wj columns j of the order with
-// R_ij given; k_j = argmax_l (rowhist_i[l] + colhist[j][l]) (TD_A; the multiset
-// union adds multiplicities; smaller l on ties).  Each j gives F-ULF (slot 2a)
-// then F-URF (slot 2a+1), the order in which Algorithm 3 tries them.  At the
-// first window of a row the row histogram is rebuilt.  Runs in a block of
-// 1024 threads: at the start of a row (k_row_begin) and after a window that
-// neither kept a candidate nor exhausted the row (k_select).
+// Window of candidates (Algorithm 3; selections of Section "The ByRow
+// strategy"): the next wj pairs (j, k) of the row's order with R_ij given.
+//   TD_A: j along the column order (td_col descending); k_j = argmax_l
+//         (rowhist_i[l] + colhist[j][l]) (the multiset union adds
+//         multiplicities; smaller l on ties);
+//   TD_B: j as TD_A; k_j = A[i][j0] if P1[i][j0] >= P1[i0][j] else A[i0][j],
+//         j0 the row's largest td (found at the row's first window), i0 the
+//         column's (from the refresh);
+//   TD:   j along the row's own order (td(i, j) descending); k_j = A[i][j];
+//   SEQ:  position q = j r + k, j increasing, then k.
+// Each pair gives F-ULF (slot 2a) then F-URF (slot 2a+1), the order in which
+// Algorithm 3 tries them.  At the first window of a row the row histogram
+// (and TD_B's j0) is rebuilt.  Runs in a block of 1024 threads: at the start
+// of a row (k_row_begin) and after a window that neither kept a candidate
+// nor exhausted the row (k_select).
 __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ctl, bool row_start)
 {
     __shared__ int sh[STMF_MAX_RANK];
     __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2];
     __shared__ int scount, spos;
-    const int i = ctl->i, tid = threadIdx.x, r = P.r;
+    __shared__ unsigned long long sj0;
+    const int i = ctl->i, tid = threadIdx.x, r = P.r, sel = P.sel;
     const float *Ri = P.R + (size_t)i * P.np;
+    const int lim = sel == STMF_SEL_SEQ ? P.n * r : P.n;    // positions of the row's order
     if (row_start) {
         if (tid < r) sh[tid] = 0;
+        if (tid == 0) sj0 = 0ull;
         __syncthreads();
         const uint8_t *Ai = P.A + (size_t)i * P.np;
+        const float *P1i = P.P1 + (size_t)i * P.np;
+        unsigned long long best = 0ull;
         for (int t = tid; t < P.n; t += 1024)
-            if (Ri[t] == Ri[t]) atomicAdd(&sh[Ai[t]], 1);
+            if (Ri[t] == Ri[t]) {
+                atomicAdd(&sh[Ai[t]], 1);
+                if (sel == STMF_SEL_TD_B) {
+                    const unsigned long long key = td_argmax_key(fabsf(Ri[t] - P1i[t]), t);
+                    best = key > best ? key : best;
+                }
+            }
+        if (sel == STMF_SEL_TD_B) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(FULL, best, o);
+                best = ob > best ? ob : best;
+            }
+            if ((tid & 31) == 0 && best) atomicMax(&sj0, best);
+        }
         __syncthreads();
         if (tid < r) P.rowhist[tid] = sh[tid];
-        if (tid == 0) { ctl->pos = 0; ctl->ncand_row = 0; }
+        if (tid == 0) {
+            ctl->pos = 0;
+            ctl->ncand_row = 0;
+            ctl->tdb_j0 = sj0 ? td_argmax_index(sj0) : 0;    // every row has a given entry (checked at set-up)
+        }
         __syncthreads();
-    } else {
+    } else if (sel == STMF_SEL_TD_A) {
         if (tid < r) sh[tid] = P.rowhist[tid];
         __syncthreads();
     }
@@ -281,13 +312,18 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         const int want = min(ctl->wj, ctl->wmax / 2);
         int pos = ctl->pos, have = 0;
         const int lane = tid;
-        while (have < want && pos < P.n) {
+        const int *ord = sel == STMF_SEL_TD ? P.roworder : P.order;
+        while (have < want && pos < lim) {
             const int q = pos + lane;
-            const int j = q < P.n ? P.order[q] : 0;
-            const bool ok = q < P.n && Ri[j] == Ri[j];
+            int j = 0, k = 0;
+            if (q < lim) {
+                if (sel == STMF_SEL_SEQ) { j = q / r; k = q - j * r; }
+                else j = ord[q];
+            }
+            const bool ok = q < lim && Ri[j] == Ri[j];
             const unsigned b = __ballot_sync(FULL, ok);
             const int rank = __popc(b & ((1u << lane) - 1u));
-            if (ok && have + rank < want) sj[have + rank] = j;
+            if (ok && have + rank < want) { sj[have + rank] = j; sk[have + rank] = k; }
             const int take = min(__popc(b), want - have);
             if (take < __popc(b)) {
                 unsigned bb = b;          // stop at the first given entry not taken
@@ -298,11 +334,11 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
             }
             have += take;
         }
-        if (lane == 0) { scount = have; spos = min(pos, P.n); }
+        if (lane == 0) { scount = have; spos = min(pos, lim); }
     }
     __syncthreads();
     const int cnt = scount;
-    {
+    if (sel == STMF_SEL_TD_A) {
         // warp a takes column a of the window; lane l loads component l's
         // count, and the warp keeps the largest (the smaller l on ties)
         const int a = tid >> 5, l = tid & 31;
@@ -315,17 +351,26 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
                 const int oc = __shfl_xor_sync(FULL, c, o), ol = __shfl_xor_sync(FULL, bl, o);
                 if (oc > c || (oc == c && ol < bl)) { c = oc; bl = ol; }
             }
-            if (l == 0) {
-                sk[a] = bl;
-                const int base = ctl->ncand_row / 2;
-                int *c0 = P.cand + 8 * (2 * a);
-                c0[0] = j; c0[1] = bl; c0[2] = 0; c0[3] = base + a; c0[4] = 0;
-                int *c1 = P.cand + 8 * (2 * a + 1);
-                c1[0] = j; c1[1] = bl; c1[2] = 1; c1[3] = base + a; c1[4] = 0;
-            }
+            if (l == 0) sk[a] = bl;
+        }
+    } else if (sel != STMF_SEL_SEQ && tid < cnt) {
+        const int j = sj[tid];
+        if (sel == STMF_SEL_TD) {
+            sk[tid] = P.A[(size_t)i * P.np + j];
+        } else {
+            const int j0 = ctl->tdb_j0, i0 = P.colarg[j];
+            const size_t e0 = (size_t)i * P.np + j0, e1 = (size_t)i0 * P.np + j;
+            sk[tid] = P.P1[e0] >= P.P1[e1] ? P.A[e0] : P.A[e1];
         }
     }
     __syncthreads();
+    if (tid < cnt) {
+        const int base = ctl->ncand_row / 2;
+        int *c0 = P.cand + 8 * (2 * tid);
+        c0[0] = sj[tid]; c0[1] = sk[tid]; c0[2] = 0; c0[3] = base + tid; c0[4] = 0;
+        int *c1 = P.cand + 8 * (2 * tid + 1);
+        c1[0] = sj[tid]; c1[1] = sk[tid]; c1[2] = 1; c1[3] = base + tid; c1[4] = 0;
+    }
     if (tid == 0) {
         // evaluation lists grouped by k (stable), so the evaluation recomputes
         // E = max over l != k only when k changes; the slots keep the paper's order
@@ -345,7 +390,7 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         ctl->na = 2 * cnt;
         ctl->nu = cnt;
         ctl->nv = cnt;
-        ctl->exhausted = spos >= P.n;
+        ctl->exhausted = spos >= lim;
         ctl->pos = spos;
     }
 }
@@ -742,6 +787,10 @@ cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P)
 
 cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph)
 {
+    if (P->sel == STMF_SEL_TD) {
+        const cudaError_t e = launch_row_order(st, P);     // the row's own column order
+        if (e != cudaSuccess) return e;
+    }
     k_row_begin<<<1, 1024, 0, st>>>(*P, in_graph, P->h_win);
     return cudaGetLastError();
 }

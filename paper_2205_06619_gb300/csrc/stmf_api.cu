@@ -116,7 +116,7 @@ void problem_free(stmf_problem *P)
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
                     P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
-                    P->scr_umax, P->scr_vmax};
+                    P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
@@ -450,6 +450,8 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (o.precision < 0 || o.precision > 1) return fail(ctx, STMF_ERR_INVALID, "precision mode %d unknown", o.precision);
     if (o.select < 0 || o.select > 1) return fail(ctx, STMF_ERR_INVALID, "select mode %d unknown", o.select);
     if (o.V0 && !o.U0) return fail(ctx, STMF_ERR_INVALID, "V0 needs U0");
+    if (o.selection < STMF_SEL_TD_A || o.selection > STMF_SEL_SEQ)
+        return fail(ctx, STMF_ERR_INVALID, "selection %d unknown", o.selection);
     const int tr = m0 > n0;                 // Algorithm 3: a tall R is transposed
     const int m = tr ? n0 : m0, n = tr ? m0 : n0;
     std::vector<int> perm;
@@ -468,6 +470,22 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     s = problem_alloc(ctx, m, n, r, window, &P);
     if (s != STMF_OK) return s;
     P->transposed = tr; P->m0 = m0; P->n0 = n0;
+    P->sel = o.selection;
+    {
+        cudaError_t ea = cudaSuccess;
+        if (P->sel == STMF_SEL_TD) {
+            ea = dalloc(&P->rowkey, P->np);
+            if (ea == cudaSuccess) ea = dalloc(&P->rowrank, P->np);
+            if (ea == cudaSuccess) ea = dalloc(&P->roworder, P->np);
+        } else if (P->sel == STMF_SEL_TD_B) {
+            ea = dalloc(&P->colarg, P->np);
+        }
+        if (ea != cudaSuccess) {
+            problem_free(P);
+            cudaGetLastError();
+            return fail(ctx, STMF_ERR_OOM, "selection buffers: %s", cudaGetErrorString(ea));
+        }
+    }
     cudaStream_t st = ctx->stream;
     if (o.precision == 1) {
         // half planes and screen partials; the planes are written by every

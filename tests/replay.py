@@ -12,7 +12,7 @@ FP32 mode reproduces the GPU's factors bit for bit) and continues.
 import oracle as orc
 
 
-def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=None):
+def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=None, selection="TD_A"):
     st = orc.prepare(R, M, r, perm=perm, picks=picks, p=p, seed=seed, U0=U0)
     Ri, Mi, Ui, Vi = st["R"], st["M"], st["U"], st["V"]
     f = orc.error(Ri, Mi, Ui, Vi)
@@ -20,7 +20,7 @@ def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=
     for rec in gpu_trace:
         sweep, i, pos, j, k, typ, f_gpu = rec
         U0_, V0_ = Ui.copy(), Vi.copy()
-        kept, fn, out, _ = orc.row_step(Ri, Mi, Ui, Vi, i, f)
+        kept, fn, out, _ = orc.row_step(Ri, Mi, Ui, Vi, i, f, selection=selection)
         gpu_kept = pos >= 0
         same = (kept == gpu_kept) and (not kept or tuple(out) == (pos, j, k, typ))
         if same:

@@ -54,6 +54,21 @@ def test_struct_layouts_match_the_library():
                                         ctypes.sizeof(api.BatchProblem)]
 
 
+def test_selection_names_match_the_header():
+    """The binding's selection names carry the values of stmf.h's STMF_SEL_*
+    (Section "The ByRow strategy"), the default is TD_A, and unknown names are
+    refused before any call."""
+    from paper_2205_06619_gb300 import api
+    text = open(os.path.join(ROOT, "include", "stmf.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"STMF_SEL_([A-Z_]+)\s*=\s*(\d+)", text))
+    assert enum == api.SELECTIONS
+    o = api.Options()
+    api.load().stmf_default_options(ctypes.byref(o))
+    assert o.selection == api.SELECTIONS["TD_A"]
+    with pytest.raises(ValueError):
+        api._selection("BEST")
+
+
 def test_invalid_arguments_fail_without_launch():
     """A NULL context and bad sizes are rejected on the host (no GPU needed)."""
     from paper_2205_06619_gb300 import api
