@@ -81,6 +81,11 @@ def lib():
         L.orc_factorize.argtypes = [i, i, i, i, P, P, i, d, P, P, i, u64, P, P, P, P, P, i64, P]
         L.orc_factorize_sel.restype = i
         L.orc_factorize_sel.argtypes = [i, i, i, i, i, P, P, i, d, P, P, i, u64, P, P, P, P, P, i64, P]
+        L.orc_colmin_perm.argtypes = [i, i, P, P, P]
+        L.orc_element_scan.restype = i
+        L.orc_element_scan.argtypes = [i, i, i, i, P, P, P, P, i, P, P, P]
+        L.orc_factorize_byelement.restype = i
+        L.orc_factorize_byelement.argtypes = [i, i, i, i, P, P, i, d, P, i, u64, P, P, P, P, P, i64, P]
         _lib = L
     return _lib
 
@@ -254,11 +259,65 @@ def finish(m0, n0, transposed, Ui, Vi, perm):
     return U, V
 
 
+def colmin_perm(R, M):
+    """PermC: columns by increasing minimum of their given entries (stable)."""
+    R, M = _d(R), _m(M)
+    m, n = R.shape
+    cp = np.empty(n, np.int32)
+    lib().orc_colmin_perm(m, n, _p(R), _p(M), _p(cp))
+    return cp
+
+
+def element_scan(R, M, U, V, q0, f, mode="fp32"):
+    """The ByElement scan from element position q0, in place on U, V.
+
+    Returns (q or -1, f_new, (i, j, k, type), tried)."""
+    R, M = _d(R), _m(M)
+    assert U.dtype == np.float64 and V.dtype == np.float64 and U.flags.c_contiguous and V.flags.c_contiguous
+    m, n = R.shape
+    r = U.shape[1]
+    fb = C.c_double(f)
+    out = np.full(5, -1, np.int32)
+    tried = C.c_int64(0)
+    q = lib().orc_element_scan(_mode(mode), m, n, r, _p(R), _p(M), _p(U), _p(V), q0, C.byref(fb), _p(out),
+                               C.byref(tried))
+    return int(q), fb.value, tuple(int(x) for x in out[1:]), tried.value
+
+
+def _factorize_byelement(R0, M0, r, sweeps, eps, picks, p, seed, U0, mode, trace_cap):
+    m0, n0 = R0.shape
+    U = np.empty((m0, r)); V = np.empty((r, n0))
+    f_hist = np.full(sweeps + 1, np.nan)
+    trace = np.empty((max(trace_cap, 1), 6), np.int32)
+    counters = np.zeros(4, np.int64)
+    empty = lib().orc_factorize_byelement(_mode(mode), m0, n0, r, _p(R0), _p(M0), sweeps, eps, _p(picks), p,
+                                          seed, _p(U0), _p(U), _p(V), _p(f_hist),
+                                          _p(trace) if trace_cap else None, trace_cap, _p(counters))
+    if empty:
+        raise ValueError("oracle: %d rows/columns without a given entry" % empty)
+    done = int(counters[0])
+    return dict(U=U, V=V, f_hist=f_hist[:done + 1], sweeps=done, tried=int(counters[1]),
+                kept=int(counters[2]), trace=trace[:int(counters[3])].copy() if trace_cap else None)
+
+
 def factorize(R0, M0, r, sweeps, eps=0.0, perm=None, picks=None, p=5, seed=0, U0=None,
-              mode="fp32", trace_cap=0, selection="TD_A"):
+              mode="fp32", trace_cap=0, selection="TD_A", strategy="ByRow"):
     """FastSTMF (Algorithm 3) with the row's selection of (j, k) (TD_A as
-    published; TD_B, TD, SEQ of Section "The ByRow strategy").
+    published; TD_B, TD, SEQ of Section "The ByRow strategy"), or, with
+    strategy="ByElement", STMF_ByElement_PermC_TD_W (Section "The ByElement
+    strategy"; perm and selection do not apply, U0 is in the frame of the
+    oriented, column-permuted matrix).
     Returns dict(U, V, f_hist, sweeps, tried, kept, trace)."""
+    if strategy not in ("ByRow", "ByElement"):
+        raise ValueError("strategy must be ByRow or ByElement")
+    if strategy == "ByElement":
+        if perm is not None or selection != "TD_A":
+            raise ValueError("ByElement takes no row permutation and no selection")
+        R0, M0 = _d(R0), _m(M0)
+        p = min(p, max(R0.shape))
+        picks = None if picks is None else np.ascontiguousarray(picks, np.int32)
+        U0 = None if U0 is None else _d(U0)
+        return _factorize_byelement(R0, M0, r, sweeps, eps, picks, p, seed, U0, mode, trace_cap)
     R0, M0 = _d(R0), _m(M0)
     m0, n0 = R0.shape
     p = min(p, max(m0, n0))  # the oriented matrix is wide: n = max(m0, n0)

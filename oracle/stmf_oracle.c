@@ -559,3 +559,161 @@ int orc_factorize(int mode, int m0, int n0, int r, const double *R0, const uint8
     return orc_factorize_sel(mode, ORC_SEL_TD_A, m0, n0, r, R0, M0, sweeps, eps, perm_in, picks_in, p, seed,
                              U0, U_out, V_out, f_hist, trace, trace_cap, counters);
 }
+
+/* ------------------------------------------------------------------------
+ * STMF_ByElement_PermC_TD_W (Section "The ByElement strategy"; its
+ * pseudocode in the Supplement).
+ * ---------------------------------------------------------------------- */
+
+/* PermC (Section "Comparison of strategies"): the columns in increasing order
+ * of their minimum value.  Reading: the minimum runs over given entries, and
+ * equal minima keep the smaller column first (a stable sort of 0..n-1).     */
+void orc_colmin_perm(int m, int n, const double *R, const uint8_t *M, int32_t *cperm)
+{
+    double *mn = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int t = 0; t < n; ++t) {
+        mn[t] = INFINITY;
+        for (int s = 0; s < m; ++s)
+            if (M[(size_t)s * n + t] && R[(size_t)s * n + t] < mn[t]) mn[t] = R[(size_t)s * n + t];
+        cperm[t] = t;
+    }
+    for (int a = 1; a < n; ++a) {                  /* stable insertion sort, ascending */
+        int32_t x = cperm[a];
+        int b = a - 1;
+        while (b >= 0 && mn[cperm[b]] > mn[x]) { cperm[b + 1] = cperm[b]; --b; }
+        cperm[b + 1] = x;
+    }
+    free(mn);
+}
+
+/* The ByElement scan from element position q0 = i*n + j (row-major): every
+ * element with R_ij given and err = td(i,j) > 0 on the current state is tried
+ * once, with k = f(i,j): F-ULF; if the error decreased keep it, else revert
+ * and try F-URF; if that decreased keep it, else revert.  Elements with
+ * err = 0 are skipped.  Returns at the first kept update, with *f the new
+ * error and out = {q, i, j, k, type}; returns -1 (state and *f unchanged) when
+ * the scan reaches the end of the matrix.  *tried counts the candidates.     */
+int orc_element_scan(int mode, int m, int n, int r, const double *R, const uint8_t *M,
+                     double *U, double *V, int q0, double *f, int32_t *out, int64_t *tried)
+{
+    double *ucol = (double *)malloc(sizeof(double) * (size_t)m);
+    double *vrow = (double *)malloc(sizeof(double) * (size_t)n);
+    int found = -1;
+    for (int q = q0; q < m * n && found < 0; ++q) {
+        const int i = q / n, j = q % n;
+        if (!M[q]) continue;
+        double best = -INFINITY;
+        int k = 0;
+        for (int l = 0; l < r; ++l) {              /* f(i,j): the smaller l on ties */
+            double x = add_(mode, U[(size_t)i * r + l], V[(size_t)l * n + j]);
+            if (x > best) { best = x; k = l; }
+        }
+        if (fabs(sub_(mode, R[q], best)) == 0.0) continue;   /* err = 0: skipped */
+        for (int type = 0; type < 2; ++type) {
+            get_col(m, r, U, k, ucol);
+            memcpy(vrow, V + (size_t)k * n, sizeof(double) * (size_t)n);
+            double fn = type == 0 ? orc_fulf(mode, m, n, r, R, M, U, V, i, j, k)
+                                  : orc_furf(mode, m, n, r, R, M, U, V, i, j, k);
+            if (tried) *tried += 1;
+            if (fn < *f) {
+                *f = fn;
+                out[0] = q; out[1] = i; out[2] = j; out[3] = k; out[4] = type;
+                found = q;
+                break;
+            }
+            set_col(m, r, U, k, ucol);
+            memcpy(V + (size_t)k * n, vrow, sizeof(double) * (size_t)n);
+        }
+    }
+    free(ucol); free(vrow);
+    return found;
+}
+
+/* The whole ByElement method.  If R is not wide it is transposed (square
+ * counts as wide); its columns are then ordered by PermC and its rows keep
+ * their order; U is initialised (Random Acol over the permuted columns, or
+ * the caller's U0 in that frame) and V = (-U)^T (x)* R.  Each sweep scans all
+ * elements once (orc_element_scan from position 0, then from just after
+ * each kept update); the loop stops after `sweeps` sweeps, or earlier when
+ * eps > 0 and a sweep changed the error by less than eps.  The output undoes
+ * the column order and the transpose.  trace (nullable, 6 int32 per record):
+ * {sweep, i, q, j, k, type} per kept update and {sweep, -1, -1, -1, -1, -1}
+ * at the end of each sweep.  counters as orc_factorize.  Returns the number of
+ * empty rows + columns (0 on success).                                      */
+int orc_factorize_byelement(int mode, int m0, int n0, int r, const double *R0, const uint8_t *M0,
+                            int sweeps, double eps, const int32_t *picks_in, int p, uint64_t seed,
+                            const double *U0, double *U_out, double *V_out, double *f_hist,
+                            int32_t *trace, int64_t trace_cap, int64_t *counters)
+{
+    const int tr = m0 > n0;
+    const int m = tr ? n0 : m0, n = tr ? m0 : n0;
+    double *Ro = (double *)malloc(sizeof(double) * (size_t)m * n);
+    uint8_t *Mo = (uint8_t *)malloc((size_t)m * n);
+    for (int s = 0; s < m; ++s)
+        for (int t = 0; t < n; ++t) {
+            size_t src = tr ? (size_t)t * n0 + s : (size_t)s * n0 + t;
+            Ro[(size_t)s * n + t] = R0[src];
+            Mo[(size_t)s * n + t] = M0[src];
+        }
+    int32_t *cperm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    orc_colmin_perm(m, n, Ro, Mo, cperm);
+    double *Rc = (double *)malloc(sizeof(double) * (size_t)m * n);
+    uint8_t *Mc = (uint8_t *)malloc((size_t)m * n);
+    for (int s = 0; s < m; ++s)
+        for (int t = 0; t < n; ++t) {
+            Rc[(size_t)s * n + t] = Ro[(size_t)s * n + cperm[t]];
+            Mc[(size_t)s * n + t] = Mo[(size_t)s * n + cperm[t]];
+        }
+    double *Ri = (double *)malloc(sizeof(double) * (size_t)m * n);
+    uint8_t *Mi = (uint8_t *)malloc((size_t)m * n);
+    double *Ui = (double *)malloc(sizeof(double) * (size_t)m * r);
+    double *Vi = (double *)malloc(sizeof(double) * (size_t)r * n);
+    int32_t *ident = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    int32_t *perm_out = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    for (int s = 0; s < m; ++s) ident[s] = s;
+    int wide_again = 0;
+    int empty = orc_prepare(mode, m, n, r, Rc, Mc, ident, picks_in, p, seed, U0, Ri, Mi, Ui, Vi, perm_out,
+                            &wide_again);
+    int64_t tried = 0, kept = 0, nrec = 0;
+    int done = 0;
+    if (empty == 0) {
+        double f = orc_error(mode, m, n, r, Ri, Mi, Ui, Vi);
+        if (f_hist) f_hist[0] = f;
+        for (int sw = 0; sw < sweeps; ++sw) {
+            double f_prev = f;
+            int q = 0;
+            for (;;) {
+                int32_t out[5];
+                int got = orc_element_scan(mode, m, n, r, Ri, Mi, Ui, Vi, q, &f, out, &tried);
+                int32_t rec[6] = {sw, -1, -1, -1, -1, -1};
+                if (got >= 0) {
+                    ++kept;
+                    rec[1] = out[1]; rec[2] = out[0]; rec[3] = out[2]; rec[4] = out[3]; rec[5] = out[4];
+                }
+                if (trace && nrec < trace_cap) memcpy(trace + 6 * nrec, rec, sizeof(rec));
+                ++nrec;
+                if (got < 0) break;
+                q = got + 1;
+            }
+            ++done;
+            if (f_hist) f_hist[sw + 1] = f;
+            if (eps > 0.0 && fabs(f_prev - f) < eps) break;
+        }
+        /* undo the column order, then the transpose */
+        if (!tr) {
+            memcpy(U_out, Ui, sizeof(double) * (size_t)m * r);
+            for (int l = 0; l < r; ++l)
+                for (int t = 0; t < n; ++t) V_out[(size_t)l * n + cperm[t]] = Vi[(size_t)l * n + t];
+        } else {
+            for (int t = 0; t < n; ++t)
+                for (int l = 0; l < r; ++l) U_out[(size_t)cperm[t] * r + l] = Vi[(size_t)l * n + t];
+            for (int s = 0; s < m; ++s)
+                for (int l = 0; l < r; ++l) V_out[(size_t)l * n0 + s] = Ui[(size_t)s * r + l];
+        }
+    }
+    if (trace_cap < nrec) nrec = trace_cap;
+    if (counters) { counters[0] = done; counters[1] = tried; counters[2] = kept; counters[3] = nrec; }
+    free(Ro); free(Mo); free(cperm); free(Rc); free(Mc); free(Ri); free(Mi); free(Ui); free(Vi);
+    free(ident); free(perm_out);
+    return empty;
+}
