@@ -313,9 +313,10 @@ def run_precision(args):
 
 def run_selection(args):
     """The four selections of (j, k) within a row (Section "The ByRow
-    strategy": TD_A as published, TD_B, TD, SEQ) on the gene-expression
-    workload: sweeps/s over sweeps W..W+K-1 of one run each (CUDA events on
-    the library's stream), with the error reached and the candidates tried.
+    strategy": TD_A as published, TD_B, TD, SEQ) and the ByElement strategy
+    (STMF_ByElement_PermC_TD_W) on the gene-expression workload: sweeps/s over
+    sweeps W..W+K-1 of one run each (CUDA events on the library's stream),
+    with the error reached and the candidates tried.
     CPU leg: the oracle computing the same row's (j, k) order for each
     selection from the library's final state."""
     import torch
@@ -325,9 +326,11 @@ def run_selection(args):
     Rg, Mw = torch.from_numpy(R_np).cuda(), api.pack_mask(M_np)
     stream = api.context().stream
     res, last = {}, None
+    runs = [("TD_A", dict(selection="TD_A")), ("TD_B", dict(selection="TD_B")), ("TD", dict(selection="TD")),
+            ("SEQ", dict(selection="SEQ")), ("ByElement", dict(strategy="ByElement"))]
     with ClockSampler(0) as clocks:
-        for sel in ("TD_A", "TD_B", "TD", "SEQ"):
-            fz = api.Factorization(Rg, Mw, rank=r, seed=args.seed, selection=sel)
+        for sel, kw in runs:
+            fz = api.Factorization(Rg, Mw, rank=r, seed=args.seed, **kw)
             fz.run(args.warmup)
             rep0 = fz.run(0)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -363,7 +366,8 @@ def run_selection(args):
             "warmup": args.warmup, "ms_per_step": 1e3 / a_["sweeps_per_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "selection: gene-expression 1000x5000 rank-10, 80% given, each selection of "
-                                   "(j, k) from the same Random Acol start",
+                                   "(j, k) of ByRow from the same Random Acol start, and ByElement (its PermC "
+                                   "column order changes the Acol start)",
                        "step": "one ByRow sweep (sweeps W..W+K-1 of each run)", "l2": "not flushed"},
             "selections": res, "clocks": clocks.summary(), "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)

@@ -76,6 +76,25 @@ typedef struct stmf_mlp stmf_mlp;         /* learned-initialisation network  */
  * l attaining (U(x)V)_st. */
 enum { STMF_SEL_TD_A = 0, STMF_SEL_TD_B = 1, STMF_SEL_TD = 2, STMF_SEL_SEQ = 3 };
 
+/* Update strategies (Section "The ByElement strategy", Section "The ByRow
+ * strategy").
+ *   BYROW:     Algorithm 3 (FastSTMF): rows in a random order, one kept
+ *              update per row at most, (j, k) by `selection`.
+ *   BYELEMENT: STMF_ByElement_PermC_TD_W (the Supplement's pseudocode): R
+ *              oriented wide, its columns in increasing order of their
+ *              minimum given entry (equal minima: smaller column first), rows
+ *              in their own order.  A sweep visits every element (i, j) in
+ *              row-major order; an element with R_ij given and
+ *              td(i,j) = |R_ij - (U(x)V)_ij| > 0 is tried once with
+ *              k = f(i,j): F-ULF, else F-URF, keeping the first that lowers
+ *              the error; the scan goes on from the next element.  Needs
+ *              perm = NULL and selection = TD_A; U0 / V0 are in the frame of
+ *              the oriented, column-permuted matrix.  Trace: one record per
+ *              kept update {sweep, i, q = i*n + j, j, k, type, f} (oriented,
+ *              permuted frame) and one {sweep, -1, -1, -1, -1, -1, f} at the
+ *              end of each sweep. */
+enum { STMF_STRATEGY_BYROW = 0, STMF_STRATEGY_BYELEMENT = 1 };
+
 /* Options of the factorization (Algorithm 3 and its readings). */
 typedef struct {
     int sweeps;          /* passes over all rows (the loop "while not converged") */
@@ -116,6 +135,7 @@ typedef struct {
                             TD keeps a per-row column order (three extra launches
                             per row); TD_B a per-column argmax (one extra launch
                             per refresh).                                          */
+    int strategy;        /* STMF_STRATEGY_*: 0 = ByRow (Algorithm 3), 1 = ByElement   */
 } stmf_options;
 
 /* A trace record: sweep, row (oriented, permuted index), position of the kept

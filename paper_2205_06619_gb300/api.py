@@ -41,11 +41,21 @@ class Options(C.Structure):
                 ("precision", C.c_int), ("acol_p", C.c_int), ("seed", C.c_uint64),
                 ("perm", C.c_void_p), ("picks", C.c_void_p), ("U0", C.c_void_p),
                 ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("V0", C.c_void_p), ("mlp", C.c_void_p),
-                ("selection", C.c_int)]
+                ("selection", C.c_int), ("strategy", C.c_int)]
 
 
 # selections of (j, k) within a row (Section "The ByRow strategy"; stmf.h STMF_SEL_*)
 SELECTIONS = {"TD_A": 0, "TD_B": 1, "TD": 2, "SEQ": 3}
+
+
+# update strategies (stmf.h STMF_STRATEGY_*): Algorithm 3, and the ByElement method
+STRATEGIES = {"ByRow": 0, "ByElement": 1}
+
+
+def _strategy(name):
+    if name not in STRATEGIES:
+        raise ValueError("strategy must be one of %s" % sorted(STRATEGIES))
+    return STRATEGIES[name]
 
 
 def _selection(name):
@@ -270,12 +280,13 @@ def selection_stats_noalloc(R, U, V, mask_words=None, td_col=None, colhist=None)
 
 
 def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=0, perm=None, picks=None,
-             U0=None, trace=None, mlp=None, V0=None, selection="TD_A"):
+             U0=None, trace=None, mlp=None, V0=None, selection="TD_A", strategy="ByRow"):
     o = Options()
     load().stmf_default_options(C.byref(o))
     o.sweeps, o.eps, o.window, o.select, o.precision, o.acol_p, o.seed = (
         sweeps, eps, window, select, precision, acol_p, seed)
     o.selection = _selection(selection)
+    o.strategy = _strategy(strategy)
     keep = []
     if perm is not None:
         a = np.ascontiguousarray(perm, dtype=np.int32); keep.append(a); o.perm = a.ctypes.data
@@ -369,11 +380,13 @@ def sweep_log(trace):
 
 
 def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5,
-              seed=0, perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None, selection="TD_A"):
+              seed=0, perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None, selection="TD_A",
+              strategy="ByRow"):
     """FastSTMF (Algorithm 3) on the device.  R: float32 CUDA (m x n).
     mlp: an MLP (learned initialisation on the device) or None (Random Acol).
     selection: "TD_A" (the method as published), "TD_B", "TD" or "SEQ"
-    (Section "The ByRow strategy").
+    (Section "The ByRow strategy").  strategy: "ByRow" (Algorithm 3) or
+    "ByElement" (STMF_ByElement_PermC_TD_W; trace records per kept update).
 
     Returns (U m x r, V r x n, report dict, trace list or None)."""
     torch = _torch()
@@ -382,7 +395,7 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     ctx = context()
     trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
     o, keep = _options(sweeps, eps, window, select, precision, acol_p, seed, perm, picks, U0, trace, mlp, V0,
-                       selection)
+                       selection, strategy)
     U = torch.empty((m, rank), device=R.device, dtype=torch.float32)
     V = torch.empty((rank, n), device=R.device, dtype=torch.float32)
     rep = Report()
@@ -395,7 +408,8 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     return U, V, rep.as_dict(), tr
 
 
-def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0, mlp=None, selection="TD_A"):
+def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0, mlp=None, selection="TD_A",
+                      strategy="ByRow"):
     """Many independent problems in one device launch (stmf_factorize_batched).
 
     problems: list of dicts with R (float32 CUDA m x n), mask_words (or None),
@@ -418,7 +432,7 @@ def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0, mlp=No
                               0 if mw is None else mw.shape[1], U.data_ptr(), V.data_ptr(), pr.get("seed", 0),
                               pr.get("sweeps", 1))
         outs.append((U, V))
-    o, keep = _options(0, eps, window, select, precision, mlp=mlp, selection=selection)
+    o, keep = _options(0, eps, window, select, precision, mlp=mlp, selection=selection, strategy=strategy)
     reps = (Report * max(n, 1))()
     tuned = (C.c_int * max(n, 1))()
     ctx.check(load().stmf_factorize_batched(ctx.h, n, arr, C.byref(o), reps, tuned))
@@ -497,13 +511,14 @@ class Factorization:
     orientation; ``report`` holds the cumulative counters."""
 
     def __init__(self, R, mask_words=None, rank=3, window=0, select=0, precision=0, acol_p=5, seed=0,
-                 perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None, selection="TD_A"):
+                 perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None, selection="TD_A",
+                 strategy="ByRow"):
         _check_f32(R, "R")
         self.ctx = context()
         self.m, self.n, self.r = R.shape[0], R.shape[1], rank
         self.trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
         o, self._keep = _options(0, 0.0, window, select, precision, acol_p, seed, perm, picks, U0, self.trace,
-                                 mlp, V0, selection)
+                                 mlp, V0, selection, strategy)
         h = C.c_void_p()
         ldm = mask_words.shape[1] if mask_words is not None else 0
         self.ctx.check(load().stmf_factorize_begin(self.ctx.h, self.m, self.n, rank, _ptr(R), R.stride(0),

@@ -117,6 +117,7 @@ struct stmf_ctl {
     unsigned scr_mp;   // running max of the finite |P1|, |P2| over given entries (float bits)
     long long screened;// candidates the screen proved non-improving (cumulative)
     int tdb_j0;        // TD_B: column of the largest td(i, t) of the current row
+    int more;          // the row loop goes on (ByRow: rows left; ByElement: elements left in the sweep)
 };
 
 struct stmf_problem {
@@ -137,6 +138,8 @@ struct stmf_problem {
     // selection of (j, k) within a row (STMF_SEL_*); the buffers of the
     // selections other than TD_A are NULL unless that selection is used
     int sel;
+    int strategy;      // STMF_STRATEGY_*
+    int *cperm;        // ByElement: n, oriented column t <- source column cperm[t] (PermC); NULL otherwise
     double *rowkey;    // np: TD keys td(i, t) of the current row (0 where not given)
     int *rowrank;      // np
     int *roworder;     // np: TD order of the current row (decreasing td(i, t), ties to smaller t)
@@ -188,9 +191,10 @@ cudaError_t launch_row_order(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_pack(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm,
                         int m, int n, float *Rp, int ldp, int mp, int *bad);
 cudaError_t launch_pack_oriented(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm,
-                                 int m, int n, int transposed, const int *perm, float *Rp, int ldp,
-                                 int mp, int *bad);
-cudaError_t launch_unorient(cudaStream_t st, const stmf_problem *P, int transposed, const int *perm,
+                                 int m, int n, int transposed, const int *perm, const int *cperm, float *Rp,
+                                 int ldp, int mp, int *bad);
+cudaError_t launch_col_min(cudaStream_t st, const float *Rp, int ldp, int m, int n, float *cmin);
+cudaError_t launch_unorient(cudaStream_t st, const stmf_problem *P, int transposed, const int *perm, const int *cperm,
                             float *U_out, float *V_out);
 cudaError_t launch_empty_rows(cudaStream_t st, const float *X, int ldx, int rows, int *nempty);
 cudaError_t launch_transpose(cudaStream_t st, const float *X, int ldx, int rows, int cols,

@@ -41,19 +41,21 @@ __global__ void k_pack(const float *__restrict__ R, int ldr, const uint32_t *__r
     Rp[(size_t)s * ldp + t] = v;
 }
 
-// Oriented, permuted copy for Algorithm 3: Rp[s][t] = R0[perm[s]][t], or for a
-// transposed (tall) input Rp[s][t] = R0[t][perm[s]]; NaN where not given.
+// Oriented, permuted copy: Rp[s][t] = R0[perm[s]][c(t)], or for a transposed
+// (tall) input Rp[s][t] = R0[c(t)][perm[s]], with c(t) = cperm[t] (ByElement's
+// PermC) or t (cperm NULL); NaN where not given.
 __global__ void k_pack_oriented(const float *__restrict__ R, int ldr, const uint32_t *__restrict__ mask,
                                 int ldm, int m, int n, int transposed, const int *__restrict__ perm,
-                                float *__restrict__ Rp, int ldp, int mp, int *__restrict__ bad)
+                                const int *__restrict__ cperm, float *__restrict__ Rp, int ldp, int mp,
+                                int *__restrict__ bad)
 {
     const int t = blockIdx.x * 32 + threadIdx.x;
     const int s = blockIdx.y * 8 + threadIdx.y;
     if (s >= mp || t >= ldp) return;
     float v = QNAN;
     if (s < m && t < n) {
-        const int so = perm[s];
-        const int a = transposed ? t : so, b = transposed ? so : t;   // source row, column
+        const int so = perm[s], to = cperm ? cperm[t] : t;
+        const int a = transposed ? to : so, b = transposed ? so : to;   // source row, column
         const bool given = mask ? ((mask[(size_t)a * ldm + (b >> 5)] >> (b & 31)) & 1u) : true;
         if (given) {
             v = R[(size_t)a * ldr + b];
@@ -63,11 +65,12 @@ __global__ void k_pack_oriented(const float *__restrict__ R, int ldr, const uint
     Rp[(size_t)s * ldp + t] = v;
 }
 
-// Undo the permutation and the transpose (end of Algorithm 3):
-//   not transposed: U_out[perm[s], :] = U[s, :],  V_out = V
-//   transposed:     U_out = V^T,                  V_out[:, perm[s]] = U[s, :]^T
+// Undo the permutations and the transpose (end of Algorithm 3; the ByElement
+// pseudocode), with c(t) = cperm[t] or t:
+//   not transposed: U_out[perm[s], :] = U[s, :],  V_out[:, c(t)] = V[:, t]
+//   transposed:     U_out[c(t), :] = V[:, t]^T,   V_out[:, perm[s]] = U[s, :]^T
 __global__ void k_unorient(const float *__restrict__ U, const float *__restrict__ V, int m, int n, int r,
-                           int np, int transposed, const int *__restrict__ perm,
+                           int np, int transposed, const int *__restrict__ perm, const int *__restrict__ cperm,
                            float *__restrict__ U_out, float *__restrict__ V_out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,8 +81,29 @@ __global__ void k_unorient(const float *__restrict__ U, const float *__restrict_
     }
     if (e < r * n) {
         const int l = e / n, t = e % n;
-        if (!transposed) V_out[e] = V[(size_t)l * np + t];
-        else U_out[(size_t)t * r + l] = V[(size_t)l * np + t];
+        const int c = cperm ? cperm[t] : t;
+        if (!transposed) V_out[(size_t)l * n + c] = V[(size_t)l * np + t];
+        else U_out[(size_t)c * r + l] = V[(size_t)l * np + t];
+    }
+}
+
+// PermC keys (ByElement): the minimum given entry of every column of the
+// packed R (NaN where not given, which fminf drops).  A block covers 32
+// columns; its 32 warps stride over the rows.
+__global__ void __launch_bounds__(1024) k_col_min(const float *__restrict__ Rp, int ldp, int m, int n,
+                                                  float *__restrict__ cmin)
+{
+    __shared__ float red[32][33];
+    const int c = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + c;
+    float x = INFINITY;
+    if (t < n)
+        for (int s = q; s < m; s += 32) x = fminf(x, Rp[(size_t)s * ldp + t]);
+    red[q][c] = x;
+    __syncthreads();
+    if (q == 0 && t < n) {
+        for (int z = 1; z < 32; ++z) x = fminf(x, red[z][c]);
+        cmin[t] = x;
     }
 }
 
@@ -259,6 +283,10 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
 //         column's (from the refresh);
 //   TD:   j along the row's own order (td(i, j) descending); k_j = A[i][j];
 //   SEQ:  position q = j r + k, j increasing, then k.
+// With the ByElement strategy the positions are the elements q = i n + j in
+// row-major order, from where the scan stands (not reset per row): an
+// element is a candidate when R_ij is given and td(i,j) > 0, i.e. R_ij !=
+// P1_ij, with k = f(i,j) = A_ij; the window's elements may span rows.
 // Each pair gives F-ULF (slot 2a) then F-URF (slot 2a+1), the order in which
 // Algorithm 3 tries them.  At the first window of a row the row histogram
 // (and TD_B's j0) is rebuilt.  Runs in a block of 1024 threads: at the start
@@ -267,13 +295,18 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
 __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ctl, bool row_start)
 {
     __shared__ int sh[STMF_MAX_RANK];
-    __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2];
+    __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2], si[STMF_WMAX / 2], sq[STMF_WMAX / 2];
     __shared__ int scount, spos;
     __shared__ unsigned long long sj0;
-    const int i = ctl->i, tid = threadIdx.x, r = P.r, sel = P.sel;
+    const bool elem = P.strategy == STMF_STRATEGY_BYELEMENT;
+    const int i = elem ? 0 : ctl->i, tid = threadIdx.x, r = P.r, sel = P.sel;
     const float *Ri = P.R + (size_t)i * P.np;
-    const int lim = sel == STMF_SEL_SEQ ? P.n * r : P.n;    // positions of the row's order
-    if (row_start) {
+    // positions of the row's order (ByElement: of the whole sweep)
+    const int lim = elem ? P.m * P.n : (sel == STMF_SEL_SEQ ? P.n * r : P.n);
+    if (row_start && elem) {
+        if (tid == 0) ctl->ncand_row = 0;
+        __syncthreads();
+    } else if (row_start) {
         if (tid < r) sh[tid] = 0;
         if (tid == 0) sj0 = 0ull;
         __syncthreads();
@@ -315,15 +348,26 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         const int *ord = sel == STMF_SEL_TD ? P.roworder : P.order;
         while (have < want && pos < lim) {
             const int q = pos + lane;
-            int j = 0, k = 0;
+            int j = 0, k = 0, ei = i;
+            bool ok = false;
             if (q < lim) {
-                if (sel == STMF_SEL_SEQ) { j = q / r; k = q - j * r; }
-                else j = ord[q];
+                if (elem) {
+                    ei = q / P.n; j = q - ei * P.n;
+                    const size_t e = (size_t)ei * P.np + j;
+                    const float x = P.R[e];
+                    ok = x == x && x != P.P1[e];         // given, and td(i,j) > 0
+                    k = P.A[e];
+                } else {
+                    if (sel == STMF_SEL_SEQ) { j = q / r; k = q - j * r; }
+                    else j = ord[q];
+                    ok = Ri[j] == Ri[j];
+                }
             }
-            const bool ok = q < lim && Ri[j] == Ri[j];
             const unsigned b = __ballot_sync(FULL, ok);
             const int rank = __popc(b & ((1u << lane) - 1u));
-            if (ok && have + rank < want) { sj[have + rank] = j; sk[have + rank] = k; }
+            if (ok && have + rank < want) {
+                sj[have + rank] = j; sk[have + rank] = k; si[have + rank] = ei; sq[have + rank] = q;
+            }
             const int take = min(__popc(b), want - have);
             if (take < __popc(b)) {
                 unsigned bb = b;          // stop at the first given entry not taken
@@ -338,7 +382,9 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
     }
     __syncthreads();
     const int cnt = scount;
-    if (sel == STMF_SEL_TD_A) {
+    if (elem) {
+        // k = f(i,j) was read with the element
+    } else if (sel == STMF_SEL_TD_A) {
         // warp a takes column a of the window; lane l loads component l's
         // count, and the warp keeps the largest (the smaller l on ties)
         const int a = tid >> 5, l = tid & 31;
@@ -365,11 +411,14 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
     }
     __syncthreads();
     if (tid < cnt) {
+        // slot: j, k, type, index within the row (or ByElement segment),
+        // screen flag, row i, position recorded in the trace
         const int base = ctl->ncand_row / 2;
+        const int ci = elem ? si[tid] : i, cq = elem ? sq[tid] : base + tid;
         int *c0 = P.cand + 8 * (2 * tid);
-        c0[0] = sj[tid]; c0[1] = sk[tid]; c0[2] = 0; c0[3] = base + tid; c0[4] = 0;
+        c0[0] = sj[tid]; c0[1] = sk[tid]; c0[2] = 0; c0[3] = base + tid; c0[4] = 0; c0[5] = ci; c0[6] = cq;
         int *c1 = P.cand + 8 * (2 * tid + 1);
-        c1[0] = sj[tid]; c1[1] = sk[tid]; c1[2] = 1; c1[3] = base + tid; c1[4] = 0;
+        c1[0] = sj[tid]; c1[1] = sk[tid]; c1[2] = 1; c1[3] = base + tid; c1[4] = 0; c1[5] = ci; c1[6] = cq;
     }
     if (tid == 0) {
         // evaluation lists grouped by k (stable), so the evaluation recomputes
@@ -405,7 +454,7 @@ __global__ void k_seed(stmf_problem P)
     const int c = blockIdx.y;
     if (c >= ctl->nc) return;
     const int *cd = P.cand + 8 * c;
-    const int j = cd[0], k = cd[1], type = cd[2], i = ctl->i;
+    const int j = cd[0], k = cd[1], type = cd[2], i = cd[5];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (type == 0) {
         if (x < P.mp) P.Uc[(size_t)c * P.mp + x] = x < P.m ? INFINITY : 0.f;
@@ -538,22 +587,36 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
             ctl->f_new = ctl->f + sf[kept];
         }
         if (!single) {
+            const bool elem = P.strategy == STMF_STRATEGY_BYELEMENT;
             if (kept >= 0) {
                 const int *cd = P.cand + 8 * kept;
                 ctl->f = ctl->f_new;          // exact value recomputed by the refresh
                 ctl->dirty_k = cd[1];
                 ctl->accepted += 1;
-                put_trace(ctl, cd[3], cd[0], cd[1], cd[2], ctl->f_new);
+                if (elem) {
+                    ctl->i = cd[5];
+                    ctl->pos = cd[6] + 1;     // ByElement: the scan goes on from the next element
+                }
+                put_trace(ctl, cd[6], cd[0], cd[1], cd[2], ctl->f_new);
                 ctl->row_done = 1;
             } else if (ctl->exhausted) {
-                put_trace(ctl, -1, -1, -1, -1, ctl->f);
+                if (!elem) put_trace(ctl, -1, -1, -1, -1, ctl->f);
                 ctl->row_done = 1;
             } else {
                 ctl->wj = min(ctl->wj * 2, ctl->wmax / 2);
                 ctl->row_done = 0;
             }
             if (ctl->row_done) {
-                ctl->i += 1;
+                if (elem) {
+                    ctl->more = kept >= 0 && ctl->pos < P.m * P.n;
+                    if (!ctl->more) {
+                        ctl->i = -1;          // end of the sweep's scan
+                        put_trace(ctl, -1, -1, -1, -1, ctl->f);
+                    }
+                } else {
+                    ctl->i += 1;
+                    ctl->more = ctl->i < ctl->m;
+                }
                 // the next row's first window covers as many columns as this
                 // row consumed (rounded up to a power of two): a window's
                 // size never changes the decision, only the work per launch
@@ -566,7 +629,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
                 cudaGraphSetConditional(h_win, ctl->row_done ? 0u : 1u);
                 if (ctl->row_done) {
                     cudaGraphSetConditional(h_dirty, kept >= 0 ? 1u : 0u);
-                    cudaGraphSetConditional(h_row, ctl->i < ctl->m ? 1u : 0u);
+                    cudaGraphSetConditional(h_row, ctl->more ? 1u : 0u);
                 }
             }
         }
@@ -593,7 +656,7 @@ __global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph
     ctl_load(sctl, P.ctl);
     stmf_ctl *ctl = &sctl;
     if (threadIdx.x == 0) {
-        ctl->pos = 0;
+        if (P.strategy != STMF_STRATEGY_BYELEMENT) ctl->pos = 0;   // ByElement: the scan position carries on
         ctl->ncand_row = 0;
         ctl->wj = ctl->wj0;
         ctl->kept = 0;
@@ -612,8 +675,10 @@ __global__ void k_sweep_begin(stmf_problem P, int in_graph, cudaGraphConditional
 {
     stmf_ctl *ctl = P.ctl;
     ctl->i = 0;
+    ctl->pos = 0;
+    ctl->more = ctl->m > 0;
     if (in_graph) {
-        cudaGraphSetConditional(h_row, ctl->m > 0 ? 1u : 0u);
+        cudaGraphSetConditional(h_row, ctl->more ? 1u : 0u);
         cudaGraphSetConditional(h_dirty, ctl->dirty_k != -2 ? 1u : 0u);
     }
 }
@@ -644,7 +709,7 @@ __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
 {
     stmf_ctl *ctl = P.ctl;
     int *c0 = P.cand;
-    c0[0] = j; c0[1] = k; c0[2] = type; c0[3] = 0; c0[4] = 0;
+    c0[0] = j; c0[1] = k; c0[2] = type; c0[3] = 0; c0[4] = 0; c0[5] = i; c0[6] = 0;
     ctl->i = i;
     ctl->nc = 1;
     ctl->nu = type == 0 ? 1 : 0;
@@ -681,19 +746,25 @@ cudaError_t launch_pack(cudaStream_t st, const float *R, int ldr, const uint32_t
 }
 
 cudaError_t launch_pack_oriented(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm,
-                                 int m, int n, int transposed, const int *perm, float *Rp, int ldp, int mp,
-                                 int *bad)
+                                 int m, int n, int transposed, const int *perm, const int *cperm, float *Rp,
+                                 int ldp, int mp, int *bad)
 {
     dim3 grid(ldp / 32, mp / 8), block(32, 8);
-    k_pack_oriented<<<grid, block, 0, st>>>(R, ldr, mask, ldm, m, n, transposed, perm, Rp, ldp, mp, bad);
+    k_pack_oriented<<<grid, block, 0, st>>>(R, ldr, mask, ldm, m, n, transposed, perm, cperm, Rp, ldp, mp, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_min(cudaStream_t st, const float *Rp, int ldp, int m, int n, float *cmin)
+{
+    k_col_min<<<(n + 31) / 32, 1024, 0, st>>>(Rp, ldp, m, n, cmin);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unorient(cudaStream_t st, const stmf_problem *P, int transposed, const int *perm,
-                            float *U_out, float *V_out)
+                            const int *cperm, float *U_out, float *V_out)
 {
     const int tot = max(P->m * P->r, P->r * P->n);
-    k_unorient<<<(tot + 255) / 256, 256, 0, st>>>(P->U, P->V, P->m, P->n, P->r, P->np, transposed, perm,
+    k_unorient<<<(tot + 255) / 256, 256, 0, st>>>(P->U, P->V, P->m, P->n, P->r, P->np, transposed, perm, cperm,
                                                   U_out, V_out);
     return cudaGetLastError();
 }

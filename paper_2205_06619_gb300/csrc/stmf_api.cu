@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/stmf.h: argument validation,
 // device workspaces, set-up of a problem, the F-ULF / F-URF single updates
 // and the row loop of Algorithm 3 (FastSTMF).
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -116,7 +117,7 @@ void problem_free(stmf_problem *P)
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
                     P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
-                    P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg};
+                    P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg, P->cperm};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
@@ -418,7 +419,7 @@ stmf_status sweep_host(stmf_problem *P)
     CK(launch_sweep_begin(st, P, 0));
     stmf_status s = read_ctl(P);
     if (s != STMF_OK) return s;
-    for (int i = 0; i < P->m; ++i) {
+    while (P->ctl_host->more) {           // ByRow: one pass per row; ByElement: per kept update
         if (P->ctl_host->dirty_k != -2) {
             s = refresh(P);
             if (s != STMF_OK) return s;
@@ -452,6 +453,11 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (o.V0 && !o.U0) return fail(ctx, STMF_ERR_INVALID, "V0 needs U0");
     if (o.selection < STMF_SEL_TD_A || o.selection > STMF_SEL_SEQ)
         return fail(ctx, STMF_ERR_INVALID, "selection %d unknown", o.selection);
+    if (o.strategy != STMF_STRATEGY_BYROW && o.strategy != STMF_STRATEGY_BYELEMENT)
+        return fail(ctx, STMF_ERR_INVALID, "strategy %d unknown", o.strategy);
+    const bool elem = o.strategy == STMF_STRATEGY_BYELEMENT;
+    if (elem && (o.perm || o.selection != STMF_SEL_TD_A))
+        return fail(ctx, STMF_ERR_INVALID, "the ByElement strategy takes no row permutation and no selection");
     const int tr = m0 > n0;                 // Algorithm 3: a tall R is transposed
     const int m = tr ? n0 : m0, n = tr ? m0 : n0;
     std::vector<int> perm;
@@ -462,6 +468,9 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
             if (x < 0 || x >= m || seen[x]) return fail(ctx, STMF_ERR_INVALID, "perm is not a permutation of 0..%d", m - 1);
             seen[x] = 1;
         }
+    } else if (elem) {
+        perm.resize(m);                     // ByElement keeps the rows in their order
+        for (int s = 0; s < m; ++s) perm[s] = s;
     } else {
         random_permutation(m, o.seed, perm);
     }
@@ -471,6 +480,7 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (s != STMF_OK) return s;
     P->transposed = tr; P->m0 = m0; P->n0 = n0;
     P->sel = o.selection;
+    P->strategy = o.strategy;
     {
         cudaError_t ea = cudaSuccess;
         if (P->sel == STMF_SEL_TD) {
@@ -512,7 +522,30 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->perm, perm.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, tr, P->perm, P->R, P->np, P->mp, d_bad);
+    if (e == cudaSuccess) e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, tr, P->perm, nullptr, P->R,
+                                                   P->np, P->mp, d_bad);
+    if (e == cudaSuccess && elem) {
+        // PermC: columns in increasing order of their minimum given entry,
+        // equal minima keeping the smaller column first; then pack again
+        float *d_cmin = nullptr;
+        std::vector<float> cmin(n);
+        std::vector<int> cp(n);
+        e = cudaMalloc(&d_cmin, sizeof(float) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&P->cperm, sizeof(int) * n);
+        if (e == cudaSuccess) e = launch_col_min(st, P->R, P->np, m, n, d_cmin);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cmin.data(), d_cmin, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            for (int t = 0; t < n; ++t) cp[t] = t;
+            std::stable_sort(cp.begin(), cp.end(), [&](int a, int b) { return cmin[a] < cmin[b]; });
+            e = cudaMemcpyAsync(P->cperm, cp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess)
+            e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, tr, P->perm, P->cperm, P->R, P->np, P->mp,
+                                     d_bad);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // cp, cmin stay alive until the copies end
+        if (d_cmin) cudaFree(d_cmin);
+    }
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -615,7 +648,7 @@ stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *tra
 {
     stmf_ctx *ctx = P->ctx;
     cudaStream_t st = ctx->stream;
-    if (U_out && V_out) CK(launch_unorient(st, P, P->transposed, P->perm, U_out, V_out));
+    if (U_out && V_out) CK(launch_unorient(st, P, P->transposed, P->perm, P->cperm, U_out, V_out));
     stmf_status s = read_ctl(P);
     if (s != STMF_OK) return s;
     if (trace_out && P->trace_dev) {
@@ -687,7 +720,7 @@ stmf_status sweep_rows_host(stmf_problem *P, int rows)
     stmf_status s = read_ctl(P);
     if (s != STMF_OK) return s;
     const int nr = rows < P->m ? rows : P->m;
-    for (int i = 0; i < nr; ++i) {
+    for (int i = 0; i < nr && P->ctl_host->more; ++i) {
         if (P->ctl_host->dirty_k != -2) CS(refresh(P));
         CK(launch_row_begin(st, P, 0));
         while (true) {
@@ -756,7 +789,7 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
         if (P->ctl_host->dirty_k != -2) { CS(refresh(P)); CS(read_ctl(P)); }
         P->sweeps_done = P->ctl_host->sweep;
         P->seconds = secs;
-        CK(launch_unorient(st, P, P->transposed, P->perm, probs[q].U_out, probs[q].V_out));
+        CK(launch_unorient(st, P, P->transposed, P->perm, P->cperm, probs[q].U_out, probs[q].V_out));
         if (reports) fill_report(P, &reports[q]);
     }
     CK(cudaStreamSynchronize(st));

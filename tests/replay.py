@@ -41,3 +41,52 @@ def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=
         Ui, Vi, f = Ug, Vg, f_g
     U, V = orc.finish(R.shape[0], R.shape[1], st["transposed"], Ui, Vi, st["perm"])
     return dict(U=U, V=V, f=f, divergences=divergences, perm=st["perm"], transposed=st["transposed"])
+
+
+def replay_byelement(R, M, r, gpu_trace, seed=0, picks=None, p=5, tol=1e-6):
+    """The same lockstep replay for the ByElement method: at each GPU record
+    (a kept update, or the end of a sweep) the oracle scans from its own
+    position to its first kept update; a different outcome is accepted only
+    as a near-tie within ``tol`` relative, and the oracle then adopts the
+    GPU's outcome."""
+    import numpy as np
+    R = np.asarray(R, dtype=np.float64)
+    M = np.asarray(M, dtype=bool)
+    tr = R.shape[0] > R.shape[1]
+    Ro, Mo = (R.T.copy(), M.T.copy()) if tr else (R, M)
+    cp = orc.colmin_perm(Ro, Mo)
+    Rc, Mc = Ro[:, cp].copy(), Mo[:, cp].copy()
+    m = Rc.shape[0]
+    st = orc.prepare(Rc, Mc, r, perm=np.arange(m, dtype=np.int32), picks=picks, p=p, seed=seed)
+    Ri, Mi, Ui, Vi = st["R"], st["M"], st["U"], st["V"]
+    f = orc.error(Ri, Mi, Ui, Vi)
+    q = 0
+    divergences = []
+    for rec in gpu_trace:
+        sweep, i, pos, j, k, typ, f_gpu = rec
+        U0_, V0_ = Ui.copy(), Vi.copy()
+        got, fn, out, _ = orc.element_scan(Ri, Mi, Ui, Vi, q, f)
+        gpu_kept = i >= 0
+        same = (got >= 0) == gpu_kept and (not gpu_kept or (got == pos and out == (i, j, k, typ)))
+        if same:
+            f = fn
+            assert abs(f_gpu - f) <= tol * max(f, 1e-30), (rec, f)
+            q = got + 1 if gpu_kept else 0
+            continue
+        f_old = f
+        f_orc = fn if got >= 0 else f_old
+        if gpu_kept:
+            fun = orc.fulf if typ == 0 else orc.furf
+            Ug, Vg, f_g = fun(Ri, Mi, U0_, V0_, i, j, k)
+        else:
+            Ug, Vg, f_g = U0_, V0_, f_old
+        scale = tol * max(f_old, 1e-30)
+        ok = abs(f_g - f_orc) <= scale or abs(f_g - f_old) <= scale or abs(f_orc - f_old) <= scale
+        assert ok, ("decision differs beyond tolerance", rec, got, out, f_old, f_orc, f_g)
+        divergences.append((rec, got, out, f_old, f_orc, f_g))
+        Ui, Vi, f = Ug, Vg, f_g
+        q = pos + 1 if gpu_kept else 0
+    Vo = np.empty_like(Vi)
+    Vo[:, cp] = Vi
+    U, V = (Vo.T.copy(), Ui.T.copy()) if tr else (Ui, Vo)
+    return dict(U=U, V=V, f=f, divergences=divergences, transposed=tr, cperm=cp)

@@ -67,6 +67,11 @@ def test_selection_names_match_the_header():
     assert o.selection == api.SELECTIONS["TD_A"]
     with pytest.raises(ValueError):
         api._selection("BEST")
+    strategies = dict((k, int(v)) for k, v in re.findall(r"STMF_STRATEGY_([A-Z_]+)\s*=\s*(\d+)", text))
+    assert {k.upper(): v for k, v in api.STRATEGIES.items()} == strategies
+    assert o.strategy == api.STRATEGIES["ByRow"]
+    with pytest.raises(ValueError):
+        api._strategy("ByColumn")
 
 
 def test_invalid_arguments_fail_without_launch():
