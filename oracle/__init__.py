@@ -86,6 +86,14 @@ def lib():
         L.orc_element_scan.argtypes = [i, i, i, i, P, P, P, P, i, P, P, P]
         L.orc_factorize_byelement.restype = i
         L.orc_factorize_byelement.argtypes = [i, i, i, i, P, P, i, d, P, i, u64, P, P, P, P, P, i64, P]
+        L.orc_matrix_coin.restype = i
+        L.orc_matrix_coin.argtypes = [u64, i64, i, i, i]
+        L.orc_matrix_order.restype = i
+        L.orc_matrix_order.argtypes = [i, i, i, i, P, P, P, P, u64, i64, P, P, P, P]
+        L.orc_matrix_step.restype = i
+        L.orc_matrix_step.argtypes = [i, i, i, i, P, P, P, P, u64, i64, P, P, P]
+        L.orc_factorize_bymatrix.restype = i
+        L.orc_factorize_bymatrix.argtypes = [i, i, i, i, P, P, i, d, P, i, u64, P, P, P, P, P, i64, P]
         _lib = L
     return _lib
 
@@ -284,6 +292,55 @@ def element_scan(R, M, U, V, q0, f, mode="fp32"):
     return int(q), fb.value, tuple(int(x) for x in out[1:]), tried.value
 
 
+def matrix_coin(seed, it, m, n, q):
+    """ByMatrix's coin for iteration it and element q: 0 = F-ULF, 1 = F-URF."""
+    return int(lib().orc_matrix_coin(seed, it, m, n, q))
+
+
+def matrix_order(R, M, U, V, seed, it, mode="fp32"):
+    """ByMatrix order of iteration it: (q, k, type, err) arrays."""
+    R, M, U, V = _d(R), _m(M), _d(U), _d(V)
+    m, n = R.shape
+    r = U.shape[1]
+    qs = np.empty(m * n, np.int32); ks = np.empty(m * n, np.int32); ty = np.empty(m * n, np.int32)
+    errs = np.empty(m * n)
+    c = lib().orc_matrix_order(_mode(mode), m, n, r, _p(R), _p(M), _p(U), _p(V), seed, it, _p(qs), _p(ks),
+                               _p(ty), _p(errs))
+    return qs[:c].copy(), ks[:c].copy(), ty[:c].copy(), errs[:c].copy()
+
+
+def matrix_step(R, M, U, V, seed, it, f, mode="fp32"):
+    """One ByMatrix iteration in place on U, V.
+
+    Returns (kept, f_new, (pos, i, j, k, type), tried)."""
+    R, M = _d(R), _m(M)
+    assert U.dtype == np.float64 and V.dtype == np.float64 and U.flags.c_contiguous and V.flags.c_contiguous
+    m, n = R.shape
+    r = U.shape[1]
+    fb = C.c_double(f)
+    out = np.full(5, -1, np.int32)
+    tried = C.c_int64(0)
+    kept = lib().orc_matrix_step(_mode(mode), m, n, r, _p(R), _p(M), _p(U), _p(V), seed, it, C.byref(fb),
+                                 _p(out), C.byref(tried))
+    return bool(kept), fb.value, tuple(int(x) for x in out), tried.value
+
+
+def _factorize_bymatrix(R0, M0, r, sweeps, eps, picks, p, seed, U0, mode, trace_cap):
+    m0, n0 = R0.shape
+    U = np.empty((m0, r)); V = np.empty((r, n0))
+    f_hist = np.full(sweeps + 1, np.nan)
+    trace = np.empty((max(trace_cap, 1), 6), np.int32)
+    counters = np.zeros(4, np.int64)
+    empty = lib().orc_factorize_bymatrix(_mode(mode), m0, n0, r, _p(R0), _p(M0), sweeps, eps, _p(picks), p,
+                                         seed, _p(U0), _p(U), _p(V), _p(f_hist),
+                                         _p(trace) if trace_cap else None, trace_cap, _p(counters))
+    if empty:
+        raise ValueError("oracle: %d rows/columns without a given entry" % empty)
+    done = int(counters[0])
+    return dict(U=U, V=V, f_hist=f_hist[:done + 1], sweeps=done, tried=int(counters[1]),
+                kept=int(counters[2]), trace=trace[:int(counters[3])].copy() if trace_cap else None)
+
+
 def _factorize_byelement(R0, M0, r, sweeps, eps, picks, p, seed, U0, mode, trace_cap):
     m0, n0 = R0.shape
     U = np.empty((m0, r)); V = np.empty((r, n0))
@@ -306,18 +363,21 @@ def factorize(R0, M0, r, sweeps, eps=0.0, perm=None, picks=None, p=5, seed=0, U0
     published; TD_B, TD, SEQ of Section "The ByRow strategy"), or, with
     strategy="ByElement", STMF_ByElement_PermC_TD_W (Section "The ByElement
     strategy"; perm and selection do not apply, U0 is in the frame of the
-    oriented, column-permuted matrix).
+    oriented, column-permuted matrix), or with strategy="ByMatrix",
+    STMF_ByMatrix_NoPerm_TD_W (Section "The ByMatrix strategy"; `sweeps`
+    counts its iterations, each keeping at most one update).
     Returns dict(U, V, f_hist, sweeps, tried, kept, trace)."""
-    if strategy not in ("ByRow", "ByElement"):
-        raise ValueError("strategy must be ByRow or ByElement")
-    if strategy == "ByElement":
+    if strategy not in ("ByRow", "ByElement", "ByMatrix"):
+        raise ValueError("strategy must be ByRow, ByElement or ByMatrix")
+    if strategy != "ByRow":
         if perm is not None or selection != "TD_A":
-            raise ValueError("ByElement takes no row permutation and no selection")
+            raise ValueError("%s takes no row permutation and no selection" % strategy)
         R0, M0 = _d(R0), _m(M0)
         p = min(p, max(R0.shape))
         picks = None if picks is None else np.ascontiguousarray(picks, np.int32)
         U0 = None if U0 is None else _d(U0)
-        return _factorize_byelement(R0, M0, r, sweeps, eps, picks, p, seed, U0, mode, trace_cap)
+        fn = _factorize_byelement if strategy == "ByElement" else _factorize_bymatrix
+        return fn(R0, M0, r, sweeps, eps, picks, p, seed, U0, mode, trace_cap)
     R0, M0 = _d(R0), _m(M0)
     m0, n0 = R0.shape
     p = min(p, max(m0, n0))  # the oriented matrix is wide: n = max(m0, n0)

@@ -717,3 +717,153 @@ int orc_factorize_byelement(int mode, int m0, int n0, int r, const double *R0, c
     free(ident); free(perm_out);
     return empty;
 }
+
+/* ------------------------------------------------------------------------
+ * STMF_ByMatrix_NoPerm_TD_W (Section "The ByMatrix strategy"; its
+ * pseudocode in the Supplement).
+ * ---------------------------------------------------------------------- */
+
+/* The coin of "random() < 0.5" (Reading: one fair coin per iteration and
+ * element, drawn from SplitMix64 keyed by seed ^ 0x5A5A...5A at counter
+ * it * m * n + q; the top bit 0 chooses F-ULF, 1 F-URF).                    */
+int orc_matrix_coin(uint64_t seed, int64_t it, int m, int n, int q)
+{
+    uint64_t c = (uint64_t)it * (uint64_t)m * (uint64_t)n + (uint64_t)q;
+    return (int)(orc_splitmix64(seed ^ 0x5A5A5A5A5A5A5A5Aull, c) >> 63);
+}
+
+typedef struct { double err; int32_t q; } orc_err_item;
+
+static int cmp_err_desc(const void *a, const void *b)
+{
+    const orc_err_item *x = (const orc_err_item *)a, *y = (const orc_err_item *)b;
+    if (x->err != y->err) return x->err > y->err ? -1 : 1;   /* decreasing err */
+    return x->q < y->q ? -1 : (x->q > y->q);                  /* then smaller q */
+}
+
+/* The ByMatrix order of one iteration: every given element (i, j) with
+ *   err(i,j) = td_row(i) + td_col(j) - td(i,j)
+ * (td over given entries; td_row and td_col summed in double in index order;
+ * err evaluated as (td_row + td_col) - td in double), sorted by decreasing
+ * err, equal err keeping the smaller q = i*n + j first; each with k = f(i,j)
+ * and the iteration's coin.  Returns the count; qs, ks, types, errs
+ * (nullable) receive them in order.                                         */
+int orc_matrix_order(int mode, int m, int n, int r, const double *R, const uint8_t *M, const double *U,
+                     const double *V, uint64_t seed, int64_t it, int32_t *qs, int32_t *ks, int32_t *types,
+                     double *errs)
+{
+    double *P1 = (double *)malloc(sizeof(double) * (size_t)m * n);
+    int32_t *A = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    double *td = (double *)malloc(sizeof(double) * (size_t)m * n);
+    double *tdr = (double *)calloc((size_t)m, sizeof(double));
+    double *tdc = (double *)calloc((size_t)n, sizeof(double));
+    orc_maxplus(mode, m, n, r, U, V, P1, A, NULL);
+    for (size_t e = 0; e < (size_t)m * n; ++e) td[e] = M[e] ? fabs(sub_(mode, R[e], P1[e])) : 0.0;
+    for (int s = 0; s < m; ++s)
+        for (int t = 0; t < n; ++t)
+            if (M[(size_t)s * n + t]) tdr[s] += td[(size_t)s * n + t];
+    for (int t = 0; t < n; ++t)
+        for (int s = 0; s < m; ++s)
+            if (M[(size_t)s * n + t]) tdc[t] += td[(size_t)s * n + t];
+    orc_err_item *it_ = (orc_err_item *)malloc(sizeof(orc_err_item) * (size_t)m * n);
+    int cnt = 0;
+    for (int q = 0; q < m * n; ++q)
+        if (M[q]) {
+            it_[cnt].err = (tdr[q / n] + tdc[q % n]) - td[q];
+            it_[cnt].q = q;
+            ++cnt;
+        }
+    qsort(it_, (size_t)cnt, sizeof(orc_err_item), cmp_err_desc);
+    for (int a = 0; a < cnt; ++a) {
+        qs[a] = it_[a].q;
+        ks[a] = A[it_[a].q];
+        types[a] = orc_matrix_coin(seed, it, m, n, it_[a].q);
+        if (errs) errs[a] = it_[a].err;
+    }
+    free(P1); free(A); free(td); free(tdr); free(tdc); free(it_);
+    return cnt;
+}
+
+/* One ByMatrix iteration: in the order of orc_matrix_order, apply the
+ * element's update (F-ULF or F-URF by its coin); keep the first that lowers
+ * the error (strictly) and end the iteration, else revert and go on.
+ * out = {position, i, j, k, type}; returns 1 if an update was kept.         */
+int orc_matrix_step(int mode, int m, int n, int r, const double *R, const uint8_t *M, double *U, double *V,
+                    uint64_t seed, int64_t it, double *f, int32_t *out, int64_t *tried)
+{
+    int32_t *qs = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    int32_t *ks = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    int32_t *ty = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    double *ucol = (double *)malloc(sizeof(double) * (size_t)m);
+    double *vrow = (double *)malloc(sizeof(double) * (size_t)n);
+    int cnt = orc_matrix_order(mode, m, n, r, R, M, U, V, seed, it, qs, ks, ty, NULL);
+    int kept = 0;
+    for (int a = 0; a < cnt && !kept; ++a) {
+        const int i = qs[a] / n, j = qs[a] % n, k = ks[a];
+        get_col(m, r, U, k, ucol);
+        memcpy(vrow, V + (size_t)k * n, sizeof(double) * (size_t)n);
+        double fn = ty[a] == 0 ? orc_fulf(mode, m, n, r, R, M, U, V, i, j, k)
+                               : orc_furf(mode, m, n, r, R, M, U, V, i, j, k);
+        if (tried) *tried += 1;
+        if (fn < *f) {
+            *f = fn;
+            out[0] = a; out[1] = i; out[2] = j; out[3] = k; out[4] = ty[a];
+            kept = 1;
+        } else {
+            set_col(m, r, U, k, ucol);
+            memcpy(V + (size_t)k * n, vrow, sizeof(double) * (size_t)n);
+        }
+    }
+    if (!kept) { out[0] = -1; out[1] = -1; out[2] = -1; out[3] = -1; out[4] = -1; }
+    free(qs); free(ks); free(ty); free(ucol); free(vrow);
+    return kept;
+}
+
+/* The whole ByMatrix method: R oriented wide (square counts as wide), no
+ * permutation, U initialised (Random Acol, or U0 in the oriented frame) and
+ * V = (-U)^T (x)* R; then `iterations` iterations of orc_matrix_step (each
+ * keeps at most one update), stopping earlier when eps > 0 and an iteration
+ * changed the error by less than eps.  trace (nullable, 6 int32 per record):
+ * {iteration, i, position, j, k, type} per iteration (position -1: nothing
+ * kept).  counters as orc_factorize.                                        */
+int orc_factorize_bymatrix(int mode, int m0, int n0, int r, const double *R0, const uint8_t *M0,
+                           int iterations, double eps, const int32_t *picks_in, int p, uint64_t seed,
+                           const double *U0, double *U_out, double *V_out, double *f_hist,
+                           int32_t *trace, int64_t trace_cap, int64_t *counters)
+{
+    const int tr = m0 > n0;
+    const int m = tr ? n0 : m0, n = tr ? m0 : n0;
+    double *Ri = (double *)malloc(sizeof(double) * (size_t)m * n);
+    uint8_t *Mi = (uint8_t *)malloc((size_t)m * n);
+    double *Ui = (double *)malloc(sizeof(double) * (size_t)m * r);
+    double *Vi = (double *)malloc(sizeof(double) * (size_t)r * n);
+    int32_t *ident = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    int32_t *perm_out = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    for (int s = 0; s < m; ++s) ident[s] = s;
+    int transposed = 0;
+    int empty = orc_prepare(mode, m0, n0, r, R0, M0, ident, picks_in, p, seed, U0, Ri, Mi, Ui, Vi, perm_out,
+                            &transposed);
+    int64_t tried = 0, kept = 0, nrec = 0;
+    int done = 0;
+    if (empty == 0) {
+        double f = orc_error(mode, m, n, r, Ri, Mi, Ui, Vi);
+        if (f_hist) f_hist[0] = f;
+        for (int it = 0; it < iterations; ++it) {
+            double f_prev = f;
+            int32_t out[5];
+            kept += orc_matrix_step(mode, m, n, r, Ri, Mi, Ui, Vi, seed, it, &f, out, &tried);
+            if (trace && nrec < trace_cap) {
+                int32_t *rec = trace + 6 * nrec;
+                rec[0] = it; rec[1] = out[1]; rec[2] = out[0]; rec[3] = out[2]; rec[4] = out[3]; rec[5] = out[4];
+                ++nrec;
+            }
+            ++done;
+            if (f_hist) f_hist[it + 1] = f;
+            if (eps > 0.0 && fabs(f_prev - f) < eps) break;
+        }
+        orc_finish(m0, n0, r, transposed, Ui, Vi, ident, U_out, V_out);
+    }
+    if (counters) { counters[0] = done; counters[1] = tried; counters[2] = kept; counters[3] = nrec; }
+    free(Ri); free(Mi); free(Ui); free(Vi); free(ident); free(perm_out);
+    return empty;
+}
