@@ -316,7 +316,9 @@ def run_selection(args):
     strategy": TD_A as published, TD_B, TD, SEQ) and the ByElement strategy
     (STMF_ByElement_PermC_TD_W) on the gene-expression workload: sweeps/s over
     sweeps W..W+K-1 of one run each (CUDA events on the library's stream),
-    with the error reached and the candidates tried.
+    with the error reached and the candidates tried; the ByMatrix strategy
+    (STMF_ByMatrix_NoPerm_TD_W, one update per iteration): iterations/s over
+    iterations W..W+100K-1.
     CPU leg: the oracle computing the same row's (j, k) order for each
     selection from the library's final state."""
     import torch
@@ -348,6 +350,23 @@ def run_selection(args):
             if sel == "TD_A":
                 last = fz.result()
             fz.close()
+        # ByMatrix: one update per iteration; 100 K iterations timed after W
+        fz = api.Factorization(Rg, Mw, rank=r, seed=args.seed, strategy="ByMatrix")
+        fz.run(args.warmup)
+        rep0 = fz.run(0)
+        nit = 100 * args.steps
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        rep1 = fz.run(nit)
+        b.record(stream)
+        torch.cuda.synchronize()
+        secs = a.elapsed_time(b) / 1e3
+        d = {k: rep1[k] - rep0[k] for k in ("candidates_tried", "accepted", "windows")}
+        res["ByMatrix"] = {"iterations_per_s": nit / secs, "iterations": nit, "f_start": rep0["f_final"],
+                           "f_end": rep1["f_final"], "f_init": rep1["f_init"],
+                           "per_iteration": {k: v / nit for k, v in d.items()}}
+        fz.close()
     cpu = None
     if not args.no_cpu_baseline:
         import oracle   # CPU leg: the oracle's row orders from the library's TD_A state

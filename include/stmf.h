@@ -92,8 +92,20 @@ enum { STMF_SEL_TD_A = 0, STMF_SEL_TD_B = 1, STMF_SEL_TD = 2, STMF_SEL_SEQ = 3 }
  *              the oriented, column-permuted matrix.  Trace: one record per
  *              kept update {sweep, i, q = i*n + j, j, k, type, f} (oriented,
  *              permuted frame) and one {sweep, -1, -1, -1, -1, -1, f} at the
- *              end of each sweep. */
-enum { STMF_STRATEGY_BYROW = 0, STMF_STRATEGY_BYELEMENT = 1 };
+ *              end of each sweep.
+ *   BYMATRIX:  STMF_ByMatrix_NoPerm_TD_W (the Supplement's pseudocode): R
+ *              oriented wide, no permutation.  Each iteration ranks every
+ *              given element by err = td_row(i) + td_col(j) - td(i,j)
+ *              (td_row, td_col summed in FP64 in index order; decreasing err,
+ *              equal err: smaller q = i*n + j first) and tries them in that
+ *              order with k = f(i,j) and F-ULF or F-URF by a fair coin (the
+ *              top bit of SplitMix64 keyed by seed ^ 0x5A5A5A5A5A5A5A5A at
+ *              counter it*m*n + q: 0 = F-ULF), ending at the first update that
+ *              lowers the error.  `sweeps` counts iterations.  Needs perm =
+ *              NULL and selection = TD_A.  Trace: one record per iteration
+ *              {it, i, position in the order, j, k, type, f}, or
+ *              {it, -1, -1, -1, -1, -1, f} when nothing was kept. */
+enum { STMF_STRATEGY_BYROW = 0, STMF_STRATEGY_BYELEMENT = 1, STMF_STRATEGY_BYMATRIX = 2 };
 
 /* Options of the factorization (Algorithm 3 and its readings). */
 typedef struct {
@@ -135,7 +147,8 @@ typedef struct {
                             TD keeps a per-row column order (three extra launches
                             per row); TD_B a per-column argmax (one extra launch
                             per refresh).                                          */
-    int strategy;        /* STMF_STRATEGY_*: 0 = ByRow (Algorithm 3), 1 = ByElement   */
+    int strategy;        /* STMF_STRATEGY_*: 0 = ByRow (Algorithm 3), 1 = ByElement,
+                            2 = ByMatrix                                           */
 } stmf_options;
 
 /* A trace record: sweep, row (oriented, permuted index), position of the kept

@@ -49,7 +49,7 @@ SELECTIONS = {"TD_A": 0, "TD_B": 1, "TD": 2, "SEQ": 3}
 
 
 # update strategies (stmf.h STMF_STRATEGY_*): Algorithm 3, and the ByElement method
-STRATEGIES = {"ByRow": 0, "ByElement": 1}
+STRATEGIES = {"ByRow": 0, "ByElement": 1, "ByMatrix": 2}
 
 
 def _strategy(name):
@@ -385,8 +385,9 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     """FastSTMF (Algorithm 3) on the device.  R: float32 CUDA (m x n).
     mlp: an MLP (learned initialisation on the device) or None (Random Acol).
     selection: "TD_A" (the method as published), "TD_B", "TD" or "SEQ"
-    (Section "The ByRow strategy").  strategy: "ByRow" (Algorithm 3) or
-    "ByElement" (STMF_ByElement_PermC_TD_W; trace records per kept update).
+    (Section "The ByRow strategy").  strategy: "ByRow" (Algorithm 3),
+    "ByElement" (STMF_ByElement_PermC_TD_W; trace records per kept update) or
+    "ByMatrix" (STMF_ByMatrix_NoPerm_TD_W; `sweeps` counts its iterations).
 
     Returns (U m x r, V r x n, report dict, trace list or None)."""
     torch = _torch()

@@ -48,6 +48,18 @@ __device__ __forceinline__ stmf_ff ff_add(stmf_ff a, stmf_ff b)
     return {h, e - (h - s)};
 }
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) as a counter-based
+// generator: the output of a SplitMix64 whose state was `key` after c + 1
+// steps.  ByMatrix's coin ("random() < 0.5") for iteration it and element q is
+// the top bit of draw(coin_key, it m n + q): 0 = F-ULF, 1 = F-URF.
+__device__ __forceinline__ unsigned long long splitmix64_draw(unsigned long long key, unsigned long long c)
+{
+    unsigned long long z = key + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 // Argmax key of the TD_B / TD selections: the largest td first, then the
 // smaller index.  td >= 0, so its float bits order like its value.
 __device__ __forceinline__ unsigned long long td_argmax_key(float td, int idx)
@@ -144,6 +156,13 @@ struct stmf_problem {
     int *rowrank;      // np
     int *roworder;     // np: TD order of the current row (decreasing td(i, t), ties to smaller t)
     int *colarg;       // np: TD_B i0 of column t: the row of the largest td(s, t), the smaller s on ties
+    // ByMatrix order (NULL / 0 otherwise)
+    long long ngiven;  // given entries: the length of the order
+    size_t nsort;      // padded sort length (a power of two)
+    double *tdr_seq, *tdc_seq;   // m, n: td_row, td_col summed in FP64 in index order
+    unsigned long long *skey;    // nsort sort keys
+    unsigned *sval;              // nsort: element q = i n + j, in the iteration's order after the sort
+    unsigned long long coin_key; // key of the per-element coin (seed ^ 0x5A5A...5A)
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
@@ -186,6 +205,10 @@ cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int
                                 int ldpart, int n, int r, double *tdcol, int *colhist);
 cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_row_order(cudaStream_t st, stmf_problem *P);
+// kernels_bymatrix.cu
+size_t matrix_sort_len(int m, int n);
+cudaError_t launch_matrix_order(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_count_given(cudaStream_t st, const stmf_problem *P, unsigned long long *d_cnt);
 
 // kernels_update.cu
 cudaError_t launch_pack(cudaStream_t st, const float *R, int ldr, const uint32_t *mask, int ldm,

@@ -287,23 +287,28 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
 // row-major order, from where the scan stands (not reset per row): an
 // element is a candidate when R_ij is given and td(i,j) > 0, i.e. R_ij !=
 // P1_ij, with k = f(i,j) = A_ij; the window's elements may span rows.
-// Each pair gives F-ULF (slot 2a) then F-URF (slot 2a+1), the order in which
-// Algorithm 3 tries them.  At the first window of a row the row histogram
+// With the ByMatrix strategy the positions are those of the iteration's
+// sorted order of the given elements (kernels_bymatrix.cu); each element is
+// one candidate, F-ULF or F-URF by its coin, with k = A_ij; a window takes at
+// most STMF_WMAX / 2 of them (phase 1 holds at most that many of one type).
+// Otherwise each pair gives F-ULF (slot 2a) then F-URF (slot 2a+1), the order
+// in which Algorithm 3 tries them.  At the first window of a row the row histogram
 // (and TD_B's j0) is rebuilt.  Runs in a block of 1024 threads: at the start
 // of a row (k_row_begin) and after a window that neither kept a candidate
 // nor exhausted the row (k_select).
 __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ctl, bool row_start)
 {
     __shared__ int sh[STMF_MAX_RANK];
-    __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2], si[STMF_WMAX / 2], sq[STMF_WMAX / 2];
+    __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2], si[STMF_WMAX / 2], sq[STMF_WMAX / 2], sty[STMF_WMAX / 2];
     __shared__ int scount, spos;
     __shared__ unsigned long long sj0;
-    const bool elem = P.strategy == STMF_STRATEGY_BYELEMENT;
-    const int i = elem ? 0 : ctl->i, tid = threadIdx.x, r = P.r, sel = P.sel;
+    const bool elem = P.strategy == STMF_STRATEGY_BYELEMENT, mat = P.strategy == STMF_STRATEGY_BYMATRIX;
+    const int i = (elem || mat) ? 0 : ctl->i, tid = threadIdx.x, r = P.r, sel = P.sel;
     const float *Ri = P.R + (size_t)i * P.np;
-    // positions of the row's order (ByElement: of the whole sweep)
-    const int lim = elem ? P.m * P.n : (sel == STMF_SEL_SEQ ? P.n * r : P.n);
-    if (row_start && elem) {
+    // positions of the row's order (ByElement: of the whole sweep; ByMatrix:
+    // of the iteration's sorted order)
+    const int lim = elem ? P.m * P.n : mat ? (int)P.ngiven : (sel == STMF_SEL_SEQ ? P.n * r : P.n);
+    if (row_start && (elem || mat)) {
         if (tid == 0) ctl->ncand_row = 0;
         __syncthreads();
     } else if (row_start) {
@@ -342,16 +347,26 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         __syncthreads();
     }
     if (tid < 32) {
-        const int want = min(ctl->wj, ctl->wmax / 2);
+        const int want = mat ? min(2 * ctl->wj, ctl->wmax / 2) : min(ctl->wj, ctl->wmax / 2);
         int pos = ctl->pos, have = 0;
         const int lane = tid;
         const int *ord = sel == STMF_SEL_TD ? P.roworder : P.order;
         while (have < want && pos < lim) {
             const int q = pos + lane;
-            int j = 0, k = 0, ei = i;
+            int j = 0, k = 0, ei = i, ty = 0;
             bool ok = false;
             if (q < lim) {
-                if (elem) {
+                if (mat) {
+                    const unsigned qe = P.sval[q];
+                    ok = qe < (unsigned)P.m * (unsigned)P.n;   // the first ngiven of the order are the given elements
+                    if (ok) {
+                        ei = (int)(qe / (unsigned)P.n); j = (int)(qe - (unsigned)ei * (unsigned)P.n);
+                        k = P.A[(size_t)ei * P.np + j];
+                        const unsigned long long c = (unsigned long long)ctl->sweep * (unsigned long long)P.m *
+                                                     (unsigned long long)P.n + qe;
+                        ty = (int)(splitmix64_draw(P.coin_key, c) >> 63);
+                    }
+                } else if (elem) {
                     ei = q / P.n; j = q - ei * P.n;
                     const size_t e = (size_t)ei * P.np + j;
                     const float x = P.R[e];
@@ -367,6 +382,7 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
             const int rank = __popc(b & ((1u << lane) - 1u));
             if (ok && have + rank < want) {
                 sj[have + rank] = j; sk[have + rank] = k; si[have + rank] = ei; sq[have + rank] = q;
+                sty[have + rank] = ty;
             }
             const int take = min(__popc(b), want - have);
             if (take < __popc(b)) {
@@ -382,7 +398,7 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
     }
     __syncthreads();
     const int cnt = scount;
-    if (elem) {
+    if (elem || mat) {
         // k = f(i,j) was read with the element
     } else if (sel == STMF_SEL_TD_A) {
         // warp a takes column a of the window; lane l loads component l's
@@ -410,6 +426,37 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         }
     }
     __syncthreads();
+    if (mat) {
+        // one slot per element, in the order: j, k, type (its coin), index
+        // within the iteration, screen flag, row i, position in the order
+        if (tid < cnt) {
+            int *c0 = P.cand + 8 * tid;
+            c0[0] = sj[tid]; c0[1] = sk[tid]; c0[2] = sty[tid]; c0[3] = ctl->ncand_row + tid; c0[4] = 0;
+            c0[5] = si[tid]; c0[6] = sq[tid];
+        }
+        if (tid == 0) {
+            int idx[STMF_WMAX / 2];
+            for (int a = 0; a < cnt; ++a) {          // grouped by k (stable)
+                int b = a - 1;
+                while (b >= 0 && sk[idx[b]] > sk[a]) { idx[b + 1] = idx[b]; --b; }
+                idx[b + 1] = a;
+            }
+            int nu = 0, nv = 0;
+            for (int a = 0; a < cnt; ++a) {
+                const int c = idx[a];
+                ctl->alist[a] = c;
+                if (sty[c] == 0) ctl->ulist[nu++] = c;
+                else ctl->vlist[nv++] = c;
+            }
+            ctl->nc = cnt;
+            ctl->na = cnt;
+            ctl->nu = nu;
+            ctl->nv = nv;
+            ctl->exhausted = spos >= lim;
+            ctl->pos = spos;
+        }
+        return;
+    }
     if (tid < cnt) {
         // slot: j, k, type, index within the row (or ByElement segment),
         // screen flag, row i, position recorded in the trace
@@ -587,19 +634,18 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
             ctl->f_new = ctl->f + sf[kept];
         }
         if (!single) {
-            const bool elem = P.strategy == STMF_STRATEGY_BYELEMENT;
+            const bool elem = P.strategy == STMF_STRATEGY_BYELEMENT, mat = P.strategy == STMF_STRATEGY_BYMATRIX;
             if (kept >= 0) {
                 const int *cd = P.cand + 8 * kept;
                 ctl->f = ctl->f_new;          // exact value recomputed by the refresh
                 ctl->dirty_k = cd[1];
                 ctl->accepted += 1;
-                if (elem) {
-                    ctl->i = cd[5];
-                    ctl->pos = cd[6] + 1;     // ByElement: the scan goes on from the next element
-                }
+                if (elem || mat) ctl->i = cd[5];
+                if (elem) ctl->pos = cd[6] + 1;   // ByElement: the scan goes on from the next element
                 put_trace(ctl, cd[6], cd[0], cd[1], cd[2], ctl->f_new);
                 ctl->row_done = 1;
             } else if (ctl->exhausted) {
+                if (mat) ctl->i = -1;
                 if (!elem) put_trace(ctl, -1, -1, -1, -1, ctl->f);
                 ctl->row_done = 1;
             } else {
@@ -607,7 +653,9 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
                 ctl->row_done = 0;
             }
             if (ctl->row_done) {
-                if (elem) {
+                if (mat) {
+                    ctl->more = 0;            // ByMatrix: one iteration per sweep
+                } else if (elem) {
                     ctl->more = kept >= 0 && ctl->pos < P.m * P.n;
                     if (!ctl->more) {
                         ctl->i = -1;          // end of the sweep's scan
@@ -860,6 +908,10 @@ cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph)
 {
     if (P->sel == STMF_SEL_TD) {
         const cudaError_t e = launch_row_order(st, P);     // the row's own column order
+        if (e != cudaSuccess) return e;
+    }
+    if (P->strategy == STMF_STRATEGY_BYMATRIX) {
+        const cudaError_t e = launch_matrix_order(st, P);  // the iteration's order of all given elements
         if (e != cudaSuccess) return e;
     }
     k_row_begin<<<1, 1024, 0, st>>>(*P, in_graph, P->h_win);

@@ -117,7 +117,8 @@ void problem_free(stmf_problem *P)
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
                     P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
-                    P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg, P->cperm};
+                    P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg, P->cperm,
+                    P->tdr_seq, P->tdc_seq, P->skey, P->sval};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
@@ -453,11 +454,12 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (o.V0 && !o.U0) return fail(ctx, STMF_ERR_INVALID, "V0 needs U0");
     if (o.selection < STMF_SEL_TD_A || o.selection > STMF_SEL_SEQ)
         return fail(ctx, STMF_ERR_INVALID, "selection %d unknown", o.selection);
-    if (o.strategy != STMF_STRATEGY_BYROW && o.strategy != STMF_STRATEGY_BYELEMENT)
+    if (o.strategy < STMF_STRATEGY_BYROW || o.strategy > STMF_STRATEGY_BYMATRIX)
         return fail(ctx, STMF_ERR_INVALID, "strategy %d unknown", o.strategy);
-    const bool elem = o.strategy == STMF_STRATEGY_BYELEMENT;
-    if (elem && (o.perm || o.selection != STMF_SEL_TD_A))
-        return fail(ctx, STMF_ERR_INVALID, "the ByElement strategy takes no row permutation and no selection");
+    const bool elem = o.strategy == STMF_STRATEGY_BYELEMENT, mat = o.strategy == STMF_STRATEGY_BYMATRIX;
+    if ((elem || mat) && (o.perm || o.selection != STMF_SEL_TD_A))
+        return fail(ctx, STMF_ERR_INVALID, "the %s strategy takes no row permutation and no selection",
+                    elem ? "ByElement" : "ByMatrix");
     const int tr = m0 > n0;                 // Algorithm 3: a tall R is transposed
     const int m = tr ? n0 : m0, n = tr ? m0 : n0;
     std::vector<int> perm;
@@ -468,8 +470,8 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
             if (x < 0 || x >= m || seen[x]) return fail(ctx, STMF_ERR_INVALID, "perm is not a permutation of 0..%d", m - 1);
             seen[x] = 1;
         }
-    } else if (elem) {
-        perm.resize(m);                     // ByElement keeps the rows in their order
+    } else if (elem || mat) {
+        perm.resize(m);                     // ByElement and ByMatrix keep the rows in their order
         for (int s = 0; s < m; ++s) perm[s] = s;
     } else {
         random_permutation(m, o.seed, perm);
@@ -489,6 +491,14 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
             if (ea == cudaSuccess) ea = dalloc(&P->roworder, P->np);
         } else if (P->sel == STMF_SEL_TD_B) {
             ea = dalloc(&P->colarg, P->np);
+        }
+        if (mat && ea == cudaSuccess) {
+            P->nsort = matrix_sort_len(m, n);
+            P->coin_key = o.seed ^ 0x5A5A5A5A5A5A5A5Aull;
+            ea = dalloc(&P->tdr_seq, (size_t)m);
+            if (ea == cudaSuccess) ea = dalloc(&P->tdc_seq, (size_t)n);
+            if (ea == cudaSuccess) ea = dalloc(&P->skey, P->nsort);
+            if (ea == cudaSuccess) ea = dalloc(&P->sval, P->nsort);
         }
         if (ea != cudaSuccess) {
             problem_free(P);
@@ -545,6 +555,17 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
                                      d_bad);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // cp, cmin stay alive until the copies end
         if (d_cmin) cudaFree(d_cmin);
+    }
+    if (e == cudaSuccess && mat) {
+        // ByMatrix: the length of every iteration's order
+        unsigned long long *d_cnt = nullptr, cnt = 0;
+        e = cudaMalloc(&d_cnt, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = launch_count_given(st, P, d_cnt);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (d_cnt) cudaFree(d_cnt);
+        P->ngiven = (long long)cnt;
     }
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);

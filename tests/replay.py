@@ -90,3 +90,43 @@ def replay_byelement(R, M, r, gpu_trace, seed=0, picks=None, p=5, tol=1e-6):
     Vo[:, cp] = Vi
     U, V = (Vo.T.copy(), Ui.T.copy()) if tr else (Ui, Vo)
     return dict(U=U, V=V, f=f, divergences=divergences, transposed=tr, cperm=cp)
+
+
+def replay_bymatrix(R, M, r, gpu_trace, seed=0, picks=None, p=5, tol=1e-6):
+    """The lockstep replay for the ByMatrix method: one GPU record per
+    iteration (the kept element's position in the err order, or none); the
+    oracle runs the same iteration from its own state."""
+    import numpy as np
+    R = np.asarray(R, dtype=np.float64)
+    M = np.asarray(M, dtype=bool)
+    m0, n0 = R.shape
+    tr = m0 > n0
+    m = n0 if tr else m0
+    st = orc.prepare(R, M, r, perm=np.arange(m, dtype=np.int32), picks=picks, p=p, seed=seed)
+    Ri, Mi, Ui, Vi = st["R"], st["M"], st["U"], st["V"]
+    f = orc.error(Ri, Mi, Ui, Vi)
+    divergences = []
+    for rec in gpu_trace:
+        it, i, pos, j, k, typ, f_gpu = rec
+        U0_, V0_ = Ui.copy(), Vi.copy()
+        kept, fn, out, _ = orc.matrix_step(Ri, Mi, Ui, Vi, seed, it, f)
+        gpu_kept = pos >= 0
+        same = kept == gpu_kept and (not kept or tuple(out) == (pos, i, j, k, typ))
+        if same:
+            f = fn
+            assert abs(f_gpu - f) <= tol * max(f, 1e-30), (rec, f)
+            continue
+        f_old = f
+        f_orc = fn if kept else f_old
+        if gpu_kept:
+            fun = orc.fulf if typ == 0 else orc.furf
+            Ug, Vg, f_g = fun(Ri, Mi, U0_, V0_, i, j, k)
+        else:
+            Ug, Vg, f_g = U0_, V0_, f_old
+        scale = tol * max(f_old, 1e-30)
+        ok = abs(f_g - f_orc) <= scale or abs(f_g - f_old) <= scale or abs(f_orc - f_old) <= scale
+        assert ok, ("decision differs beyond tolerance", rec, out, kept, f_old, f_orc, f_g)
+        divergences.append((rec, out, f_old, f_orc, f_g))
+        Ui, Vi, f = Ug, Vg, f_g
+    U, V = orc.finish(m0, n0, st["transposed"], Ui, Vi, st["perm"])
+    return dict(U=U, V=V, f=f, divergences=divergences)
