@@ -10,7 +10,10 @@ it; the CUDA library never does.  It shares no code with the CUDA path.
 Every function cites the passage of the paper it follows; see the C file.
 Parity is pinned by ``tests/test_oracle_pins.py`` (closed forms, tropical
 identities, residuation optimality, exact recovery, brute force on tiny
-inputs, equivariances).  The quality of the final factorization against the
+inputs, equivariances), ``tests/test_oracle_selections.py`` (the TD_B, TD and
+SEQ selections), ``tests/test_oracle_byelement.py`` and
+``tests/test_oracle_bymatrix.py`` (the ByElement and ByMatrix strategies),
+with hand-computed examples under ``tests/golden/``.  The quality of the final factorization against the
 paper's own experiments is "parity unpinned": the paper prints no absolute
 errors for reproducible inputs.
 """

@@ -123,3 +123,16 @@ def test_unknown_selection_rejected_by_the_library():
     st = a.load().stmf_factorize(ctx.h, 8, 10, 2, Rg.data_ptr(), 10, None, 0, C.byref(o), U.data_ptr(),
                                  V.data_ptr(), None)
     assert st == 1 and b"selection" in a.load().stmf_last_error(ctx.h)
+
+
+@pytest.mark.parametrize("kw", [dict(selection="TD_B"), dict(selection="TD"), dict(selection="SEQ"),
+                                dict(strategy="ByElement"), dict(strategy="ByMatrix")])
+def test_fp16_screen_keeps_the_decisions_of_every_variant(kw):
+    """The FP16 screen drops only candidates that provably do not improve, so
+    with any selection or strategy precision 1 keeps precision 0's updates."""
+    R, M, _, _ = synth.uniform_planted(40, 64, 3, 0.01, 0.8, seed=71)
+    sweeps = 12 if kw.get("strategy") == "ByMatrix" else 2
+    a = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=sweeps, seed=5, trace_cap=4000, precision=0, **kw)
+    b = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=sweeps, seed=5, trace_cap=4000, precision=1, **kw)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert [t[:6] for t in a[3]] == [t[:6] for t in b[3]]
