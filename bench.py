@@ -54,7 +54,7 @@ ALU_PEAK_TOPS = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
 # for the kernel source it was taken on
 # k_delta DRAM bytes per launch (read + write), ncu capture of the gene
 # workload (profiles/k_delta_gene_1000x5000_r10.md), valid for this source
-EVAL_TRAFFIC = {"source_sha256_prefix": "e9a1757b1ea6495d", "bytes": 47.73e6, "workload": "gene"}
+EVAL_TRAFFIC = {"source_sha256_prefix": "b80a868a23c52aee", "bytes": 47.73e6, "workload": "gene"}
 
 
 def eval_traffic(workload_name):
