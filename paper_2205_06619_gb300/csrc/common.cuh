@@ -162,6 +162,7 @@ struct stmf_problem {
     double *tdr_seq, *tdc_seq;   // m, n: td_row, td_col summed in FP64 in index order
     unsigned long long *skey;    // nsort sort keys
     unsigned *sval;              // nsort: element q = i n + j, in the iteration's order after the sort
+    unsigned long long *scnt;    // slot counter of the keys
     unsigned long long coin_key; // key of the per-element coin (seed ^ 0x5A5A...5A)
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
@@ -206,7 +207,7 @@ cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int
 cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_row_order(cudaStream_t st, stmf_problem *P);
 // kernels_bymatrix.cu
-size_t matrix_sort_len(int m, int n);
+size_t matrix_sort_len(long long ngiven);
 cudaError_t launch_matrix_order(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_count_given(cudaStream_t st, const stmf_problem *P, unsigned long long *d_cnt);
 

@@ -7,11 +7,12 @@
 // equal err keeping the smaller q = i*n + j first; the iteration's windows
 // then walk that order.
 //
-// Sort: a bitonic network over the pairs (key, q), key = 0x7fff...f - the
-// FP64 bits of err (err >= 0, so its bits order like its value, and a larger
-// err gives a smaller key), UINT64_MAX for entries that are not given and for
-// the padding up to a power of two.  The pairs are unique, so the sorted
-// sequence is the one total order, whatever the network.  Tiles of
+// Sort: a bitonic network over the pairs (key, q) of the given elements,
+// key = 0x7fff...f - the FP64 bits of err (err >= 0, so its bits order like
+// its value, and a larger err gives a smaller key).  The pairs take slots in
+// any order (atomic counter) and the rest up to a power of two holds
+// UINT64_MAX keys.  The given pairs are unique, so the sorted sequence is the
+// one total order, whatever the network and the slots.  Tiles of
 // SORT_TILE pairs run their stages in shared memory; larger strides are
 // global passes, one launch each.
 #include "common.cuh"
@@ -54,12 +55,23 @@ __global__ void k_td_colsum_seq(const float *__restrict__ R, const float *__rest
     tdc[t] = acc;
 }
 
-__global__ void k_err_keys(const float *__restrict__ R, const float *__restrict__ P1, int ld, int m, int n,
-                           const double *__restrict__ tdr, const double *__restrict__ tdc, size_t nsort,
-                           unsigned long long *__restrict__ key, unsigned *__restrict__ val)
+// Every slot empty (UINT64_MAX) and the slot counter at 0.
+__global__ void k_clear_keys(size_t nsort, unsigned long long *__restrict__ key, unsigned long long *__restrict__ cnt)
 {
     const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nsort) return;
+    if (q < nsort) key[q] = KEY_NONE;
+    if (q == 0) *cnt = 0ull;
+}
+
+// One pair per given element, in the next free slot (one atomic per warp).
+__global__ void k_err_keys(const float *__restrict__ R, const float *__restrict__ P1, int ld, int m, int n,
+                           const double *__restrict__ tdr, const double *__restrict__ tdc,
+                           unsigned long long *__restrict__ key, unsigned *__restrict__ val,
+                           unsigned long long *__restrict__ cnt)
+{
+    const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool given = false;
     unsigned long long k = KEY_NONE;
     if (q < (size_t)m * n) {
         const int i = (int)(q / n), j = (int)(q - (size_t)i * n);
@@ -68,10 +80,20 @@ __global__ void k_err_keys(const float *__restrict__ R, const float *__restrict_
         if (x == x) {
             const double err = (tdr[i] + tdc[j]) - (double)fabsf(x - P1[e]);
             k = 0x7fffffffffffffffull - (unsigned long long)__double_as_longlong(err);
+            given = true;
         }
     }
-    key[q] = k;
-    val[q] = (unsigned)q;
+    const unsigned b = __ballot_sync(0xffffffffu, given);
+    if (!b) return;
+    const int leader = __ffs(b) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (unsigned long long)__popc(b));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (given) {
+        const unsigned long long slot = base + __popc(b & ((1u << lane) - 1u));
+        key[slot] = k;
+        val[slot] = (unsigned)q;
+    }
 }
 
 __device__ __forceinline__ bool pair_after(unsigned long long ka, unsigned va, unsigned long long kb, unsigned vb)
@@ -134,12 +156,12 @@ __global__ void k_bitonic_global(unsigned long long *__restrict__ key, unsigned 
 
 }  // namespace
 
-// Padded length of the ByMatrix sort: the next power of two >= m n, at least
-// one tile.
-size_t matrix_sort_len(int m, int n)
+// Padded length of the ByMatrix sort: the next power of two >= the number of
+// given entries, at least one tile.
+size_t matrix_sort_len(long long ngiven)
 {
     size_t len = SORT_TILE;
-    while (len < (size_t)m * n) len <<= 1;
+    while (len < (size_t)ngiven) len <<= 1;
     return len;
 }
 
@@ -153,9 +175,11 @@ cudaError_t launch_matrix_order(cudaStream_t st, stmf_problem *P)
     if (e != cudaSuccess) return e;
     k_td_colsum_seq<<<(P->n + 127) / 128, 128, 0, st>>>(P->R, P->P1, P->np, P->m, P->n, P->tdc_seq);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t ns = P->nsort;
-    k_err_keys<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(P->R, P->P1, P->np, P->m, P->n, P->tdr_seq, P->tdc_seq,
-                                                             ns, P->skey, P->sval);
+    const size_t ns = P->nsort, cells = (size_t)P->m * P->n;
+    k_clear_keys<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(ns, P->skey, P->scnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_err_keys<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(P->R, P->P1, P->np, P->m, P->n, P->tdr_seq,
+                                                                P->tdc_seq, P->skey, P->sval, P->scnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const unsigned tiles = (unsigned)(ns / SORT_TILE);
     k_bitonic_tile<<<tiles, SORT_THREADS, 0, st>>>(P->skey, P->sval, 2, SORT_TILE);

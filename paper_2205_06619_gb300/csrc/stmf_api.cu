@@ -118,7 +118,7 @@ void problem_free(stmf_problem *P)
                     P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
                     P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg, P->cperm,
-                    P->tdr_seq, P->tdc_seq, P->skey, P->sval};
+                    P->tdr_seq, P->tdc_seq, P->skey, P->sval, P->scnt};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->ctl_host) cudaFreeHost(P->ctl_host);
@@ -493,12 +493,10 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
             ea = dalloc(&P->colarg, P->np);
         }
         if (mat && ea == cudaSuccess) {
-            P->nsort = matrix_sort_len(m, n);
             P->coin_key = o.seed ^ 0x5A5A5A5A5A5A5A5Aull;
             ea = dalloc(&P->tdr_seq, (size_t)m);
             if (ea == cudaSuccess) ea = dalloc(&P->tdc_seq, (size_t)n);
-            if (ea == cudaSuccess) ea = dalloc(&P->skey, P->nsort);
-            if (ea == cudaSuccess) ea = dalloc(&P->sval, P->nsort);
+            if (ea == cudaSuccess) ea = dalloc(&P->scnt, 1);
         }
         if (ea != cudaSuccess) {
             problem_free(P);
@@ -566,6 +564,17 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (d_cnt) cudaFree(d_cnt);
         P->ngiven = (long long)cnt;
+        P->nsort = matrix_sort_len(P->ngiven);
+        if (e == cudaSuccess) {
+            cudaError_t ea = dalloc(&P->skey, P->nsort);
+            if (ea == cudaSuccess) ea = dalloc(&P->sval, P->nsort);
+            if (ea != cudaSuccess) {
+                if (d_bad) cudaFree(d_bad);
+                problem_free(P);
+                cudaGetLastError();
+                return fail(ctx, STMF_ERR_OOM, "ByMatrix order buffers: %s", cudaGetErrorString(ea));
+            }
+        }
     }
     int bad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
