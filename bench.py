@@ -34,6 +34,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -92,7 +93,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # raw samples: $STMF_CLOCKS_DIR if set, else the system temporary directory
+        d = os.environ.get("STMF_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, "clocks_bench_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:

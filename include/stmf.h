@@ -319,7 +319,7 @@ typedef struct {
 stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs,
                                    const stmf_options *opts, stmf_report *reports, int *tuned_windows);
 
-/* ---- Learned initialisation of U (a spec addition; the paper uses
+/* ---- Learned initialisation of U (an addition to the paper, which uses
  * Random Acol, Section "Comparison of strategies").  A row of R is summarised
  * by a 32-quantile sketch of its given entries centred on the row median; an
  * MLP 32 -> 128 -> 128 -> r (ReLU, BF16 weights, FP32 accumulation) maps the

@@ -1,4 +1,4 @@
-// Learned initialisation of U (a spec addition; the paper initialises
+// Learned initialisation of U (an addition to the paper, which initialises
 // with Random Acol).  A row of R is summarised by a 32-quantile sketch of its
 // given entries, centred on the row median; an MLP 32 -> 128 -> 128 -> r
 // (ReLU) maps the sketch to the row of U minus the median.  Weights are held

@@ -1,5 +1,5 @@
-"""Learned initialisation of U for FastSTMF (a spec addition; the paper
-initialises with Random Acol, which stays the fallback).
+"""Learned initialisation of U for FastSTMF (an addition to the paper, which
+initialises with Random Acol; Random Acol stays the fallback).
 
 Pipeline (every numeric step runs in the library's CUDA kernels):
   1. training data: the method itself factorizes many seeded gene-expression
