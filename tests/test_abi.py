@@ -114,3 +114,15 @@ def test_sweep_log_summarises_trace_records():
     log = api.sweep_log(trace)
     assert log == [{"sweep": 0, "rows": 3, "accepted": 2, "f": 8.5, "mean_kept_position": 3.0},
                    {"sweep": 1, "rows": 3, "accepted": 1, "f": 8.0, "mean_kept_position": 0.0}]
+
+
+def test_options_carry_selection_and_strategy():
+    """The binding writes the selection and strategy into the fields the
+    library reads (host-only: the struct is filled, nothing is launched)."""
+    from paper_2205_06619_gb300 import api
+    o, _ = api._options(3, selection="TD", strategy="ByElement")
+    assert (o.sweeps, o.selection, o.strategy) == (3, api.SELECTIONS["TD"], api.STRATEGIES["ByElement"])
+    o, _ = api._options(1, strategy="ByMatrix")
+    assert (o.selection, o.strategy) == (api.SELECTIONS["TD_A"], api.STRATEGIES["ByMatrix"])
+    # the two fields sit at the end of the C struct, after the MLP handle
+    assert api.Options.strategy.offset > api.Options.selection.offset > api.Options.mlp.offset
