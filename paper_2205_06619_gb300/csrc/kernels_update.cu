@@ -291,11 +291,11 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
 // sorted order of the given elements (kernels_bymatrix.cu); each element is
 // one candidate, F-ULF or F-URF by its coin, with k = A_ij; a window takes at
 // most STMF_WMAX / 2 of them (phase 1 holds at most that many of one type).
-// Otherwise each pair gives F-ULF (slot 2a) then F-URF (slot 2a+1), the order
-// in which Algorithm 3 tries them.  At the first window of a row the row histogram
-// (and TD_B's j0) is rebuilt.  Runs in a block of 1024 threads: at the start
-// of a row (k_row_begin) and after a window that neither kept a candidate
-// nor exhausted the row (k_select).
+// Otherwise each pair gives F-ULF (slot 2a) then F-URF (slot 2a+1), the
+// order in which Algorithm 3 tries them.  At the first window of a row the
+// row histogram (and TD_B's j0) is rebuilt.  Runs in a block of 1024
+// threads: at the start of a row (k_row_begin) and after a window that
+// neither kept a candidate nor exhausted the row (k_select).
 __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ctl, bool row_start)
 {
     __shared__ int sh[STMF_MAX_RANK];
@@ -492,7 +492,8 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
 }
 
 // Seeds: F-ULF slots get V'_k. from the column statistics, F-URF slots U'_.k
-// from the row statistics; the other factor of each slot (the residuation of
+// from the row statistics, for the slot's own row i (ByElement and ByMatrix
+// windows span rows); the other factor of each slot (the residuation of
 // phase 1, combined with atomic minima) starts at +inf.  grid.y = slot,
 // grid.x covers max(np, mp).
 __global__ void k_seed(stmf_problem P)
