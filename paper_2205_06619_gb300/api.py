@@ -363,9 +363,12 @@ def decode_trace(trace: np.ndarray):
 
 def sweep_log(trace):
     """Per-sweep summary of trace records (one JSON-ready dict per sweep, in
-    sweep order): rows visited, updates kept, the b-norm error after the
-    sweep, and the mean position of the kept candidates in their rows'
-    candidate order."""
+    sweep order): records ("rows": the rows visited for ByRow; the kept
+    updates plus the end-of-sweep record for ByElement; 1 per iteration for
+    ByMatrix, whose "sweep" is an iteration), updates kept, the b-norm error
+    after the sweep, and the mean position of the kept candidates (in their
+    row's order; ByElement: element positions i*n + j; ByMatrix: positions in
+    the err order)."""
     acc = {}
     for (sw, row, pos, j, k, typ, f) in trace:
         d = acc.setdefault(sw, {"sweep": sw, "rows": 0, "accepted": 0, "f": f, "pos_sum": 0})

@@ -114,6 +114,11 @@ def test_sweep_log_summarises_trace_records():
     log = api.sweep_log(trace)
     assert log == [{"sweep": 0, "rows": 3, "accepted": 2, "f": 8.5, "mean_kept_position": 3.0},
                    {"sweep": 1, "rows": 3, "accepted": 1, "f": 8.0, "mean_kept_position": 0.0}]
+    # ByElement records: kept updates at element positions, then the sweep's end record
+    trace = [(0, 0, 3, 3, 1, 0, 9.0), (0, 2, 17, 1, 0, 1, 7.0), (0, -1, -1, -1, -1, -1, 7.0),
+             (1, -1, -1, -1, -1, -1, 7.0)]
+    assert api.sweep_log(trace) == [{"sweep": 0, "rows": 3, "accepted": 2, "f": 7.0, "mean_kept_position": 10.0},
+                                    {"sweep": 1, "rows": 1, "accepted": 0, "f": 7.0, "mean_kept_position": None}]
 
 
 def test_options_carry_selection_and_strategy():
