@@ -436,6 +436,50 @@ stmf_status sweep_host(stmf_problem *P)
     return STMF_OK;
 }
 
+// PermC of the ByElement strategy: the columns of the packed, oriented R in
+// increasing order of their minimum given entry, equal minima keeping the
+// smaller column first (a stable sort of the n keys on the host); R is then
+// packed again through that order, which P->cperm keeps for the output.
+cudaError_t setup_permc(stmf_problem *P, cudaStream_t st, const float *R, int ldr, const uint32_t *mask,
+                        int ldm_words, int *d_bad)
+{
+    const int m = P->m, n = P->n;
+    float *d_cmin = nullptr;
+    std::vector<float> cmin(n);
+    std::vector<int> cp(n);
+    cudaError_t e = cudaMalloc(&d_cmin, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->cperm, sizeof(int) * n);
+    if (e == cudaSuccess) e = launch_col_min(st, P->R, P->np, m, n, d_cmin);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cmin.data(), d_cmin, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        for (int t = 0; t < n; ++t) cp[t] = t;
+        std::stable_sort(cp.begin(), cp.end(), [&](int a, int b) { return cmin[a] < cmin[b]; });
+        e = cudaMemcpyAsync(P->cperm, cp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess)
+        e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, P->transposed, P->perm, P->cperm, P->R, P->np,
+                                 P->mp, d_bad);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // cp and cmin stay alive until the copies end
+    if (d_cmin) cudaFree(d_cmin);
+    return e;
+}
+
+// The number of given entries of the packed R into P->ngiven (the length of
+// every ByMatrix iteration's order).
+cudaError_t count_given(stmf_problem *P, cudaStream_t st)
+{
+    unsigned long long *d_cnt = nullptr, cnt = 0;
+    cudaError_t e = cudaMalloc(&d_cnt, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_count_given(st, P, d_cnt);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d_cnt) cudaFree(d_cnt);
+    P->ngiven = (long long)cnt;
+    return e;
+}
+
 // Algorithm 3 preparation: orientation, permutation, packing, init.
 stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, int ldr, const uint32_t *mask,
                          int ldm_words, const stmf_options *opts, stmf_problem **out)
@@ -532,38 +576,9 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
     if (e == cudaSuccess) e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, tr, P->perm, nullptr, P->R,
                                                    P->np, P->mp, d_bad);
-    if (e == cudaSuccess && elem) {
-        // PermC: columns in increasing order of their minimum given entry,
-        // equal minima keeping the smaller column first; then pack again
-        float *d_cmin = nullptr;
-        std::vector<float> cmin(n);
-        std::vector<int> cp(n);
-        e = cudaMalloc(&d_cmin, sizeof(float) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&P->cperm, sizeof(int) * n);
-        if (e == cudaSuccess) e = launch_col_min(st, P->R, P->np, m, n, d_cmin);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(cmin.data(), d_cmin, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess) {
-            for (int t = 0; t < n; ++t) cp[t] = t;
-            std::stable_sort(cp.begin(), cp.end(), [&](int a, int b) { return cmin[a] < cmin[b]; });
-            e = cudaMemcpyAsync(P->cperm, cp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
-        }
-        if (e == cudaSuccess)
-            e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, tr, P->perm, P->cperm, P->R, P->np, P->mp,
-                                     d_bad);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // cp, cmin stay alive until the copies end
-        if (d_cmin) cudaFree(d_cmin);
-    }
+    if (e == cudaSuccess && elem) e = setup_permc(P, st, R, ldr, mask, ldm_words, d_bad);
     if (e == cudaSuccess && mat) {
-        // ByMatrix: the length of every iteration's order
-        unsigned long long *d_cnt = nullptr, cnt = 0;
-        e = cudaMalloc(&d_cnt, sizeof(unsigned long long));
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st);
-        if (e == cudaSuccess) e = launch_count_given(st, P, d_cnt);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (d_cnt) cudaFree(d_cnt);
-        P->ngiven = (long long)cnt;
+        e = count_given(P, st);
         P->nsort = matrix_sort_len(P->ngiven);
         if (e == cudaSuccess) {
             cudaError_t ea = dalloc(&P->skey, P->nsort);
