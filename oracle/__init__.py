@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         # -ffp-contract=off: no fused multiply-add may merge the rounded steps.
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                                "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -97,6 +97,9 @@ def lib():
         L.orc_matrix_step.argtypes = [i, i, i, i, P, P, P, P, u64, i64, P, P, P]
         L.orc_factorize_bymatrix.restype = i
         L.orc_factorize_bymatrix.argtypes = [i, i, i, i, P, P, i, d, P, i, u64, P, P, P, P, P, i64, P]
+        L.orc_rmse.argtypes = [i, i, i, i, P, P, P, P, P]
+        L.orc_set_threads.argtypes = [i]
+        L.orc_max_threads.restype = i
         _lib = L
     return _lib
 
@@ -115,6 +118,18 @@ def _m(mask):
 
 def _mode(mode):
     return MODES[mode]
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's parallel loops (0: all cores); returns
+    the count now in use.  Results do not depend on it (fixed sum orders)."""
+    L = lib()
+    L.orc_set_threads(int(n))
+    return L.orc_max_threads()
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()
 
 
 def splitmix64(key: int, c: int) -> int:
@@ -187,6 +202,17 @@ def furf(R, M, U, V, i, j, k, mode="fp32"):
     r = U.shape[1]
     f = lib().orc_furf(_mode(mode), m, n, r, _p(R), _p(M), _p(U), _p(V), i, j, k)
     return U, V, float(f)
+
+
+def rmse(R, M, U, V, mode="fp32"):
+    """(RMSE-A over the given entries, RMSE-P over the held-out entries with a
+    known value, |S_A|, |S_P|) of R against U (x) V (Section "Evaluation
+    metrics").  R holds the true values of the held-out entries (NaN: none)."""
+    R, M, U, V = _d(R), _m(M), _d(U), _d(V)
+    m, n = R.shape
+    out = np.empty(4)
+    lib().orc_rmse(_mode(mode), m, n, U.shape[1], _p(R), _p(M), _p(U), _p(V), _p(out))
+    return float(out[0]), float(out[1]), int(out[2]), int(out[3])
 
 
 def row_stats(R, M, U, V, i, mode="fp32"):

@@ -2,9 +2,11 @@
  * Oracle for FastSTMF (Omanovic, Oblak, Curk: "FastSTMF: Efficient tropical
  * matrix factorization algorithm for sparse data", arXiv 2205.06619).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded CPU
- * restatement of the method, written from the paper's definitions and
- * algorithms.  Only the tests, the package's smoke() check and the CPU
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow CPU restatement of
+ * the method, written from the paper's definitions and algorithms.  The
+ * loops over independent rows or columns may run on several host threads
+ * (OpenMP); every sum runs in a fixed order, so the results do not depend on
+ * the number of threads.  Only the tests, the package's smoke() check and the CPU
  * baseline leg of bench.py may load it.  It shares no code, header, table or
  * helper with the CUDA library, and the CUDA library never calls it.
  *
@@ -22,7 +24,7 @@
  * entry of R is given/observed), U is m x r, V is r x n.
  *
  * Readings of places where the paper is silent or ambiguous are marked
- * "Reading:" below; every one of them is also listed in the design notes.
+ * "Reading:" below.
  */
 #include <math.h>
 #include <stdint.h>
@@ -43,7 +45,30 @@ static double add_(int mode, double a, double b) { return rnd(mode, a + b); }
 static double sub_(int mode, double a, double b) { return rnd(mode, a - b); }
 static double div_(int mode, double a, double b) { return rnd(mode, a / b); }
 
-int orc_version(void) { return 1; }
+int orc_version(void) { return 2; }
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads of the parallel loops (0 or less: all the host's cores). */
+void orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
+#else
+    (void)nthreads;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Random draws.  SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) used as a
@@ -99,6 +124,7 @@ void orc_acol_picks(int n, int r, int p, uint64_t seed, int32_t *picks)
 void orc_maxplus(int mode, int m, int n, int r, const double *U, const double *V,
                  double *P1, int32_t *A, double *P2)
 {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < n; ++j) {
             double best = -INFINITY, second = -INFINITY;
@@ -124,6 +150,7 @@ int orc_residuate_v(int mode, int m, int n, const double *R, const uint8_t *M,
                     const double *u, double *v)
 {
     int empty = 0;
+#pragma omp parallel for schedule(static) reduction(+ : empty)
     for (int t = 0; t < n; ++t) {
         double best = INFINITY;
         int any = 0;
@@ -143,6 +170,7 @@ int orc_residuate_u(int mode, int m, int n, const double *R, const uint8_t *M,
                     const double *v, double *u)
 {
     int empty = 0;
+#pragma omp parallel for schedule(static) reduction(+ : empty)
     for (int s = 0; s < m; ++s) {
         double best = INFINITY;
         int any = 0;
@@ -161,12 +189,15 @@ int orc_residuate_u(int mode, int m, int n, const double *R, const uint8_t *M,
 /* Approximation error in the b-norm over the given entries (Section
  * "Evaluation metrics", b-norm = sum of absolute values):
  * f = sum over given (s,t) of |R_st - (U (x) V)_st|, recomputed from
- * scratch, summed in double in row-major order.                            */
+ * scratch, summed in double: each row in column order, then the rows in row
+ * order.                                                                    */
 double orc_error(int mode, int m, int n, int r, const double *R, const uint8_t *M,
                  const double *U, const double *V)
 {
-    double f = 0.0;
-    for (int s = 0; s < m; ++s)
+    double *rowsum = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < m; ++s) {
+        double fs = 0.0;
         for (int t = 0; t < n; ++t) {
             if (!M[(size_t)s * n + t]) continue;
             double best = -INFINITY;
@@ -174,9 +205,60 @@ double orc_error(int mode, int m, int n, int r, const double *R, const uint8_t *
                 double x = add_(mode, U[(size_t)s * r + l], V[(size_t)l * n + t]);
                 if (x > best) best = x;
             }
-            f += fabs(sub_(mode, R[(size_t)s * n + t], best));
+            fs += fabs(sub_(mode, R[(size_t)s * n + t], best));
         }
+        rowsum[s] = fs;
+    }
+    double f = 0.0;
+    for (int s = 0; s < m; ++s) f += rowsum[s];
+    free(rowsum);
     return f;
+}
+
+/* Root-mean-square errors of the approximation (Section "Evaluation
+ * metrics": RMSE of the training data, RMSE-A, and of the test data of the
+ * prediction task, RMSE-P; Section "Evaluation": 20% of the entries are
+ * masked uniformly at random and used as the test set):
+ *   RMSE_S = sqrt( (1/|S|) * sum over (s,t) in S of (R_st - (U (x) V)_st)^2 )
+ * with S_A = the given entries (M = 1) and S_P = the held-out entries (M = 0)
+ * whose true value is known (R_st is a number; a NaN marks an entry with no
+ * truth).  The product entries and the difference are rounded in the mode's
+ * precision like every other add / sub; squares and sums are in double,
+ * each row in column order, then the rows in row order.
+ * out = {RMSE-A, RMSE-P, |S_A|, |S_P|}; an empty set gives NaN.              */
+void orc_rmse(int mode, int m, int n, int r, const double *R, const uint8_t *M, const double *U,
+              const double *V, double *out)
+{
+    double *acc = (double *)malloc(sizeof(double) * 4 * (size_t)(m > 0 ? m : 1));
+#pragma omp parallel for schedule(static)
+    for (int s = 0; s < m; ++s) {
+        double sa = 0.0, sp = 0.0, na = 0.0, np = 0.0;
+        for (int t = 0; t < n; ++t) {
+            const double x = R[(size_t)s * n + t];
+            const int given = M[(size_t)s * n + t] != 0;
+            if (!given && x != x) continue;
+            double best = -INFINITY;
+            for (int l = 0; l < r; ++l) {
+                double y = add_(mode, U[(size_t)s * r + l], V[(size_t)l * n + t]);
+                if (y > best) best = y;
+            }
+            const double d = sub_(mode, x, best);
+            if (given) { sa += d * d; na += 1.0; }
+            else { sp += d * d; np += 1.0; }
+        }
+        acc[4 * (size_t)s + 0] = sa; acc[4 * (size_t)s + 1] = sp;
+        acc[4 * (size_t)s + 2] = na; acc[4 * (size_t)s + 3] = np;
+    }
+    double sa = 0.0, sp = 0.0, na = 0.0, np = 0.0;
+    for (int s = 0; s < m; ++s) {
+        sa += acc[4 * (size_t)s + 0]; sp += acc[4 * (size_t)s + 1];
+        na += acc[4 * (size_t)s + 2]; np += acc[4 * (size_t)s + 3];
+    }
+    free(acc);
+    out[0] = na > 0.0 ? sqrt(sa / na) : NAN;
+    out[1] = np > 0.0 ? sqrt(sp / np) : NAN;
+    out[2] = na;
+    out[3] = np;
 }
 
 static void get_col(int m, int r, const double *U, int k, double *u)

@@ -441,3 +441,58 @@ def test_fp32_mode_outputs_are_floats(orc):
     out = orc.factorize(R, M, 3, sweeps=1, seed=2)
     assert np.array_equal(out["U"], out["U"].astype(np.float32).astype(float))
     assert np.array_equal(out["V"], out["V"].astype(np.float32).astype(float))
+
+
+def test_oracle_results_do_not_depend_on_host_threads(orc):
+    """The parallel loops of the oracle sum in a fixed order: one thread and
+    all host threads give the same decisions, factors and errors bit for bit."""
+    w = synth.workload_small(seed=5)
+    R, M = w["R"][:50, :40], w["mask"][:50, :40]
+    try:
+        orc.set_threads(1)
+        a = orc.factorize(R, M, 3, sweeps=3, seed=9, trace_cap=200)
+        orc.set_threads(0)
+        b = orc.factorize(R, M, 3, sweeps=3, seed=9, trace_cap=200)
+    finally:
+        orc.set_threads(0)
+    assert np.array_equal(a["trace"], b["trace"]) and np.array_equal(a["f_hist"], b["f_hist"])
+    assert np.array_equal(a["U"], b["U"]) and np.array_equal(a["V"], b["V"])
+
+
+def eps_stop_case(f_hist, min_stop=2):
+    """A threshold for the convergence rule (Section "Comparison of
+    strategies": stop when a sweep changes the error by less than eps) that
+    the run with these errors crosses first at sweep s*, with a factor of at
+    least 2 between eps and every change it is compared with up to s*.
+    Returns (s*, eps) or None."""
+    d = np.abs(np.diff(np.asarray(f_hist, dtype=float)))   # d[s-1]: change of sweep s
+    for s in range(min_stop, len(d) + 1):
+        before = d[:s - 1].min()
+        if d[s - 1] * 4.0 <= before:
+            eps = np.sqrt(d[s - 1] * before) if d[s - 1] > 0 else before / 2.0
+            return s, float(eps)
+    return None
+
+
+def test_factorize_eps_stop(orc):
+    """Convergence rule (Section "Comparison of strategies"): the sweep loop
+    ends after the first sweep whose change of the error is below eps; that
+    sweep is kept, and nothing else about the run changes.  Checked against
+    the changes of a run without the rule, and on an exact start, where the
+    first sweep changes nothing and ends the run."""
+    R, M, _, _ = synth.uniform_planted(30, 44, 3, 0.01, 0.8, seed=31)
+    full = orc.factorize(R, M, 3, sweeps=10, seed=2, trace_cap=1000)
+    case = eps_stop_case(full["f_hist"])
+    assert case is not None
+    s_star, eps = case
+    stop = orc.factorize(R, M, 3, sweeps=10, eps=eps, seed=2, trace_cap=1000)
+    assert stop["sweeps"] == s_star
+    assert np.array_equal(stop["f_hist"], full["f_hist"][:s_star + 1])
+    short = orc.factorize(R, M, 3, sweeps=s_star, seed=2)
+    assert np.array_equal(stop["U"], short["U"]) and np.array_equal(stop["V"], short["V"])
+    # a larger threshold that every change falls below stops after sweep 1
+    one = orc.factorize(R, M, 3, sweeps=10, eps=10.0 * full["f_hist"][0], seed=2)
+    assert one["sweeps"] == 1
+    R2, M2, Us, _ = synth.dyadic_planted(9, 14, 3, 0.8, seed=13)
+    ex = orc.factorize(R2, M2, 3, sweeps=5, eps=1e-12, perm=np.arange(9, dtype=np.int32), U0=Us.astype(float))
+    assert ex["sweeps"] == 1 and np.all(ex["f_hist"] == 0.0)
