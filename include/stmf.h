@@ -31,8 +31,13 @@
  *     or has magnitude 2^60 or more: the evaluation keeps entries that are
  *     not given at a finite sentinel far above that range).  The text
  *     of the last error of a context is available from stmf_last_error().
- *     Device-side waits are bounded: a wait that runs out returns
- *     STMF_ERR_TIMEOUT and leaves the device usable.
+ *     Device-side loops are bounded: the sweep, row and window loops of a
+ *     factorization run as conditional nodes of a CUDA graph, driven by the
+ *     device; a row never needs more windows than its candidate order has
+ *     positions, nor a sweep more row visits than m n + 1.  Should a loop
+ *     pass its bound (a logic error), every loop stops, nothing more is
+ *     committed, and the call returns STMF_ERR_TIMEOUT; the context and the
+ *     device stay usable.  No kernel spin-waits.
  */
 #ifndef STMF_H
 #define STMF_H
@@ -51,7 +56,7 @@ typedef enum {
     STMF_ERR_INVALID = 1,  /* bad argument; nothing was launched             */
     STMF_ERR_CUDA = 2,     /* a CUDA runtime call failed                      */
     STMF_ERR_OOM = 3,      /* device workspace allocation failed              */
-    STMF_ERR_TIMEOUT = 4,  /* a bounded device-side wait ran out              */
+    STMF_ERR_TIMEOUT = 4,  /* a bound of the device-driven loops ran out      */
     STMF_ERR_INTERNAL = 5  /* an internal consistency check failed            */
 } stmf_status;
 
@@ -205,7 +210,9 @@ stmf_status stmf_maxplus(stmf_ctx *ctx, int m, int n, int r,
  * strategy"; Algorithm 3) over the given entries, from the product above:
  *   td_col[j]          = sum over given i of |R_ij - (U (x) V)_ij|   (FP64)
  *   colhist[j*r + l]   = #{given i : f(i,j) = l}                      (int32)
- *   *f_host            = sum over j of td_col[j]  (the b-norm error)   (HOST)
+ *   *f_host            = sum over j of td_col[j]  (the b-norm error)   (HOST),
+ *                        summed on the device in the fixed order of the
+ *                        factorization's own error
  * td_col, colhist device (either may be NULL); f_host may be NULL.  Uses a
  * device workspace owned by ctx (grown on demand). */
 stmf_status stmf_selection_stats(stmf_ctx *ctx, int m, int n, int r,
@@ -213,11 +220,28 @@ stmf_status stmf_selection_stats(stmf_ctx *ctx, int m, int n, int r,
                                  const float *U, int ldu, const float *V, int ldv,
                                  double *td_col, int32_t *colhist, double *f_host);
 
+/* RMSE-A and RMSE-P (Section "Evaluation metrics": the root-mean-square
+ * error of the approximation on the training data, RMSE-A, and on the test
+ * data of the prediction task, RMSE-P; Section "Evaluation": 20% of the
+ * entries are masked uniformly at random and form the test set):
+ *   RMSE_S = sqrt( (1/|S|) sum over (i,j) in S of (R_ij - (U (x) V)_ij)^2 )
+ * with S_A = the given entries (mask bit 1; every entry when mask is NULL)
+ * and S_P = the entries not given whose true value R holds (R_ij not NaN).
+ * (U (x) V)_ij and R_ij - (U (x) V)_ij are FP32, as in the factorization;
+ * squares and sums FP64 in a fixed order.  R (m x n, ld ldr), mask, U (m x r,
+ * ld ldu), V (r x n, ld ldv) device; out_host (host, 4 doubles) receives
+ * {RMSE-A, RMSE-P, |S_A|, |S_P|}, NaN for an empty set.  Uses the context's
+ * workspace (grown on demand) and synchronizes its stream. */
+stmf_status stmf_rmse(stmf_ctx *ctx, int m, int n, int r, const float *R, int ldr,
+                      const uint32_t *mask, int ldm_words, const float *U, int ldu,
+                      const float *V, int ldv, double *out_host);
+
 /* stmf_selection_stats without any allocation.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
  * when they call (a process whose device-memory budget is fixed at start-up,
  * or a loop that cannot pay for cudaMalloc's synchronisation).  Arguments,
- * layouts and results are those of stmf_selection_stats.  Its scratch is one
+ * layouts and results are those of stmf_selection_stats, bit for bit (the
+ * same kernels and the same fixed summation orders).  Its scratch is one
  * file-scope device array of STMF_NOALLOC_SCRATCH_BYTES that every GPU loading
  * the library holds until the process exits; a problem needs
  *   8 * (ceil(m/128) * n + n + 1) + 4 * ceil(m/128) * n * r  bytes,
@@ -302,6 +326,8 @@ typedef struct {
     float *V_out;                /* r x n, ld n                                      */
     uint64_t seed;               /* draws its permutation and Acol picks             */
     int sweeps;                  /* sweeps of this problem                           */
+    int32_t *trace;              /* HOST, nullable: this problem's trace records, as  */
+    int64_t trace_cap;           /* stmf_options.trace of a single call; capacity    */
 } stmf_batch_problem;
 
 /* Many independent FastSTMF problems (Algorithm 3 each) of uneven size and
@@ -313,7 +339,9 @@ typedef struct {
  * eps, select and window apply to every problem; window == 0 lets the
  * library's autotuner pick each problem's window from one timed sweep per size
  * class on scratch copies (cached in ctx).  reports (host, nprob entries) and
- * tuned_windows (host, nprob ints) are nullable.  Set-up (allocation,
+ * tuned_windows (host, nprob ints) are nullable.  A problem whose trace is set
+ * receives up to trace_cap records of its row visits (the records of
+ * stmf_factorize; report[i].trace_records counts those written).  Set-up (allocation,
  * initialisation) runs before the launch; report[i].seconds is the wall time
  * of the single launch. */
 stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs,
@@ -363,7 +391,14 @@ void stmf_struct_sizes(size_t *options, size_t *report, size_t *batch_problem);
  * each).  mode 0: 1:1 FADD/FMNMX; 1: FADD only; 2: FMNMX only;
  * 3: packed half2 HADD2/HMNMX2 (two operations per lane); 4: packed
  * FP32x2 adds only; 5: one packed FP32x2 add then two scalar FMNMX (1:1 mix
- * with the additions packed).  Uses the context's stream and synchronizes it. */
+ * with the additions packed).  Modes 6 and 7 run the instruction mixes of
+ * the window evaluation's two passes and count their algorithmic operations
+ * per given entry and candidate (the units the benchmark reports): 6, the
+ * error-change pass (per two entries a packed add u + v, two FMNMX for
+ * max(E, x), a packed sub P1 - max and a packed accumulation: 4 operations
+ * per entry); 7, the residuation pass (per two entries two FADD for R - w
+ * and one three-input minimum: 2 operations per entry).  Uses the context's
+ * stream and synchronizes it. */
 stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops);
 
 #ifdef __cplusplus

@@ -24,7 +24,7 @@ EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", 
            "stmf_selection_stats", "stmf_problem_create", "stmf_problem_destroy", "stmf_update_U",
            "stmf_update_V", "stmf_problem_get", "stmf_factorize", "stmf_factorize_begin",
            "stmf_factorize_run", "stmf_factorize_end", "stmf_default_options", "stmf_struct_sizes",
-           "stmf_peak_addmax",
+           "stmf_peak_addmax", "stmf_rmse",
            "stmf_selection_stats_noalloc", "stmf_factorize_batched", "stmf_row_sketch", "stmf_mlp_param_count",
            "stmf_mlp_create", "stmf_mlp_destroy", "stmf_mlp_get_params", "stmf_mlp_forward", "stmf_mlp_gradient",
            "stmf_mlp_train_step"]
@@ -67,7 +67,7 @@ def _selection(name):
 class BatchProblem(C.Structure):
     _fields_ = [("m", C.c_int), ("n", C.c_int), ("r", C.c_int), ("R", C.c_void_p), ("ldr", C.c_int),
                 ("mask", C.c_void_p), ("ldm_words", C.c_int), ("U_out", C.c_void_p), ("V_out", C.c_void_p),
-                ("seed", C.c_uint64), ("sweeps", C.c_int)]
+                ("seed", C.c_uint64), ("sweeps", C.c_int), ("trace", C.c_void_p), ("trace_cap", C.c_int64)]
 
 
 class Report(C.Structure):
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
     L.stmf_maxplus.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, i, P]
     L.stmf_selection_stats.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, P, C.POINTER(d)]
     L.stmf_selection_stats_noalloc.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, P, P, C.POINTER(d)]
+    L.stmf_rmse.argtypes = [P, i, i, i, P, i, P, i, P, i, P, i, C.POINTER(d)]
     L.stmf_problem_create.argtypes = [P, i, i, i, P, i, P, i, P, C.POINTER(Options), C.POINTER(P)]
     L.stmf_problem_destroy.argtypes = [P]
     L.stmf_problem_destroy.restype = None
@@ -257,6 +258,20 @@ def selection_stats(R, U, V, mask_words=None):
                                           _ptr(U), U.stride(0), _ptr(V), V.stride(0), _ptr(td), _ptr(ch),
                                           C.byref(f)))
     return td, ch, f.value
+
+
+def rmse(R, U, V, mask_words=None):
+    """(RMSE-A, RMSE-P, |S_A|, |S_P|) of R against U (x) V on the device
+    (stmf_rmse): the given entries, and the held-out ones whose true value R
+    holds (NaN: none)."""
+    _check_f32(R, "R"); _check_f32(U, "U"); _check_f32(V, "V")
+    m, n = R.shape
+    ctx = context()
+    out = (C.c_double * 4)()
+    ldm = mask_words.shape[1] if mask_words is not None else 0
+    ctx.check(load().stmf_rmse(ctx.h, m, n, U.shape[1], _ptr(R), R.stride(0), _ptr(mask_words), ldm, _ptr(U),
+                               U.stride(0), _ptr(V), V.stride(0), out))
+    return out[0], out[1], int(out[2]), int(out[3])
 
 
 def selection_stats_noalloc(R, U, V, mask_words=None, td_col=None, colhist=None):
@@ -417,8 +432,10 @@ def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0, mlp=No
     """Many independent problems in one device launch (stmf_factorize_batched).
 
     problems: list of dicts with R (float32 CUDA m x n), mask_words (or None),
-    rank, sweeps, seed.  window=0 lets the library's autotuner choose each
-    problem's window.  Returns (list of (U, V, report dict), tuned windows)."""
+    rank, sweeps, seed and optionally trace_cap.  window=0 lets the library's
+    autotuner choose each problem's window.  Returns (list of (U, V, report
+    dict), tuned windows); a problem with trace_cap > 0 gets its decoded trace
+    records in report["trace"]."""
     torch = _torch()
     ctx = context()
     n = len(problems)
@@ -432,15 +449,23 @@ def factorize_batched(problems, window=0, select=0, eps=0.0, precision=0, mlp=No
         U = torch.empty((m, r), device=R.device, dtype=torch.float32)
         V = torch.empty((r, nn), device=R.device, dtype=torch.float32)
         mw = pr.get("mask_words")
+        cap = int(pr.get("trace_cap", 0))
+        tr = np.zeros((cap, STMF_TRACE_INTS), np.int32) if cap else None
         arr[q] = BatchProblem(m, nn, r, R.data_ptr(), R.stride(0), 0 if mw is None else mw.data_ptr(),
                               0 if mw is None else mw.shape[1], U.data_ptr(), V.data_ptr(), pr.get("seed", 0),
-                              pr.get("sweeps", 1))
-        outs.append((U, V))
+                              pr.get("sweeps", 1), 0 if tr is None else tr.ctypes.data, cap)
+        outs.append((U, V, tr))
     o, keep = _options(0, eps, window, select, precision, mlp=mlp, selection=selection, strategy=strategy)
     reps = (Report * max(n, 1))()
     tuned = (C.c_int * max(n, 1))()
     ctx.check(load().stmf_factorize_batched(ctx.h, n, arr, C.byref(o), reps, tuned))
-    return [(U, V, reps[q].as_dict()) for q, (U, V) in enumerate(outs)], [tuned[q] for q in range(n)]
+    res = []
+    for q, (U, V, tr) in enumerate(outs):
+        rep = reps[q].as_dict()
+        if tr is not None:
+            rep["trace"] = decode_trace(tr[:min(len(tr), rep["trace_records"])])
+        res.append((U, V, rep))
+    return res, [tuned[q] for q in range(n)]
 
 
 def row_sketch(R, mask_words=None):

@@ -28,6 +28,7 @@
 // every error change the evaluation forms there is exactly 0 (see k_delta).
 #define STMF_SENTINEL 8.5070592e37f                 // 2^126
 #define STMF_DELTA_MAX_BLOCKS_PER_SM 8   // capacity of the phase-2 partials, per SM
+#define STMF_DELTA_GROUP 32              // phase-2 blocks per second-stage group
 
 static inline int stmf_roundup(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -130,6 +131,11 @@ struct stmf_ctl {
     long long screened;// candidates the screen proved non-improving (cumulative)
     int tdb_j0;        // TD_B: column of the largest td(i, t) of the current row
     int more;          // the row loop goes on (ByRow: rows left; ByElement: elements left in the sweep)
+    // Bounds of the device-driven loops (conditional graph nodes): a correct
+    // run never reaches them; past one the loops end with err =
+    // STMF_ERR_TIMEOUT and nothing more is committed.
+    long long win_row, win_cap;     // windows of the current row (ByElement: segment) / their bound
+    long long rows_sweep, row_cap;  // row visits (segments) of the current sweep / their bound
 };
 
 struct stmf_problem {
@@ -168,6 +174,8 @@ struct stmf_problem {
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
     float2 *part;      // STMF_WMAX x (phase-2 blocks) partial changes, float-float (hi, lo)
+    float2 *gpart;     // STMF_WMAX x (phase-2 groups) group sums of the partials, float-float
+    unsigned *grp_cnt; // per group: blocks of the running phase-2 launch that have finished (0 between launches)
     double *fc;        // STMF_WMAX candidate errors
     // FP16 screening (precision 1; all NULL otherwise)
     int precision;
@@ -205,6 +213,11 @@ int planes_nparts(int m);
 cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int *chpart, int nparts,
                                 int ldpart, int n, int r, double *tdcol, int *colhist);
 cudaError_t launch_refresh_planes(cudaStream_t st, stmf_problem *P);
+cudaError_t launch_error_sum(cudaStream_t st, const double *tdcol, int n, double *out);   // fixed-order sum
+int rmse_blocks(int m, int num_sms);
+cudaError_t launch_rmse(cudaStream_t st, int num_sms, int m, int n, int r, const float *R, int ldr,
+                        const uint32_t *mask, int ldm, const float *U, int ldu, const float *V, int ldv,
+                        double *part, double *out);
 cudaError_t launch_row_order(cudaStream_t st, stmf_problem *P);
 // kernels_bymatrix.cu
 size_t matrix_sort_len(long long ngiven);
@@ -218,6 +231,7 @@ cudaError_t launch_pack_oriented(cudaStream_t st, const float *R, int ldr, const
                                  int m, int n, int transposed, const int *perm, const int *cperm, float *Rp,
                                  int ldp, int mp, int *bad);
 cudaError_t launch_col_min(cudaStream_t st, const float *Rp, int ldp, int m, int n, float *cmin);
+cudaError_t launch_permc_order(cudaStream_t st, const float *cmin, int n, int *rank, int *cperm);
 cudaError_t launch_unorient(cudaStream_t st, const stmf_problem *P, int transposed, const int *perm, const int *cperm,
                             float *U_out, float *V_out);
 cudaError_t launch_empty_rows(cudaStream_t st, const float *X, int ldx, int rows, int *nempty);
@@ -236,7 +250,7 @@ cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph);
 cudaError_t launch_res(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_delta(cudaStream_t st, stmf_problem *P);
 int delta_grid(const stmf_problem *P);
-int delta_parts(const stmf_problem *P);   // phase-2 partials per candidate
+int delta_parts(const stmf_problem *P);   // phase-2 group partials per candidate (what the decision sums)
 int delta_depth(const stmf_problem *P);
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);
@@ -258,3 +272,4 @@ int mlp_rank(const stmf_mlp *M);
 
 // peak.cu
 cudaError_t launch_peak(cudaStream_t st, int mode, int iters, int blocks, float *sink);
+double peak_ops(int mode, int iters, int blocks);

@@ -357,6 +357,79 @@ __global__ void __launch_bounds__(1024) k_scatter_f(const double *__restrict__ t
     }
 }
 
+// f = sum_j td_col[j] with k_scatter_f's fixed order (strided per thread,
+// then a fixed tree), written to *out: the error of stmf_selection_stats and
+// of its allocation-free form, equal bit for bit to the factorization's.
+__global__ void __launch_bounds__(1024) k_error_sum(const double *__restrict__ tdcol, int n, double *__restrict__ out)
+{
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += 1024) s += tdcol[j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 512; o; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// RMSE-A / RMSE-P (Section "Evaluation metrics"): squared residuals of the
+// approximation over the given entries and over the held-out entries with a
+// known value (R not NaN).  P = max_l (U_sl + V_lt) and d = R - P in FP32, as
+// in the factorization; d^2 and the sums in FP64.  Block b takes rows b,
+// b + grid, ...; each thread's columns in order, then a fixed tree over the
+// block: part[4 b + {0, 1, 2, 3}] = (sum_A, sum_P, |S_A|, |S_P|).
+constexpr int RMSE_THREADS = 256;
+__global__ void __launch_bounds__(RMSE_THREADS) k_rmse_part(int m, int n, int r, const float *__restrict__ R, int ldr,
+                                                            const uint32_t *__restrict__ mask, int ldm,
+                                                            const float *__restrict__ U, int ldu,
+                                                            const float *__restrict__ V, int ldv,
+                                                            double *__restrict__ part)
+{
+    __shared__ float su[STMF_MAX_RANK];
+    __shared__ double red[4][RMSE_THREADS];
+    const int tid = threadIdx.x;
+    double sa = 0.0, sp = 0.0, na = 0.0, np = 0.0;
+    for (int s = blockIdx.x; s < m; s += gridDim.x) {
+        __syncthreads();
+        if (tid < r) su[tid] = U[(size_t)s * ldu + tid];
+        __syncthreads();
+        for (int t = tid; t < n; t += RMSE_THREADS) {
+            const float x = R[(size_t)s * ldr + t];
+            const bool given = mask ? ((mask[(size_t)s * ldm + (t >> 5)] >> (t & 31)) & 1u) : true;
+            if (!given && x != x) continue;
+            float p = -INFINITY;
+            for (int l = 0; l < r; ++l) p = fmaxf(p, su[l] + V[(size_t)l * ldv + t]);
+            const double d = (double)(x - p);
+            if (given) { sa += d * d; na += 1.0; }
+            else { sp += d * d; np += 1.0; }
+        }
+    }
+    red[0][tid] = sa; red[1][tid] = sp; red[2][tid] = na; red[3][tid] = np;
+    __syncthreads();
+    for (int o = RMSE_THREADS / 2; o; o >>= 1) {
+        if (tid < o)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q][tid] += red[q][tid + o];
+        __syncthreads();
+    }
+    if (tid < 4) part[4 * (size_t)blockIdx.x + tid] = red[tid][0];
+}
+
+// Sums the block partials in block order; out = (RMSE-A, RMSE-P, |S_A|, |S_P|).
+__global__ void k_rmse_final(const double *__restrict__ part, int nb, double *__restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < nb; ++b)
+        for (int q = 0; q < 4; ++q) a[q] += part[4 * (size_t)b + q];
+    out[0] = a[2] > 0.0 ? sqrt(a[0] / a[2]) : (double)NAN;
+    out[1] = a[3] > 0.0 ? sqrt(a[1] / a[3]) : (double)NAN;
+    out[2] = a[2];
+    out[3] = a[3];
+}
+
 // TD selection (Section "The ByRow strategy"): the key of column t for row
 // i = ctl->i is its tropical distance td(i,t) = |R_it - P1_it| where R_it is
 // given, else 0 (the window skips those columns).  Ranked like the column
@@ -457,6 +530,24 @@ cudaError_t launch_td_finalize2(cudaStream_t st, const double *tdpart, const int
                                 int ldpart, int n, int r, double *tdcol, int *colhist)
 {
     k_td_finalize<<<(n + 255) / 256, 256, 0, st>>>(tdpart, chpart, nparts, ldpart, n, r, tdcol, colhist, nullptr);
+    return cudaGetLastError();
+}
+
+int rmse_blocks(int m, int num_sms) { return m < 4 * num_sms ? m : 4 * num_sms; }
+
+cudaError_t launch_rmse(cudaStream_t st, int num_sms, int m, int n, int r, const float *R, int ldr,
+                        const uint32_t *mask, int ldm, const float *U, int ldu, const float *V, int ldv,
+                        double *part, double *out)
+{
+    const int nb = rmse_blocks(m, num_sms);
+    k_rmse_part<<<nb, RMSE_THREADS, 0, st>>>(m, n, r, R, ldr, mask, ldm, U, ldu, V, ldv, part);
+    k_rmse_final<<<1, 32, 0, st>>>(part, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_error_sum(cudaStream_t st, const double *tdcol, int n, double *out)
+{
+    k_error_sum<<<1, 1024, 0, st>>>(tdcol, n, out);
     return cudaGetLastError();
 }
 

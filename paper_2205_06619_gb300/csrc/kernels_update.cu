@@ -107,6 +107,43 @@ __global__ void __launch_bounds__(1024) k_col_min(const float *__restrict__ Rp, 
     }
 }
 
+// PermC order (ByElement): the columns by increasing minimum given entry,
+// equal minima keeping the smaller column first.  Keys are the minima mapped
+// to unsigned integers that order like the floats (-0 counts as +0, as in a
+// float comparison); rank_t = #{e : key_e < key_t} + #{e < t : key_e = key_t},
+// counted over a 2-D grid (columns x key chunks held in shared memory).
+constexpr int PERMC_CHUNK = 512;
+__device__ __forceinline__ unsigned ordered_key(float x)
+{
+    const unsigned b = __float_as_uint(x + 0.0f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(256) k_permc_rank(const float *__restrict__ cmin, int n, int *__restrict__ rank)
+{
+    __shared__ unsigned sk[PERMC_CHUNK];
+    const int t = blockIdx.x * 256 + threadIdx.x;
+    const int base = blockIdx.y * PERMC_CHUNK;
+    const int len = min(PERMC_CHUNK, n - base);
+    for (int e = threadIdx.x; e < len; e += 256) sk[e] = ordered_key(cmin[base + e]);
+    __syncthreads();
+    if (t >= n) return;
+    const unsigned kt = ordered_key(cmin[t]);
+    const int tl = t - base;   // chunk-local index of t (may be outside the chunk)
+    int cnt = 0;
+    for (int e = 0; e < len; ++e) {
+        const unsigned x = sk[e];
+        cnt += (x < kt) | ((x == kt) & (e < tl));
+    }
+    if (cnt) atomicAdd(&rank[t], cnt);
+}
+
+__global__ void k_permc_scatter(const int *__restrict__ rank, int n, int *__restrict__ cperm)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) cperm[rank[t]] = t;
+}
+
 // Number of rows among the first `rows` that hold no given (non-NaN) entry.
 __global__ void k_empty_rows(const float *__restrict__ X, int ldx, int rows, int *__restrict__ nempty)
 {
@@ -565,7 +602,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         stmf_ff x = {0.f, 0.f};
         const bool live = c < nc && !P.cand[8 * c + 4];    // dropped: proved non-improving by the FP16 screen
         if (live) {
-            const float2 *part = P.part + (size_t)c * nblk;
+            const float2 *part = P.gpart + (size_t)c * nblk;
             stmf_ff x0 = {0.f, 0.f}, x1 = x0, x2 = x0, x3 = x0;
             int b = sub;
             for (; b + 48 < nblk; b += 64) {
@@ -610,7 +647,21 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         if (lane == 0) skept = kept;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !single && ++ctl->win_row > ctl->win_cap) {
+        // more windows in this row than its candidates allow: stop every loop
+        ctl->err = STMF_ERR_TIMEOUT;
+        skept = -1;
+    }
+    __syncthreads();
+    if (tid == 0 && ctl->err == STMF_ERR_TIMEOUT && !single) {
+        ctl->row_done = 1;
+        ctl->more = 0;
+        if (in_graph) {
+            cudaGraphSetConditional(h_win, 0u);
+            cudaGraphSetConditional(h_dirty, 0u);
+            cudaGraphSetConditional(h_row, 0u);
+        }
+    } else if (tid == 0) {
         const int kept = skept;
         ctl->issued += nc;
         ctl->windows += 1;
@@ -684,7 +735,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         }
     }
     __syncthreads();
-    const int kept = skept;
+    const int kept = ctl->err == STMF_ERR_TIMEOUT ? -1 : skept;
     if (kept >= 0) {
         const int k = P.cand[8 * kept + 1];
         for (int s = tid; s < P.m; s += 1024) P.U[(size_t)s * P.r + k] = P.Uc[(size_t)kept * P.mp + s];
@@ -699,21 +750,32 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
 
 // Start of a row: row state reset and the row's first window; in a graph,
 // opens the window loop.
-__global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_win)
+__global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_win,
+                                                    cudaGraphConditionalHandle h_row)
 {
     __shared__ stmf_ctl sctl;
     ctl_load(sctl, P.ctl);
     stmf_ctl *ctl = &sctl;
+    __shared__ int sstop;
     if (threadIdx.x == 0) {
         if (P.strategy != STMF_STRATEGY_BYELEMENT) ctl->pos = 0;   // ByElement: the scan position carries on
         ctl->ncand_row = 0;
         ctl->wj = ctl->wj0;
         ctl->kept = 0;
         ctl->row_done = 0;
-        if (in_graph) cudaGraphSetConditional(h_win, 1u);
+        ctl->win_row = 0;
+        // more row visits in this sweep than the sweep has rows (segments):
+        // stop every loop
+        if (++ctl->rows_sweep > ctl->row_cap) ctl->err = STMF_ERR_TIMEOUT;
+        sstop = ctl->err == STMF_ERR_TIMEOUT;
+        if (sstop) { ctl->row_done = 1; ctl->more = 0; }
+        if (in_graph) {
+            cudaGraphSetConditional(h_win, sstop ? 0u : 1u);
+            if (sstop) cudaGraphSetConditional(h_row, 0u);
+        }
     }
     __syncthreads();
-    build_window(P, ctl, true);
+    if (!sstop) build_window(P, ctl, true);
     ctl_store(P.ctl, sctl);
 }
 
@@ -725,7 +787,8 @@ __global__ void k_sweep_begin(stmf_problem P, int in_graph, cudaGraphConditional
     stmf_ctl *ctl = P.ctl;
     ctl->i = 0;
     ctl->pos = 0;
-    ctl->more = ctl->m > 0;
+    ctl->rows_sweep = 0;
+    ctl->more = ctl->m > 0 && ctl->err != STMF_ERR_TIMEOUT;
     if (in_graph) {
         cudaGraphSetConditional(h_row, ctl->more ? 1u : 0u);
         cudaGraphSetConditional(h_dirty, ctl->dirty_k != -2 ? 1u : 0u);
@@ -750,7 +813,7 @@ __global__ void k_sweep_end(stmf_problem P, cudaGraphConditionalHandle h_sweep)
     const double d = ctl->f_prev - ctl->f;
     const bool converged = ctl->eps > 0.0 && d < ctl->eps && -d < ctl->eps;
     ctl->f_prev = ctl->f;
-    cudaGraphSetConditional(h_sweep, (ctl->sweep < ctl->sweep_target && !converged) ? 1u : 0u);
+    cudaGraphSetConditional(h_sweep, (ctl->sweep < ctl->sweep_target && !converged && !ctl->err) ? 1u : 0u);
 }
 
 // One explicit candidate (stmf_update_U / stmf_update_V): slot 0.
@@ -815,6 +878,18 @@ cudaError_t launch_unorient(cudaStream_t st, const stmf_problem *P, int transpos
     const int tot = max(P->m * P->r, P->r * P->n);
     k_unorient<<<(tot + 255) / 256, 256, 0, st>>>(P->U, P->V, P->m, P->n, P->r, P->np, transposed, perm, cperm,
                                                   U_out, V_out);
+    return cudaGetLastError();
+}
+
+// cperm = the PermC order of the n column minima cmin (device); rank is n
+// ints of scratch.
+cudaError_t launch_permc_order(cudaStream_t st, const float *cmin, int n, int *rank, int *cperm)
+{
+    cudaError_t e = cudaMemsetAsync(rank, 0, sizeof(int) * (size_t)n, st);
+    if (e != cudaSuccess) return e;
+    dim3 grid((n + 255) / 256, (n + PERMC_CHUNK - 1) / PERMC_CHUNK);
+    k_permc_rank<<<grid, 256, 0, st>>>(cmin, n, rank);
+    k_permc_scatter<<<(n + 255) / 256, 256, 0, st>>>(rank, n, cperm);
     return cudaGetLastError();
 }
 
@@ -915,7 +990,7 @@ cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph)
         const cudaError_t e = launch_matrix_order(st, P);  // the iteration's order of all given elements
         if (e != cudaSuccess) return e;
     }
-    k_row_begin<<<1, 1024, 0, st>>>(*P, in_graph, P->h_win);
+    k_row_begin<<<1, 1024, 0, st>>>(*P, in_graph, P->h_win, P->h_row);
     return cudaGetLastError();
 }
 

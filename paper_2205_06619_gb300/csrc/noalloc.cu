@@ -25,21 +25,6 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[STMF_NOALLOC_SCRATCH_B
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[STMF_NOALLOC_MAX_DEVICES];
 
-// f = sum over j of td_col[j] in a fixed order (one block).
-__global__ void __launch_bounds__(1024) k_noalloc_sum(const double *__restrict__ td, int n, double *__restrict__ out)
-{
-    __shared__ double red[1024];
-    double s = 0.0;
-    for (int j = threadIdx.x; j < n; j += 1024) s += td[j];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 512; o; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = red[0];
-}
-
 stmf_status nfail(stmf_ctx *ctx, stmf_status st, const char *msg)
 {
     if (ctx) snprintf(ctx->err, sizeof(ctx->err), "%s", msg);
@@ -105,8 +90,7 @@ extern "C" stmf_status stmf_selection_stats_noalloc(stmf_ctx *ctx, int m, int n,
     double *tdout = td_col ? td_col : tdtmp;
     if (e == cudaSuccess) e = launch_td_finalize2(st, tdpart, chpart, (int)nparts, n, n, r, tdout, colhist);
     if (e == cudaSuccess && f_host) {
-        k_noalloc_sum<<<1, 1024, 0, st>>>(tdout, n, fdev);
-        e = cudaGetLastError();
+        e = launch_error_sum(st, tdout, n, fdev);
         if (e == cudaSuccess) e = cudaMemcpyAsync(f_host, fdev, sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }

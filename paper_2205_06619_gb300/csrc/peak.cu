@@ -6,7 +6,19 @@
 //   mode 4: packed FP32x2 adds only (add.rn.f32x2: 2 operations per lane)
 //   mode 5: one packed FP32x2 add then two scalar FMNMX (the add:max = 1:1
 //           mix of a max-plus loop with its additions packed)
-// Operations counted: one per FP32 lane operation (two per packed instruction).
+//   mode 6: the instruction mix of the error-change pass (k_delta) per two
+//           entries of a candidate: x = u + v (packed add), the two maxima
+//           max(E, x) (FMNMX), the change P1 - max (packed sub) and its
+//           accumulation (packed add)
+//   mode 7: the instruction mix of the residuation pass (k_res) per two
+//           entries of a candidate: two subtractions R - w (FADD) and one
+//           three-input minimum that folds both into the running minimum
+// Operations counted: modes 0-5, one per FP32 lane operation (two per packed
+// instruction); modes 6 and 7, the algorithmic operations of the pass they
+// mirror per entry and candidate (4 for mode 6: add, max, sub, accumulate;
+// 2 for mode 7: sub, min), so that a kernel's achieved rate in those units
+// divides by them directly.  Every chain is loop-carried, so no instruction
+// can be hoisted out of the loop.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -78,7 +90,75 @@ __global__ void __launch_bounds__(256) k_peak_f32x2(int iters, float b, float c,
     if (s == 12345.678f) sink[threadIdx.x] = s;
 }
 
+// mode 6: 8 independent chains; each step is the per-pair sequence of the
+// error-change pass, with the running sum fed back as the next step's u.
+__global__ void __launch_bounds__(256) k_peak_delta(int iters, float e0, float *sink)
+{
+    unsigned long long acc[8], C, Pp;
+    const float E0 = e0 + threadIdx.x * 1e-6f, E1 = e0 - 1e-3f;
+    asm volatile("mov.b64 %0, {%1, %2};" : "=l"(C) : "f"(1e-7f), "f"(-1e-7f));
+    asm volatile("mov.b64 %0, {%1, %2};" : "=l"(Pp) : "f"(2.0f), "f"(3.0f));
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        asm volatile("mov.b64 %0, {%1, %2};" : "=l"(acc[q]) : "f"(0.1f * q), "f"(-0.1f * q));
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            unsigned long long x, mp, d;
+            float lo, hi;
+            asm volatile("add.rn.f32x2 %0, %1, %2;" : "=l"(x) : "l"(acc[q]), "l"(C));
+            asm volatile("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+            asm volatile("max.f32 %0, %1, %2;" : "=f"(lo) : "f"(lo), "f"(E0));
+            asm volatile("max.f32 %0, %1, %2;" : "=f"(hi) : "f"(hi), "f"(E1));
+            asm volatile("mov.b64 %0, {%1, %2};" : "=l"(mp) : "f"(lo), "f"(hi));
+            asm volatile("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(Pp), "l"(mp));
+            asm volatile("add.rn.f32x2 %0, %1, %2;" : "=l"(acc[q]) : "l"(acc[q]), "l"(d));
+        }
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float a, b;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(acc[q]));
+        t += a + b;
+    }
+    if (t == 12345.678f) sink[threadIdx.x] = t;
+}
+
+// mode 7: 8 independent running minima; each step subtracts two values from
+// the running minimum and folds both back with one three-input minimum.
+__global__ void __launch_bounds__(256) k_peak_res(int iters, float w0, float *sink)
+{
+    float acc[8];
+    const float wa = w0 + threadIdx.x * 1e-9f, wb = w0 * 0.5f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 1e3f + q;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float d0, d1;
+            asm volatile("sub.f32 %0, %1, %2;" : "=f"(d0) : "f"(acc[q]), "f"(wa));
+            asm volatile("sub.f32 %0, %1, %2;" : "=f"(d1) : "f"(acc[q]), "f"(wb));
+            asm volatile("min.f32 %0, %1, %2, %3;" : "=f"(acc[q]) : "f"(acc[q]), "f"(d0), "f"(d1));
+        }
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += acc[q];
+    if (t == 12345.678f) sink[threadIdx.x] = t;
+}
+
 }  // namespace
+
+// Lane operations (modes 0-5) or algorithmic operations (modes 6, 7) that one
+// launch of `blocks` x 256 threads performs.
+double peak_ops(int mode, int iters, int blocks)
+{
+    const double th = (double)blocks * 256.0 * iters;
+    if (mode == 6) return th * 8.0 * 2.0 * 4.0;    // 8 chains x 2 entries x 4 ops
+    if (mode == 7) return th * 8.0 * 2.0 * 2.0;    // 8 chains x 2 entries x 2 ops
+    return th * 8.0 * 2.0 * (mode >= 3 ? 2.0 : 1.0);
+}
 
 cudaError_t launch_peak(cudaStream_t st, int mode, int iters, int blocks, float *sink)
 {
@@ -90,7 +170,9 @@ cudaError_t launch_peak(cudaStream_t st, int mode, int iters, int blocks, float 
     case 2: k_peak<2><<<blocks, 256, 0, st>>>(iters, -1e30f, 1e30f, sink); break;
     case 3: k_peak_half2<<<blocks, 256, 0, st>>>(iters, 1e-3f, -60000.f, sink); break;
     case 4: k_peak_f32x2<0><<<blocks, 256, 0, st>>>(iters, b, -b, sink); break;
-    default: k_peak_f32x2<1><<<blocks, 256, 0, st>>>(iters, b, c, sink); break;
+    case 5: k_peak_f32x2<1><<<blocks, 256, 0, st>>>(iters, b, c, sink); break;
+    case 6: k_peak_delta<<<blocks, 256, 0, st>>>(iters, 1.0f, sink); break;
+    default: k_peak_res<<<blocks, 256, 0, st>>>(iters, 1e-30f, sink); break;
     }
     return cudaGetLastError();
 }

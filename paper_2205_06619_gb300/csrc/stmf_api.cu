@@ -115,7 +115,7 @@ void problem_free(stmf_problem *P)
     if (P->sweep_graph) cudaGraphDestroy(P->sweep_graph);
     void *ptrs[] = {P->R, P->RT, P->U, P->V, P->P1, P->P2, P->A, P->cmin1, P->cmin2, P->carg,
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
-                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
+                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->gpart, P->grp_cnt, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
                     P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg, P->cperm,
                     P->tdr_seq, P->tdc_seq, P->skey, P->sval, P->scnt};
@@ -154,7 +154,11 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     A(dalloc(&P->tdcol, np)); A(dalloc(&P->colhist, np * r)); A(dalloc(&P->rowhist, STMF_MAX_RANK));
     A(dalloc(&P->rank, np)); A(dalloc(&P->order, np)); A(dalloc(&P->cand, 8 * STMF_WMAX));
     A(dalloc(&P->Uc, (size_t)STMF_WMAX * mp)); A(dalloc(&P->Vc, (size_t)STMF_WMAX * np));
-    A(dalloc(&P->part, (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * ctx->num_sms * STMF_WMAX));   // float2
+    const size_t max_blocks = (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * ctx->num_sms;
+    const size_t max_groups = (max_blocks + STMF_DELTA_GROUP - 1) / STMF_DELTA_GROUP;
+    A(dalloc(&P->part, max_blocks * STMF_WMAX));   // float2
+    A(dalloc(&P->gpart, max_groups * STMF_WMAX));  // float2
+    A(dalloc(&P->grp_cnt, max_groups));
     A(dalloc(&P->fc, STMF_WMAX)); A(dalloc(&P->ctl, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&P->ctl_host, sizeof(stmf_ctl));
     if (e != cudaSuccess) {
@@ -172,11 +176,13 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     c.dirty_k = -1;
     c.ev_t0 = ~0ull;
     c.ev_d0 = ~0ull;
+    c.win_cap = c.row_cap = 1ll << 60;   // refined by the factorization's set-up
     e = cudaMemsetAsync(P->U, 0, sizeof(float) * mp * r, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->V, 0, sizeof(float) * r * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P1, 0, sizeof(float) * mp * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P2, 0, sizeof(float) * mp * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->A, 0, mp * np, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->grp_cnt, 0, sizeof(unsigned) * max_groups, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "memset: %s", cudaGetErrorString(e)); }
     *out = P;
@@ -438,30 +444,25 @@ stmf_status sweep_host(stmf_problem *P)
 
 // PermC of the ByElement strategy: the columns of the packed, oriented R in
 // increasing order of their minimum given entry, equal minima keeping the
-// smaller column first (a stable sort of the n keys on the host); R is then
-// packed again through that order, which P->cperm keeps for the output.
+// smaller column first (a rank count on the device); R is then packed again
+// through that order, which P->cperm keeps for the output.
 cudaError_t setup_permc(stmf_problem *P, cudaStream_t st, const float *R, int ldr, const uint32_t *mask,
                         int ldm_words, int *d_bad)
 {
     const int m = P->m, n = P->n;
     float *d_cmin = nullptr;
-    std::vector<float> cmin(n);
-    std::vector<int> cp(n);
+    int *d_rank = nullptr;
     cudaError_t e = cudaMalloc(&d_cmin, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_rank, sizeof(int) * n);
     if (e == cudaSuccess) e = cudaMalloc(&P->cperm, sizeof(int) * n);
     if (e == cudaSuccess) e = launch_col_min(st, P->R, P->np, m, n, d_cmin);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cmin.data(), d_cmin, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) {
-        for (int t = 0; t < n; ++t) cp[t] = t;
-        std::stable_sort(cp.begin(), cp.end(), [&](int a, int b) { return cmin[a] < cmin[b]; });
-        e = cudaMemcpyAsync(P->cperm, cp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
-    }
+    if (e == cudaSuccess) e = launch_permc_order(st, d_cmin, n, d_rank, P->cperm);
     if (e == cudaSuccess)
         e = launch_pack_oriented(st, R, ldr, mask, ldm_words, m, n, P->transposed, P->perm, P->cperm, P->R, P->np,
                                  P->mp, d_bad);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // cp and cmin stay alive until the copies end
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the scratch stays alive until the kernels end
     if (d_cmin) cudaFree(d_cmin);
+    if (d_rank) cudaFree(d_rank);
     return e;
 }
 
@@ -481,6 +482,8 @@ cudaError_t count_given(stmf_problem *P, cudaStream_t st)
 }
 
 // Algorithm 3 preparation: orientation, permutation, packing, init.
+cudaError_t set_loop_bounds(stmf_problem *P);
+
 stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, int ldr, const uint32_t *mask,
                          int ldm_words, const stmf_options *opts, stmf_problem **out)
 {
@@ -619,12 +622,41 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
         if (e == cudaSuccess) e = set_ctl(P, &stmf_ctl::trace_cap, (long long)o.trace_cap);
     }
     if (e == cudaSuccess) e = set_ctl(P, &stmf_ctl::select_mode, o.select);
+    if (e == cudaSuccess) e = set_loop_bounds(P);
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "trace buffer: %s", cudaGetErrorString(e)); }
     s = read_ctl(P);
     if (s != STMF_OK) { problem_free(P); return s; }
     P->f_init = P->ctl_host->f;
     *out = P;
     return STMF_OK;
+}
+
+// Bounds of the device-driven loops.  A row (ByElement: a segment of the
+// scan) consumes at least one position of its order per window, so it never
+// needs more windows than the order has positions; a sweep never visits more
+// rows (segments) than m n + 1.  Reaching a bound means a logic error: the
+// loops stop with STMF_ERR_TIMEOUT instead of running on.  For tests,
+// STMF_TEST_WINDOW_CAP=N in the environment sets the window bound to N.
+cudaError_t set_loop_bounds(stmf_problem *P)
+{
+    long long lim = P->n;
+    if (P->sel == STMF_SEL_SEQ) lim = (long long)P->n * P->r;
+    if (P->strategy == STMF_STRATEGY_BYELEMENT || P->strategy == STMF_STRATEGY_BYMATRIX) lim = (long long)P->m * P->n;
+    long long win_cap = lim + 2;
+    const char *t = getenv("STMF_TEST_WINDOW_CAP");
+    if (t && atoll(t) > 0) win_cap = atoll(t);
+    cudaError_t e = set_ctl(P, &stmf_ctl::win_cap, win_cap);
+    if (e == cudaSuccess) e = set_ctl(P, &stmf_ctl::row_cap, (long long)P->m * P->n + 2);
+    return e;
+}
+
+stmf_status device_error(stmf_problem *P, int q)
+{
+    const int err = P->ctl_host->err;
+    if (err == STMF_ERR_TIMEOUT)
+        return fail(P->ctx, STMF_ERR_TIMEOUT, "problem %d: a bound of the device-driven loops ran out (%lld windows "
+                    "in one row, %lld row visits in one sweep)", q, P->ctl_host->win_row, P->ctl_host->rows_sweep);
+    return fail(P->ctx, STMF_ERR_INTERNAL, "problem %d: device error %d", q, err);
 }
 
 stmf_status fastmf_run(stmf_problem *P, int sweeps, double eps)
@@ -649,7 +681,7 @@ stmf_status fastmf_run(stmf_problem *P, int sweeps, double eps)
         }
         stmf_status s = read_ctl(P);
         if (s != STMF_OK) return s;
-        if (P->ctl_host->err) return fail(ctx, STMF_ERR_INTERNAL, "device error %d", P->ctl_host->err);
+        if (P->ctl_host->err) return device_error(P, 0);
         P->sweeps_done += 1;
         const double f = P->ctl_host->f;
         if (eps > 0.0 && f_prev - f < eps && f - f_prev < eps) break;
@@ -792,6 +824,8 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
         if (b.ldr < b.n) return fail(ctx, STMF_ERR_INVALID, "problem %d: ldr < n", q);
         if (b.mask && b.ldm_words < (b.n + 31) / 32) return fail(ctx, STMF_ERR_INVALID, "problem %d: ldm_words", q);
         if (b.sweeps < 0) return fail(ctx, STMF_ERR_INVALID, "problem %d: sweeps < 0", q);
+        if (b.trace_cap < 0 || (b.trace_cap > 0 && !b.trace))
+            return fail(ctx, STMF_ERR_INVALID, "problem %d: trace_cap without a trace buffer", q);
     }
     std::vector<int> win(nprob, o.window ? (o.window + 1) / 2 * 2 : 0);
     if (!o.window)
@@ -806,7 +840,8 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
         stmf_options po = o;
         po.window = win[q]; po.seed = b.seed; po.perm = nullptr; po.picks = nullptr; po.U0 = nullptr;
         po.V0 = nullptr;
-        po.trace = nullptr; po.trace_cap = 0;
+        po.trace = b.trace_cap > 0 ? b.trace : nullptr;
+        po.trace_cap = b.trace_cap > 0 ? b.trace_cap : 0;
         CS(fastmf_begin(ctx, b.m, b.n, b.r, b.R, b.ldr, b.mask, b.ldm_words, &po, &Ps[q]));
         CK(set_ctl(Ps[q], &stmf_ctl::sweep_target, b.sweeps));
         CK(set_ctl(Ps[q], &stmf_ctl::eps, o.eps));
@@ -830,11 +865,12 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
     for (int q = 0; q < nprob; ++q) {
         stmf_problem *P = Ps[q];
         CS(read_ctl(P));
-        if (P->ctl_host->err) return fail(ctx, STMF_ERR_INTERNAL, "problem %d: device error %d", q, P->ctl_host->err);
+        if (P->ctl_host->err) return device_error(P, q);
         if (P->ctl_host->dirty_k != -2) { CS(refresh(P)); CS(read_ctl(P)); }
         P->sweeps_done = P->ctl_host->sweep;
         P->seconds = secs;
-        CK(launch_unorient(st, P, P->transposed, P->perm, P->cperm, probs[q].U_out, probs[q].V_out));
+        CS(fastmf_end(P, probs[q].U_out, probs[q].V_out, probs[q].trace_cap > 0 ? probs[q].trace : nullptr,
+                      probs[q].trace_cap));
         if (reports) fill_report(P, &reports[q]);
     }
     CK(cudaStreamSynchronize(st));
@@ -921,7 +957,7 @@ stmf_status stmf_selection_stats(stmf_ctx *ctx, int m, int n, int r, const float
     if (ldr < n || ldu < r || ldv < n) return fail(ctx, STMF_ERR_INVALID, "leading dimension too small");
     if (mask && ldm_words < (n + 31) / 32) return fail(ctx, STMF_ERR_INVALID, "ldm_words < ceil(n/32)");
     const int nparts = planes_nparts(m);
-    const size_t need = sizeof(double) * ((size_t)nparts * n + n) + sizeof(int) * (size_t)nparts * n * r + 256;
+    const size_t need = sizeof(double) * ((size_t)nparts * n + n + 1) + sizeof(int) * (size_t)nparts * n * r + 256;
     if (ctx->ws_bytes < need) {
         if (ctx->ws) cudaFree(ctx->ws);
         ctx->ws = nullptr; ctx->ws_bytes = 0;
@@ -930,20 +966,42 @@ stmf_status stmf_selection_stats(stmf_ctx *ctx, int m, int n, int r, const float
     }
     double *tdpart = (double *)ctx->ws;
     double *tdtmp = tdpart + (size_t)nparts * n;
-    int *chpart = (int *)(tdtmp + n);
+    double *fdev = tdtmp + n;
+    int *chpart = (int *)(fdev + 1);
     cudaStream_t st = ctx->stream;
     CK(launch_maxplus(st, m, n, r, U, ldu, V, ldv, mask, ldm_words, nullptr, 0, nullptr, 0, nullptr, R, ldr,
                       tdpart, chpart));
     double *tdout = td_col ? td_col : tdtmp;
     CK(launch_td_finalize2(st, tdpart, chpart, nparts, n, n, r, tdout, colhist));
     if (f_host) {
-        std::vector<double> h(n);
-        CK(cudaMemcpyAsync(h.data(), tdout, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        CK(launch_error_sum(st, tdout, n, fdev));
+        CK(cudaMemcpyAsync(f_host, fdev, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        double f = 0.0;
-        for (int t = 0; t < n; ++t) f += h[t];
-        *f_host = f;
     }
+    return STMF_OK;
+}
+
+stmf_status stmf_rmse(stmf_ctx *ctx, int m, int n, int r, const float *R, int ldr, const uint32_t *mask,
+                      int ldm_words, const float *U, int ldu, const float *V, int ldv, double *out_host)
+{
+    stmf_status s = check_common(ctx, m, n, r);
+    if (s != STMF_OK) return s;
+    if (!R || !U || !V || !out_host) return fail(ctx, STMF_ERR_INVALID, "R, U, V and out are required");
+    if (ldr < n || ldu < r || ldv < n) return fail(ctx, STMF_ERR_INVALID, "leading dimension too small");
+    if (mask && ldm_words < (n + 31) / 32) return fail(ctx, STMF_ERR_INVALID, "ldm_words < ceil(n/32)");
+    const size_t need = sizeof(double) * (4 * (size_t)rmse_blocks(m, ctx->num_sms) + 4) + 256;
+    if (ctx->ws_bytes < need) {
+        if (ctx->ws) cudaFree(ctx->ws);
+        ctx->ws = nullptr; ctx->ws_bytes = 0;
+        CK(cudaMalloc(&ctx->ws, need));
+        ctx->ws_bytes = need;
+    }
+    double *part = (double *)ctx->ws;
+    double *out = part + 4 * (size_t)rmse_blocks(m, ctx->num_sms);
+    cudaStream_t st = ctx->stream;
+    CK(launch_rmse(st, ctx->num_sms, m, n, r, R, ldr, mask, ldm_words, U, ldu, V, ldv, part, out));
+    CK(cudaMemcpyAsync(out_host, out, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     return STMF_OK;
 }
 
@@ -1069,7 +1127,7 @@ stmf_status stmf_factorize_batched(stmf_ctx *ctx, int nprob, const stmf_batch_pr
 
 stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops)
 {
-    if (!ctx || !gops || iters < 1 || mode < 0 || mode > 5) return fail(ctx, STMF_ERR_INVALID, "bad arguments");
+    if (!ctx || !gops || iters < 1 || mode < 0 || mode > 7) return fail(ctx, STMF_ERR_INVALID, "bad arguments");
     CK(cudaSetDevice(ctx->device));
     float *sink = nullptr;
     CK(cudaMalloc(&sink, 256 * sizeof(float)));
@@ -1087,8 +1145,7 @@ stmf_status stmf_peak_addmax(stmf_ctx *ctx, int mode, int iters, double *gops)
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(sink);
-    const double lane_ops = (double)blocks * 256.0 * iters * 8.0 * 2.0 * (mode >= 3 ? 2.0 : 1.0);
-    *gops = lane_ops / (ms * 1e-3) / 1e9;
+    *gops = peak_ops(mode, iters, blocks) / (ms * 1e-3) / 1e9;
     return STMF_OK;
 }
 

@@ -12,15 +12,28 @@ FP32 mode reproduces the GPU's factors bit for bit) and continues.
 import oracle as orc
 
 
-def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=None, selection="TD_A"):
+def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=None, selection="TD_A",
+           state=None):
+    """state (optional): (U, V) in the caller's frame, the factors the GPU held
+    before its first traced row visit (a run resumed mid-way); the oracle
+    starts from them instead of its own initialisation.  The result's
+    "tried" lists the candidates the oracle tried at each row visit."""
     st = orc.prepare(R, M, r, perm=perm, picks=picks, p=p, seed=seed, U0=U0)
     Ri, Mi, Ui, Vi = st["R"], st["M"], st["U"], st["V"]
+    if state is not None:
+        import numpy as np
+        Us, Vs = (np.asarray(x, dtype=np.float64) for x in state)
+        if st["transposed"]:
+            Us, Vs = Vs.T, Us.T
+        Ui = np.ascontiguousarray(Us[st["perm"]])
+        Vi = np.ascontiguousarray(Vs)
     f = orc.error(Ri, Mi, Ui, Vi)
-    divergences = []
+    divergences, tried = [], []
     for rec in gpu_trace:
         sweep, i, pos, j, k, typ, f_gpu = rec
         U0_, V0_ = Ui.copy(), Vi.copy()
-        kept, fn, out, _ = orc.row_step(Ri, Mi, Ui, Vi, i, f, selection=selection)
+        kept, fn, out, nt = orc.row_step(Ri, Mi, Ui, Vi, i, f, selection=selection)
+        tried.append(nt)
         gpu_kept = pos >= 0
         same = (kept == gpu_kept) and (not kept or tuple(out) == (pos, j, k, typ))
         if same:
@@ -40,7 +53,7 @@ def replay(R, M, r, gpu_trace, seed=0, perm=None, picks=None, p=5, tol=1e-6, U0=
         divergences.append((rec, out, f_old, f_orc, f_g))
         Ui, Vi, f = Ug, Vg, f_g
     U, V = orc.finish(R.shape[0], R.shape[1], st["transposed"], Ui, Vi, st["perm"])
-    return dict(U=U, V=V, f=f, divergences=divergences, perm=st["perm"], transposed=st["transposed"])
+    return dict(U=U, V=V, f=f, divergences=divergences, perm=st["perm"], transposed=st["transposed"], tried=tried)
 
 
 def replay_byelement(R, M, r, gpu_trace, seed=0, picks=None, p=5, tol=1e-6):

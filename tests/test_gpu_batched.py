@@ -43,3 +43,80 @@ def test_batched_equals_one_at_a_time(window):
         assert rep["candidates_tried"] == rep1["candidates_tried"] and rep["accepted"] == rep1["accepted"]
         assert rep["sweeps_done"] == pr["sweeps"]
         assert abs(rep["f_final"] - rep1["f_final"]) <= 1e-9 * max(rep1["f_final"], 1e-30)
+
+
+def _ragged_problems(seed, count, sweeps):
+    """Problems of uneven shape (tall and wide), rank and density, with their
+    host copies for the oracle."""
+    from paper_2205_06619_gb300 import api
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        m = int(rng.integers(6, 70)); n = int(rng.integers(6, 90))
+        r = int(rng.integers(1, 6)); d = float(rng.uniform(0.4, 0.95))
+        R, M, _, _ = synth.uniform_planted(m, n, r, 0.01, d, seed=int(rng.integers(1 << 30)))
+        out.append(dict(R=_tg(R), mask_words=api.pack_mask(M), rank=r, sweeps=sweeps,
+                        seed=int(rng.integers(1 << 30)), R_np=R, M_np=M))
+    return out
+
+
+def test_batched_replays_every_problem_against_the_oracle():
+    """Each problem of one batched launch exposes its trace; the replay
+    harness checks every row visit of every problem against the oracle's
+    ByRow step (Algorithm 3) and the final factors bit for bit."""
+    from paper_2205_06619_gb300 import api
+    from tests.replay import replay
+    probs = _ragged_problems(41, 10, 3)
+    for pr in probs:
+        pr["trace_cap"] = 3 * max(pr["R_np"].shape) + 8
+    outs, _ = api.factorize_batched(probs, window=8)
+    for pr, (U, V, rep) in zip(probs, outs):
+        tr = rep["trace"]
+        assert len(tr) == rep["trace_records"] == 3 * min(pr["R_np"].shape)
+        out = replay(pr["R_np"], pr["M_np"], pr["rank"], tr, seed=pr["seed"])
+        assert np.array_equal(U.cpu().numpy().astype(np.float64), out["U"])
+        assert np.array_equal(V.cpu().numpy().astype(np.float64), out["V"])
+        assert abs(rep["f_final"] - out["f"]) <= 1e-6 * max(out["f"], 1e-30)
+        assert len(out["divergences"]) <= 3       # near-ties within 1e-6 relative, adopted by the replay
+
+
+def test_batched_eps_stop_matches_the_oracle():
+    """The device-driven sweep loop of the batched form (k_sweep_end) applies
+    the convergence rule of Section "Comparison of strategies" per problem:
+    each problem's decisions replay against the oracle (near-ties adopted),
+    and it stops after the first sweep whose change of the replayed error is
+    below eps; eps is chosen 1.5x or more away from every change."""
+    import oracle as orc
+    from paper_2205_06619_gb300 import api
+    from tests.replay import replay
+    from tests.test_oracle_pins import eps_stop_case
+    cands = _ragged_problems(43, 24, 10)
+    chosen = []
+    for pr in cands:
+        full = orc.factorize(pr["R_np"], pr["M_np"], pr["rank"], sweeps=10, seed=pr["seed"])
+        case = eps_stop_case(full["f_hist"])
+        if case is not None:
+            chosen.append((pr, case, np.abs(np.diff(full["f_hist"]))))
+    # one eps for the whole batch: keep the problems with no change within 1.5x of it
+    eps = float(np.median([c[1] for _, c, _ in chosen]))
+    batch = [pr for pr, _, d in chosen if np.all(np.abs(np.log(d[d > 0] / eps)) > np.log(1.5))]
+    assert len(batch) >= 4
+    for pr in batch:
+        pr["trace_cap"] = 10 * max(pr["R_np"].shape) + 8
+    outs, _ = api.factorize_batched(batch, window=8, eps=eps)
+    stopped_early = 0
+    for pr, (U, V, rep) in zip(batch, outs):
+        tr = rep["trace"]
+        out = replay(pr["R_np"], pr["M_np"], pr["rank"], tr, seed=pr["seed"])
+        assert np.array_equal(U.cpu().numpy().astype(np.float64), out["U"])
+        assert np.array_equal(V.cpu().numpy().astype(np.float64), out["V"])
+        # the rule on the replayed errors: f after each sweep = f of its last record
+        st = orc.prepare(pr["R_np"], pr["M_np"], pr["rank"], seed=pr["seed"])
+        f_hist = [orc.error(st["R"], st["M"], st["U"], st["V"])]
+        for sw in range(rep["sweeps_done"]):
+            f_hist.append([t[6] for t in tr if t[0] == sw][-1])
+        d = np.abs(np.diff(f_hist))
+        stop = next((s + 1 for s in range(len(d)) if d[s] < eps), 10)
+        assert rep["sweeps_done"] == stop
+        stopped_early += stop < 10
+    assert stopped_early >= 4

@@ -97,3 +97,24 @@ def test_byelement_rejects_row_permutation_and_selection():
         a.factorize(tg(R), a.pack_mask(M), rank=2, sweeps=1, strategy="ByElement", selection="TD")
     U, V, rep, _ = a.factorize(tg(R), a.pack_mask(M), rank=2, sweeps=1)     # the context stays usable
     assert rep["sweeps_done"] == 1
+
+
+def test_permc_order_with_ties_signed_zeros_and_negative_minima():
+    """PermC (Section "The ByElement strategy": columns by increasing minimum
+    given entry), computed on the device by rank counting: equal minima keep
+    the smaller column first, -0 and +0 count as equal, a smaller entry that
+    is not given does not count.  Checked through the replay of two sweeps,
+    whose start depends on the column order (Acol draws its picks over the
+    permuted columns) and whose every decision follows it."""
+    rng = np.random.default_rng(61)
+    m, n = 24, 700                       # more columns than one rank chunk of 512
+    R = rng.integers(0, 40, size=(m, n)).astype(np.float64) / 8.0 - 2.0
+    M = rng.random((m, n)) < 0.85
+    M[0, :] = True
+    mins = rng.integers(-6, 6, size=n).astype(np.float64) / 4.0    # many ties, negatives
+    mins[5] = -0.0; mins[9] = 0.0; mins[600] = -0.0                # signed zeros tie with 0.0
+    R = np.maximum(R, mins[None, :] + 0.125)
+    R[0, :] = mins                                                 # row 0 holds each column's minimum
+    R[1, 7] = -50.0; M[1, 7] = False                               # not given: no effect on the minimum
+    assert np.signbit(R[0, 5]) and not np.signbit(R[0, 9])
+    run_and_replay(R.astype(np.float32), M, 3, 2, 8, window=16, divergences=2)

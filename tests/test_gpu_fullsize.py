@@ -56,3 +56,46 @@ def test_gene_scale_sweep_properties_and_first_rows():
     # decisions of the first 3 rows of sweep 0, replayed by the oracle
     out = replay(R, M, 10, trace[:3], seed=0)
     assert len(out["divergences"]) == 0
+
+
+def test_gene_scale_deep_rows_after_five_sweeps():
+    """The measured regime: after 5 sweeps of the 1000 x 5000 rank-10 workload
+    most rows keep an early candidate, but some try thousands over many
+    windows.  The oracle follows sweep 6 from the GPU's factors after sweep 5:
+    rows the GPU's trace shows trying fewer than 1000 candidates are advanced
+    by applying the GPU's own decision with the oracle's F-ULF / F-URF (which
+    reproduces the GPU's factors bit for bit), and the first two rows that
+    tried 1000 or more (up to 9000) get the oracle's full ByRow step
+    (Algorithm 3), whose decision and error must be the GPU's."""
+    from paper_2205_06619_gb300 import api
+    w = synth.workload_gene(seed=0)
+    R, M = w["R"], w["mask"]
+    fz = api.Factorization(_tg(R), api.pack_mask(M), rank=10, seed=0, trace_cap=6000)
+    fz.run(5)
+    U5, V5 = (x.cpu().numpy() for x in fz.result())
+    rep = fz.run(1)
+    fz.result()
+    recs = [t for t in fz.trace_records() if t[0] == 5]
+    assert len(recs) == 1000 and rep["sweeps_done"] == 6
+    st = orc.prepare(R, M, 10, seed=0)
+    Ri, Mi = st["R"], st["M"]
+    Ui = np.ascontiguousarray(U5.astype(np.float64)[st["perm"]])
+    Vi = np.ascontiguousarray(V5.astype(np.float64))
+    f = orc.error(Ri, Mi, Ui, Vi)
+    given = Mi.sum(axis=1)
+    deep = []
+    for sweep, i, pos, j, k, typ, f_gpu in recs:
+        est = 2 * pos + typ + 1 if pos >= 0 else 2 * int(given[i])     # candidates the GPU tried
+        if 1000 <= est <= 9000 and len(deep) < 2:
+            kept, f, out, nt = orc.row_step(Ri, Mi, Ui, Vi, i, f)
+            assert nt == est
+            assert kept == (pos >= 0) and (not kept or out == (pos, j, k, typ)), (i, out, (pos, j, k, typ))
+            assert abs(f_gpu - f) <= 1e-6 * f
+            deep.append((i, nt))
+        elif pos >= 0:
+            fun = orc.fulf if typ == 0 else orc.furf
+            Ui, Vi, f = fun(Ri, Mi, Ui, Vi, i, j, k)
+            assert abs(f_gpu - f) <= 1e-6 * f
+        if len(deep) == 2:
+            break
+    assert len(deep) == 2, deep

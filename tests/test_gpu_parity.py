@@ -322,3 +322,57 @@ def test_injected_allocation_failures_leave_the_context_usable(monkeypatch):
     assert abs(torch.cuda.mem_get_info()[0] - free0) < 64 * 1024 * 1024
     again = api().factorize(Rg, Mw, rank=3, sweeps=1, seed=0)
     assert torch.equal(again[0], ref[0]) and torch.equal(again[1], ref[1])
+
+
+def test_factorize_eps_stop_matches_the_oracle():
+    """Convergence rule (Section "Comparison of strategies"): with eps > 0 the
+    host-driven sweep loop of stmf_factorize stops after the same sweep as the
+    oracle, with the oracle's factors and error; eps is chosen a factor of 2
+    or more away from every change it is compared with."""
+    from tests.test_oracle_pins import eps_stop_case
+    R, M, _, _ = synth.uniform_planted(40, 56, 3, 0.01, 0.8, seed=32)
+    full = orc.factorize(R, M, 3, sweeps=10, seed=6)
+    s_star, eps = eps_stop_case(full["f_hist"])
+    ref = orc.factorize(R, M, 3, sweeps=10, eps=eps, seed=6)
+    assert ref["sweeps"] == s_star
+    U, V, rep, _ = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=10, eps=eps, seed=6)
+    assert rep["sweeps_done"] == s_star
+    assert np.array_equal(U.cpu().numpy().astype(np.float64), ref["U"])
+    assert np.array_equal(V.cpu().numpy().astype(np.float64), ref["V"])
+    assert rel(rep["f_final"], ref["f_hist"][-1]) <= TOL
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_loop_bound_stops_cleanly_with_timeout(monkeypatch, graph):
+    """The device-driven loops are bounded.  A test-only bound of one window
+    per row (STMF_TEST_WINDOW_CAP=1) is passed by the first row that needs a
+    second window: every loop stops, nothing of that window is committed, the
+    call returns STMF_ERR_TIMEOUT, and the context then runs the same
+    factorization normally.  Single calls (graph- and host-driven) and the
+    batched form."""
+    from tests.replay import replay
+    if not graph:
+        monkeypatch.setenv("STMF_NO_GRAPH", "1")
+    R, M, _, _ = synth.uniform_planted(40, 64, 3, 0.01, 0.8, seed=33)
+    Rg, Mw = tg(R), api().pack_mask(M)
+    ref = api().factorize(Rg, Mw, rank=3, sweeps=2, seed=1, window=2, trace_cap=500)
+    assert ref[2]["windows"] > ref[2]["trace_records"]        # some row needed a second window
+    monkeypatch.setenv("STMF_TEST_WINDOW_CAP", "1")
+    with pytest.raises(api().StmfError) as ei:
+        api().factorize(Rg, Mw, rank=3, sweeps=2, seed=1, window=2)
+    assert ei.value.status == 4          # STMF_ERR_TIMEOUT
+    with pytest.raises(api().StmfError) as ei:
+        api().factorize_batched([dict(R=Rg, mask_words=Mw, rank=3, sweeps=2, seed=1)], window=2)
+    assert ei.value.status == 4
+    # the rows before the stop are the method's own: a run resumed in pieces
+    fz = api().Factorization(Rg, Mw, rank=3, seed=1, window=2, trace_cap=500)
+    with pytest.raises(api().StmfError):
+        fz.run(2)
+    fz.result()
+    part = fz.trace_records()
+    fz.close()
+    out = replay(R, M, 3, part, seed=1)
+    assert len(out["divergences"]) == 0
+    monkeypatch.delenv("STMF_TEST_WINDOW_CAP")
+    again = api().factorize(Rg, Mw, rank=3, sweeps=2, seed=1, window=2)
+    assert torch.equal(again[0], ref[0]) and torch.equal(again[1], ref[1])
