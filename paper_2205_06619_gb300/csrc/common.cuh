@@ -28,7 +28,6 @@
 // every error change the evaluation forms there is exactly 0 (see k_delta).
 #define STMF_SENTINEL 8.5070592e37f                 // 2^126
 #define STMF_DELTA_MAX_BLOCKS_PER_SM 8   // capacity of the phase-2 partials, per SM
-#define STMF_DELTA_GROUP 32              // phase-2 blocks per second-stage group
 
 static inline int stmf_roundup(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -174,8 +173,6 @@ struct stmf_problem {
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
     float2 *part;      // STMF_WMAX x (phase-2 blocks) partial changes, float-float (hi, lo)
-    float2 *gpart;     // STMF_WMAX x (phase-2 groups) group sums of the partials, float-float
-    unsigned *grp_cnt; // per group: blocks of the running phase-2 launch that have finished (0 between launches)
     double *fc;        // STMF_WMAX candidate errors
     // FP16 screening (precision 1; all NULL otherwise)
     int precision;
@@ -250,7 +247,7 @@ cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph);
 cudaError_t launch_res(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_delta(cudaStream_t st, stmf_problem *P);
 int delta_grid(const stmf_problem *P);
-int delta_parts(const stmf_problem *P);   // phase-2 group partials per candidate (what the decision sums)
+int delta_parts(const stmf_problem *P);   // phase-2 partials per candidate
 int delta_depth(const stmf_problem *P);
 cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);

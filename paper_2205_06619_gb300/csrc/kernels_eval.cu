@@ -144,8 +144,6 @@ constexpr int DEL_THREADS = 128;
 constexpr int DEL_COLS = 4 * DEL_THREADS;
 constexpr int DEL_BLOCKS_PER_SM = 5;
 static_assert(DEL_BLOCKS_PER_SM <= STMF_DELTA_MAX_BLOCKS_PER_SM, "phase-2 partials buffer too small");
-constexpr int DEL_GROUP = STMF_DELTA_GROUP;   // blocks whose partials the second stage sums together
-static_assert(DEL_GROUP == 32, "the second stage gives one lane per block of a group");
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
@@ -250,34 +248,6 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
             x = ff_add(x, {__shfl_xor_sync(FULLM, x.hi, o), __shfl_xor_sync(FULLM, x.lo, o)});
         if (lane == 0) P.part[(size_t)sslot[c] * gridDim.x + blockIdx.x] = make_float2(x.hi, x.lo);
     }
-    // Second stage: the last block of each group of DEL_GROUP consecutive
-    // blocks to finish sums the group's partials in block order (a fence
-    // before the arrival count publishes this block's partials; no block
-    // waits for another), so the decision reads one partial per group.
-    __shared__ int slast;
-    __threadfence();
-    __syncthreads();
-    const int g = blockIdx.x / DEL_GROUP, b0 = g * DEL_GROUP;
-    const int gb = min(DEL_GROUP, (int)gridDim.x - b0);
-    if (tid == 0) slast = atomicAdd(&P.grp_cnt[g], 1u) == (unsigned)(gb - 1);
-    __syncthreads();
-    if (slast) {
-        __threadfence();
-        const int ng = (gridDim.x + DEL_GROUP - 1) / DEL_GROUP;
-        for (int c = warp; c < na; c += DEL_THREADS / 32) {
-            const int slot = sslot[c];
-            stmf_ff x = {0.f, 0.f};
-            if (lane < gb) {
-                const float2 q = __ldcg(P.part + (size_t)slot * gridDim.x + b0 + lane);
-                x = {q.x, q.y};
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1)
-                x = ff_add(x, {__shfl_xor_sync(FULLM, x.hi, o), __shfl_xor_sync(FULLM, x.lo, o)});
-            if (lane == 0) P.gpart[(size_t)slot * ng + g] = make_float2(x.hi, x.lo);
-        }
-        if (tid == 0) P.grp_cnt[g] = 0u;     // ready for the next launch
-    }
     if (tid == 0) atomicMax(&P.ctl->ev_t1, global_ns());
 }
 
@@ -312,7 +282,7 @@ int delta_grid(const stmf_problem *P)
     return ntiles < cap ? ntiles : cap;
 }
 
-int delta_parts(const stmf_problem *P) { return (delta_grid(P) + DEL_GROUP - 1) / DEL_GROUP; }
+int delta_parts(const stmf_problem *P) { return delta_grid(P); }
 
 int delta_depth(const stmf_problem *P)
 {

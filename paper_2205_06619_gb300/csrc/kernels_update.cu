@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         stmf_ff x = {0.f, 0.f};
         const bool live = c < nc && !P.cand[8 * c + 4];    // dropped: proved non-improving by the FP16 screen
         if (live) {
-            const float2 *part = P.gpart + (size_t)c * nblk;
+            const float2 *part = P.part + (size_t)c * nblk;
             stmf_ff x0 = {0.f, 0.f}, x1 = x0, x2 = x0, x3 = x0;
             int b = sub;
             for (; b + 48 < nblk; b += 64) {

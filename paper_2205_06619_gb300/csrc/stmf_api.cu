@@ -115,7 +115,7 @@ void problem_free(stmf_problem *P)
     if (P->sweep_graph) cudaGraphDestroy(P->sweep_graph);
     void *ptrs[] = {P->R, P->RT, P->U, P->V, P->P1, P->P2, P->A, P->cmin1, P->cmin2, P->carg,
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
-                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->gpart, P->grp_cnt, P->fc,
+                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
                     P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg, P->cperm,
                     P->tdr_seq, P->tdc_seq, P->skey, P->sval, P->scnt};
@@ -154,11 +154,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     A(dalloc(&P->tdcol, np)); A(dalloc(&P->colhist, np * r)); A(dalloc(&P->rowhist, STMF_MAX_RANK));
     A(dalloc(&P->rank, np)); A(dalloc(&P->order, np)); A(dalloc(&P->cand, 8 * STMF_WMAX));
     A(dalloc(&P->Uc, (size_t)STMF_WMAX * mp)); A(dalloc(&P->Vc, (size_t)STMF_WMAX * np));
-    const size_t max_blocks = (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * ctx->num_sms;
-    const size_t max_groups = (max_blocks + STMF_DELTA_GROUP - 1) / STMF_DELTA_GROUP;
-    A(dalloc(&P->part, max_blocks * STMF_WMAX));   // float2
-    A(dalloc(&P->gpart, max_groups * STMF_WMAX));  // float2
-    A(dalloc(&P->grp_cnt, max_groups));
+    A(dalloc(&P->part, (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * ctx->num_sms * STMF_WMAX));   // float2
     A(dalloc(&P->fc, STMF_WMAX)); A(dalloc(&P->ctl, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&P->ctl_host, sizeof(stmf_ctl));
     if (e != cudaSuccess) {
@@ -182,7 +178,6 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P1, 0, sizeof(float) * mp * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P2, 0, sizeof(float) * mp * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->A, 0, mp * np, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(P->grp_cnt, 0, sizeof(unsigned) * max_groups, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "memset: %s", cudaGetErrorString(e)); }
     *out = P;
