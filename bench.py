@@ -218,10 +218,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def progress(msg):
+    """A progress line on stderr (a long run that is cut off still leaves its finished legs)."""
+    print("[bench] " + msg, file=sys.stderr, flush=True)
+
+
 def run_batch(args):
-    """Many independent problems: the one-at-a-time method vs one batched
-    launch on the same problems (identical decisions, so identical final
-    errors: the times are times to equal error)."""
+    """Many independent problems (SURVEY config 3: 64 problems, rows
+    U{100..2000}, columns U{200..8000}, ranks U{3..20}, given densities
+    U[0.2, 0.9], generated as the small workload, 10 sweeps each): the whole
+    batch in one batched launch, and, on a seeded subset of the same problems
+    (the one-at-a-time leg of the whole batch takes tens of minutes), the
+    batched launch against one problem at a time.  Decisions are identical,
+    so the final errors are equal and the times are times to equal error."""
     import torch
     from paper_2205_06619_gb300 import api, synth
     rng = np.random.default_rng(args.seed)
@@ -235,32 +244,52 @@ def run_batch(args):
         probs.append(dict(R=torch.from_numpy(R).cuda(), mask_words=api.pack_mask(M), rank=r, sweeps=10, seed=q,
                           m=m, n=n))
     torch.cuda.synchronize()
-    # autotuning runs first (its result is cached in the context)
-    t = time.perf_counter()
-    api.factorize_batched(probs[:1], window=0)
-    outs, tuned = api.factorize_batched(probs, window=0)
-    t_tune_and_run = time.perf_counter() - t
-    t = time.perf_counter()
-    outs, tuned = api.factorize_batched(probs, window=0)
-    torch.cuda.synchronize()
-    t_batched = time.perf_counter() - t
-    launch = outs[0][2]["seconds"]
-    t = time.perf_counter()
-    plain = [api.factorize(p["R"], p["mask_words"], rank=p["rank"], sweeps=p["sweeps"], seed=p["seed"])
-             for p in probs]
-    torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t
-    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs, plain))
+    subset = [int(x) for x in np.random.default_rng(args.seed + 1).choice(len(probs), size=min(args.batch_subset,
+                                                                                               len(probs)),
+                                                                          replace=False)]
+    with ClockSampler(0) as clocks:
+        # the autotuner runs first (one timed trial per size class, cached in the context)
+        t = time.perf_counter()
+        api.factorize_batched(probs[:1], window=0)
+        _, tuned = api.factorize_batched(probs, window=0)   # tunes every size class of the batch
+        t_tune_and_run = time.perf_counter() - t
+        progress("batch: tuning and first batched run %.1f s" % t_tune_and_run)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        outs, tuned = api.factorize_batched(probs, window=0)
+        torch.cuda.synchronize()
+        t_batched = time.perf_counter() - t
+        progress("batch: whole batch in one launch %.1f s (%d sweeps)" % (t_batched, 10 * len(probs)))
+        sub = [probs[q] for q in subset]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        outs_sub, _ = api.factorize_batched(sub, window=0)
+        torch.cuda.synchronize()
+        t_batched_sub = time.perf_counter() - t
+        progress("batch: subset %s batched %.1f s" % (subset, t_batched_sub))
+        t = time.perf_counter()
+        plain = [api.factorize(p["R"], p["mask_words"], rank=p["rank"], sweeps=p["sweeps"], seed=p["seed"])
+                 for p in sub]
+        torch.cuda.synchronize()
+        t_plain_sub = time.perf_counter() - t
+    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs_sub, plain))
+    same_full = all(torch.equal(outs[q][0], outs_sub[i][0]) and torch.equal(outs[q][1], outs_sub[i][1])
+                    for i, q in enumerate(subset))
     sweeps = sum(p["sweeps"] for p in probs)
+    entries = sum(p["m"] * p["n"] for p in probs)
     line = {"metric": METRIC, "value": sweeps / t_batched, "unit": "sweeps/s", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": 1e3 * t_batched, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch of %d problems, rows U{100..2000}*%.2f, cols U{200..8000}*%.2f, "
-                                   "rank U{3..20}, given U[0.2,0.9], 10 sweeps each" % (args.batch_count, sc, sc),
-                       "step": "the whole batch"},
-            "batched_seconds": t_batched, "batched_launch_seconds": launch, "plain_seconds": t_plain,
-            "speedup_vs_plain": t_plain / t_batched, "identical_results": same,
-            "tuned_windows": sorted(set(tuned)), "first_call_with_tuning_seconds": t_tune_and_run}
+                                   "rank U{3..20}, given U[0.2,0.9], 10 sweeps each (%.1f M entries in all)"
+                                   % (args.batch_count, sc, sc, entries / 1e6),
+                       "step": "the whole batch in one launch"},
+            "batched_seconds": t_batched, "batched_launch_seconds": outs[0][2]["seconds"],
+            "subset": {"problems": subset, "batched_seconds": t_batched_sub, "one_at_a_time_seconds": t_plain_sub,
+                       "speedup_vs_one_at_a_time": t_plain_sub / t_batched_sub, "identical_results": same},
+            "whole_batch_equals_subset_batch": same_full,
+            "tuned_windows": sorted(set(tuned)), "first_call_with_tuning_seconds": t_tune_and_run,
+            "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -413,7 +442,8 @@ def run_learned(args):
     m, n = args.learned_m, args.learned_n
     T_sweeps = args.learned_sweeps
     t = time.perf_counter()
-    X, T = learned_init.training_set(args.learned_train, m, n, 10, T_sweeps, seed=args.seed)
+    X, T = learned_init.training_set(args.learned_train, m, n, 10, args.learned_train_sweeps or T_sweeps,
+                                     seed=args.seed, target=args.learned_target)
     t_data = time.perf_counter() - t
     t = time.perf_counter()
     net, hist = learned_init.train(X, T, 10, epochs=args.learned_epochs, batch=256, lr=1e-3, seed=args.seed)
@@ -435,7 +465,10 @@ def run_learned(args):
         f_target, f0_plain = rep["f_final"], rep["f_init"]
         fz.close()
         t = time.perf_counter()
-        U0 = learned_init.predict_U(net, Rg, Mw)
+        U_ref = None
+        if args.learned_target == "sorted":   # Random Acol's start gives the components' order per row
+            U_ref = api.factorize(Rg, Mw, rank=10, sweeps=0, seed=seed, perm=perm)[0]
+        U0 = learned_init.predict_U(net, Rg, Mw, U_ref=U_ref)
         U0 = U0[torch.from_numpy(perm.astype(np.int64)).cuda()].contiguous()
         fz = api.Factorization(Rg, Mw, rank=10, seed=seed, perm=perm, U0=U0)
         f0_learn = fz.run(0)["f_init"]
@@ -456,9 +489,11 @@ def run_learned(args):
             "unit": "time-to-equal-error speedup vs Random Acol (mean over matrices)", "n_gpus": 1, "steps": len(rows),
             "warmup": 0, "higher_is_better": True, "dtype": "f32 (MLP: bf16 weights, f32 accumulation)",
             "data": "synthetic", "vs_baseline": None, "scaling": "weak",
-            "config": {"workload": "learned init: train on %d method factorizations of %dx%d rank-10 gene-like "
-                                   "matrices (%d sweeps), evaluate on %d fresh ones" %
-                                   (args.learned_train, m, n, T_sweeps, args.learned_eval)},
+            "config": {"workload": "learned init (%s targets): train on %d method factorizations of %dx%d "
+                                   "rank-10 gene-like matrices (%d sweeps), evaluate on %d fresh ones against the "
+                                   "plain method's error after %d sweeps" %
+                                   (args.learned_target, args.learned_train, m, n,
+                                    args.learned_train_sweeps or T_sweeps, args.learned_eval, T_sweeps)},
             "train": {"samples": int(X.shape[0]), "epochs": args.learned_epochs, "loss_first": hist[0],
                       "loss_last": hist[-1], "data_seconds": t_data, "train_seconds": t_train},
             "reached_fraction": len(ok) / len(rows),
@@ -483,8 +518,11 @@ def main():
     ap.add_argument("--learned-n", type=int, default=1000)
     ap.add_argument("--learned-sweeps", type=int, default=10)
     ap.add_argument("--learned-epochs", type=int, default=30)
+    ap.add_argument("--learned-target", default="sorted", choices=["sorted", "canonical"])
+    ap.add_argument("--learned-train-sweeps", type=int, default=0, help="sweeps of the training runs (0: as eval)")
     ap.add_argument("--batch-count", type=int, default=64)
-    ap.add_argument("--batch-scale", type=float, default=0.25, help="size scale of the batch workload")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="size scale of the batch workload")
+    ap.add_argument("--batch-subset", type=int, default=8, help="problems of the one-at-a-time comparison")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -581,7 +619,7 @@ def main():
     value = sweeps_all / t_timed
     d = {k: rep1[k] - rep0[k] for k in ("candidates_tried", "candidates_issued", "accepted", "refreshes",
                                         "windows", "eval_ns", "eval_launches", "eval_candidates", "eval_res_ns",
-                                        "eval_delta_ns")}
+                                        "eval_delta_ns", "candidates_discarded")}
     ops = 6.0 * n_obs * d["candidates_tried"] + 2.0 * r * n_obs * d["refreshes"]
     gops = ops / (t_timed / world) / 1e9 * world
     # algorithmic ops per given entry and candidate: phase 1 (residuation)
@@ -592,10 +630,13 @@ def main():
     achieved = (6.0 * n_obs * ec) / (d["eval_ns"] * 1e-9) / 1e12 if d["eval_ns"] else None
     # the window evaluation's peak: 4 ops at the k_delta mix and 2 at the k_res mix per entry and candidate
     peak_eval = 6.0 / (4.0 / peaks["k_delta_mix"] + 2.0 / peaks["k_res_mix"])
-    # per window: k_seed, k_res, k_delta, k_select (which also picks the next
-    # window); per row k_row_begin; per refresh k_stats, k_maxplus_planes,
-    # k_td_finalize, k_rank, k_scatter_f; per sweep k_sweep_begin
-    launches = 4 * d["windows"] + args.steps * m_or + 5 * d["refreshes"] + args.steps
+    # per pipeline step: k_res, k_delta (window t), k_select (window t-1; it
+    # also builds window t+1), k_seed (window t+1); a row takes one step more
+    # than it decides windows; per row k_row_begin and the seeds of window 0;
+    # per refresh k_stats, k_maxplus_planes, k_td_finalize, k_rank,
+    # k_scatter_f; per sweep k_sweep_begin
+    rows_visited = args.steps * m_or
+    launches = 4 * (d["windows"] + rows_visited) + 2 * rows_visited + 5 * d["refreshes"] + args.steps
 
     if rank_id != 0:
         if dist is not None:
@@ -636,6 +677,9 @@ def main():
                          "accepted_per_sweep": d["accepted"] / args.steps,
                          "windows_per_row": d["windows"] / (args.steps * m_or),
                          "candidates_per_window": d["candidates_issued"] / max(d["windows"], 1),
+                         "candidates_dropped_per_sweep": d["candidates_discarded"] / args.steps,
+                         "launch_shapes": {"k_res_chunk": rep1["eval_res_chunk"],
+                                           "k_delta_blocks": rep1["eval_delta_blocks"]},
                          "window_eval_share_of_sweep": d["eval_ns"] * 1e-9 / t_timed if world == 1 else None},
         "peaks_measured_Tops": {k: rd(v) for k, v in peaks.items()},
         "heldout_rmse": heldout,

@@ -154,6 +154,13 @@ typedef struct {
                             per refresh).                                          */
     int strategy;        /* STMF_STRATEGY_*: 0 = ByRow (Algorithm 3), 1 = ByElement,
                             2 = ByMatrix                                           */
+    int res_chunk;       /* launch shape of the window evaluation's phase 1: columns
+                            per task, a multiple of 8 in [32, 128]; 0 = the
+                            library's choice (the batched form's autotuner, else a
+                            wave heuristic).  Never changes a result.             */
+    int delta_blocks_per_sm; /* phase 2's blocks per SM, 1..5; 0 = the library's
+                            choice.  Never changes a decision (the error sums
+                            are regrouped, within their float-float accuracy).   */
 } stmf_options;
 
 /* A trace record: sweep, row (oriented, permuted index), position of the kept
@@ -182,6 +189,11 @@ typedef struct {
                                     (precision 1; counted in candidates_issued)   */
     int64_t eval_res_ns;      /* summed durations of the phase-1 (residuation) launches */
     int64_t eval_delta_ns;    /* summed durations of the phase-2 (error change) launches */
+    int64_t candidates_discarded; /* candidates evaluated one window ahead of the decisions
+                                     and dropped because the row ended first (not in
+                                     candidates_issued)                              */
+    int64_t eval_res_chunk;   /* phase 1's column chunk (launch shape in use)          */
+    int64_t eval_delta_blocks;/* phase 2's blocks per launch (launch shape in use)     */
 } stmf_report;
 
 /* Context: binds a device and a stream (cudaStream_t passed as void*; NULL =
@@ -377,6 +389,31 @@ stmf_status stmf_mlp_gradient(stmf_mlp *mlp, int B, const float *X, const float 
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the FP32 master parameters
  * with learning rate lr; loss (host, nullable) receives the batch loss. */
 stmf_status stmf_mlp_train_step(stmf_mlp *mlp, int B, const float *X, const float *T, float lr, double *loss);
+
+/* U0 (m x r, device) = MLP(sketch of row s of R) + median of row s: the
+ * learned start (the sketch as stmf_row_sketch; mask NULL: the given entries
+ * are those of R that are not NaN); n <= 12288.  Uses the MLP's context and
+ * stream; returns when U0 is written. */
+stmf_status stmf_mlp_predict(stmf_mlp *mlp, int m, int n, const float *R, int ldr, const uint32_t *mask,
+                             int ldm_words, float *U0);
+/* Training targets from a factorization (U m x r, V r x n; device, row
+ * strides ldu, ldv): the gauge (U_.l + c, V_l. - c leaves U (x) V unchanged,
+ * and so does any order of the components) is fixed by c_l = max over t < n
+ * of V_lt, and the components are ordered by decreasing sum over rows of
+ * U_sl + c_l (FP64, rows in index order; equal sums: smaller l first).
+ * sorted = 0: T[s*r + p] = (U_s,l_p + c_l_p) - median[s], l_p the component at
+ * position p; sorted = 1: row s's values U_sl + c_l in decreasing order, minus
+ * median[s].  FP32; T (m x r) and median (m) device.  Scratch is allocated and
+ * freed inside; the call returns when T is written. */
+stmf_status stmf_mlp_targets(stmf_ctx *ctx, int m, int n, int r, const float *U, int ldu, const float *V, int ldv,
+                             const float *median, int sorted, float *T);
+/* out[s*ldo + l] = the value of row s of Y whose rank in its row (decreasing)
+ * equals the rank of U_ref[s*ldu + l] in its row (decreasing; equal values:
+ * the smaller index first): predictions made for "sorted" targets handed to
+ * the components in the order of a reference start.  Device pointers, r <=
+ * STMF_MAX_RANK; out may not alias Y.  Asynchronous on ctx's stream. */
+stmf_status stmf_assign_by_rank(stmf_ctx *ctx, int m, int r, const float *Y, int ldy, const float *U_ref, int ldu,
+                                float *out, int ldo);
 
 /* Fills *opts with the defaults (sweeps 1, eps 0, library window, first
  * improving, FP32, acol_p 5, seed 0, no explicit draws, no trace, no MLP). */

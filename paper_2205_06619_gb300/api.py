@@ -27,7 +27,8 @@ EXPORTS = ["stmf_create", "stmf_destroy", "stmf_last_error", "stmf_set_stream", 
            "stmf_peak_addmax", "stmf_rmse",
            "stmf_selection_stats_noalloc", "stmf_factorize_batched", "stmf_row_sketch", "stmf_mlp_param_count",
            "stmf_mlp_create", "stmf_mlp_destroy", "stmf_mlp_get_params", "stmf_mlp_forward", "stmf_mlp_gradient",
-           "stmf_mlp_train_step"]
+           "stmf_mlp_train_step", "stmf_mlp_targets", "stmf_assign_by_rank",
+           "stmf_mlp_predict"]
 
 
 class StmfError(RuntimeError):
@@ -41,7 +42,8 @@ class Options(C.Structure):
                 ("precision", C.c_int), ("acol_p", C.c_int), ("seed", C.c_uint64),
                 ("perm", C.c_void_p), ("picks", C.c_void_p), ("U0", C.c_void_p),
                 ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("V0", C.c_void_p), ("mlp", C.c_void_p),
-                ("selection", C.c_int), ("strategy", C.c_int)]
+                ("selection", C.c_int), ("strategy", C.c_int), ("res_chunk", C.c_int),
+                ("delta_blocks_per_sm", C.c_int)]
 
 
 # selections of (j, k) within a row (Section "The ByRow strategy"; stmf.h STMF_SEL_*)
@@ -76,7 +78,9 @@ class Report(C.Structure):
                 ("candidates_issued", C.c_int64), ("accepted", C.c_int64), ("refreshes", C.c_int64),
                 ("windows", C.c_int64), ("trace_records", C.c_int64), ("eval_ns", C.c_int64),
                 ("eval_launches", C.c_int64), ("eval_candidates", C.c_int64), ("seconds", C.c_double),
-                ("candidates_screened", C.c_int64), ("eval_res_ns", C.c_int64), ("eval_delta_ns", C.c_int64)]
+                ("candidates_screened", C.c_int64), ("eval_res_ns", C.c_int64), ("eval_delta_ns", C.c_int64),
+                ("candidates_discarded", C.c_int64), ("eval_res_chunk", C.c_int64),
+                ("eval_delta_blocks", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +132,9 @@ def load(build_if_missing: bool = True):
     L.stmf_mlp_forward.argtypes = [P, i, P, P]
     L.stmf_mlp_gradient.argtypes = [P, i, P, P, C.POINTER(d), P]
     L.stmf_mlp_train_step.argtypes = [P, i, P, P, C.c_float, C.POINTER(d)]
+    L.stmf_mlp_predict.argtypes = [P, i, i, P, i, P, i, P]
+    L.stmf_mlp_targets.argtypes = [P, i, i, i, P, i, P, i, P, i, P]
+    L.stmf_assign_by_rank.argtypes = [P, i, i, P, i, P, i, P, i]
     L.stmf_default_options.argtypes = [C.POINTER(Options)]
     L.stmf_default_options.restype = None
     L.stmf_struct_sizes.argtypes = [C.POINTER(C.c_size_t)] * 3
@@ -295,13 +302,17 @@ def selection_stats_noalloc(R, U, V, mask_words=None, td_col=None, colhist=None)
 
 
 def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=0, perm=None, picks=None,
-             U0=None, trace=None, mlp=None, V0=None, selection="TD_A", strategy="ByRow"):
+             U0=None, trace=None, mlp=None, V0=None, selection="TD_A", strategy="ByRow", shapes=None):
+    """shapes: (res_chunk, delta_blocks_per_sm), the window evaluation's launch
+    shapes (0: the library's choice); they never change a decision."""
     o = Options()
     load().stmf_default_options(C.byref(o))
     o.sweeps, o.eps, o.window, o.select, o.precision, o.acol_p, o.seed = (
         sweeps, eps, window, select, precision, acol_p, seed)
     o.selection = _selection(selection)
     o.strategy = _strategy(strategy)
+    if shapes is not None:
+        o.res_chunk, o.delta_blocks_per_sm = int(shapes[0]), int(shapes[1])
     keep = []
     if perm is not None:
         a = np.ascontiguousarray(perm, dtype=np.int32); keep.append(a); o.perm = a.ctypes.data
@@ -399,8 +410,9 @@ def sweep_log(trace):
 
 def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5,
               seed=0, perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None, selection="TD_A",
-              strategy="ByRow"):
+              strategy="ByRow", shapes=None):
     """FastSTMF (Algorithm 3) on the device.  R: float32 CUDA (m x n).
+    shapes: (res_chunk, delta_blocks_per_sm) launch shapes, or None.
     mlp: an MLP (learned initialisation on the device) or None (Random Acol).
     selection: "TD_A" (the method as published), "TD_B", "TD" or "SEQ"
     (Section "The ByRow strategy").  strategy: "ByRow" (Algorithm 3),
@@ -414,7 +426,7 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
     ctx = context()
     trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
     o, keep = _options(sweeps, eps, window, select, precision, acol_p, seed, perm, picks, U0, trace, mlp, V0,
-                       selection, strategy)
+                       selection, strategy, shapes)
     U = torch.empty((m, rank), device=R.device, dtype=torch.float32)
     V = torch.empty((rank, n), device=R.device, dtype=torch.float32)
     rep = Report()
@@ -482,6 +494,43 @@ def row_sketch(R, mask_words=None):
     return sk, md
 
 
+def mlp_targets(U, V, median, sorted_rows=False):
+    """Training targets (m x r) of the learned initialisation from a
+    factorization U (m x r), V (r x n) and the row medians (stmf_mlp_targets):
+    gauge fixed by max_t V_lt = 0, components in decreasing order of their
+    row sums; sorted_rows: each row's values in decreasing order instead."""
+    torch = _torch()
+    _check_f32(U, "U")
+    _check_f32(V, "V")
+    if median.dtype != torch.float32 or not median.is_cuda or median.dim() != 1 or median.stride(0) != 1:
+        raise TypeError("median must be a contiguous 1-D float32 CUDA tensor")
+    m, r = U.shape
+    if V.shape[0] != r or median.shape[0] != m:
+        raise ValueError("U, V and median disagree in shape")
+    ctx = context()
+    T = torch.empty((m, r), device=U.device, dtype=torch.float32)
+    ctx.check(load().stmf_mlp_targets(ctx.h, m, V.shape[1], r, _ptr(U), U.stride(0), _ptr(V), V.stride(0),
+                                      _ptr(median), int(bool(sorted_rows)), _ptr(T)))
+    return T
+
+
+def assign_by_rank(Y, U_ref):
+    """out[s][l] = the value of Y[s] whose rank in its row (decreasing) is the
+    rank of U_ref[s][l] in its row (decreasing, equal values: smaller index
+    first) (stmf_assign_by_rank)."""
+    torch = _torch()
+    _check_f32(Y, "Y")
+    _check_f32(U_ref, "U_ref")
+    if Y.shape != U_ref.shape:
+        raise ValueError("Y and U_ref differ in shape")
+    m, r = Y.shape
+    ctx = context()
+    out = torch.empty((m, r), device=Y.device, dtype=torch.float32)
+    ctx.check(load().stmf_assign_by_rank(ctx.h, m, r, _ptr(Y), Y.stride(0), _ptr(U_ref), U_ref.stride(0),
+                                         _ptr(out), r))
+    return out
+
+
 class MLP:
     """The learned-initialisation network on the device (stmf_mlp_*)."""
 
@@ -518,6 +567,17 @@ class MLP:
         self.ctx.check(load().stmf_mlp_forward(self.h, X.shape[0], _ptr(X), _ptr(Y)))
         return Y
 
+    def predict(self, R, mask_words=None):
+        """U0 (m x r) = MLP(row sketch of R) + row median (stmf_mlp_predict)."""
+        torch = _torch()
+        _check_f32(R, "R")
+        m, n = R.shape
+        U0 = torch.empty((m, self.r), device=R.device, dtype=torch.float32)
+        ldm = mask_words.shape[1] if mask_words is not None else 0
+        self.ctx.check(load().stmf_mlp_predict(self.h, m, n, _ptr(R), R.stride(0), _ptr(mask_words), ldm,
+                                               _ptr(U0)))
+        return U0
+
     def gradient(self, X, T):
         g = np.empty(self.np, np.float32)
         loss = C.c_double()
@@ -541,13 +601,13 @@ class Factorization:
 
     def __init__(self, R, mask_words=None, rank=3, window=0, select=0, precision=0, acol_p=5, seed=0,
                  perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None, selection="TD_A",
-                 strategy="ByRow"):
+                 strategy="ByRow", shapes=None):
         _check_f32(R, "R")
         self.ctx = context()
         self.m, self.n, self.r = R.shape[0], R.shape[1], rank
         self.trace = np.zeros((trace_cap, STMF_TRACE_INTS), np.int32) if trace_cap else None
         o, self._keep = _options(0, 0.0, window, select, precision, acol_p, seed, perm, picks, U0, self.trace,
-                                 mlp, V0, selection, strategy)
+                                 mlp, V0, selection, strategy, shapes)
         h = C.c_void_p()
         ldm = mask_words.shape[1] if mask_words is not None else 0
         self.ctx.check(load().stmf_factorize_begin(self.ctx.h, self.m, self.n, rank, _ptr(R), R.stride(0),

@@ -78,7 +78,26 @@ struct stmf_ctx {
     char err[512];
     void *ws;          // workspace for stmf_selection_stats
     size_t ws_bytes;
-    void *tune;        // autotuner cache (std::map of size class -> window), owned
+    void *tune;        // autotuner cache (std::map of size class -> window and launch shapes), owned
+};
+
+// One window of candidates and its evaluation.  Two of them alternate so
+// that the evaluation of window t (the phase-1 and phase-2 kernels) runs
+// while k_select decides window t-1 and builds window t+1 into the other
+// buffer: each kernel touches only its own buffer's window, candidate slots,
+// U'/V' and partials.
+struct stmf_win {
+    int nc;            // candidates in the window
+    int na;            // slots to evaluate in phase 2 (after the FP16 screen)
+    int nu, nv;        // F-ULF / F-URF slots of phase 1
+    int exhausted;     // 1 when the window reached the end of the row's candidates
+    int live;          // 1 from the build until the decision
+    int screened;      // candidates the FP16 screen proved non-improving
+    int pad_;
+    int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // phase-1 slots per type, grouped by k
+    int alist[STMF_WMAX];                             // phase-2 slots, grouped by k
+    unsigned long long ev_t0, ev_t1;   // earliest start / latest end of the window's evaluation
+    unsigned long long ev_r1, ev_d0;   // end of its phase-1 launch / start of its phase-2 launch
 };
 
 // Control block in device memory.  The kernels of the row loop read and
@@ -89,30 +108,24 @@ struct stmf_ctl {
     int i;             // current row
     int m;             // rows per sweep
     int sweep;         // sweep index (for the trace)
-    int pos;           // next position in the column order
-    int wj;            // j-candidates of the next window (each gives F-ULF, F-URF)
+    int pos;           // next position in the column order (of the next window to build)
+    int wj;            // j-candidates of the next window to build (each gives F-ULF, F-URF)
     int wj0;           // j-candidates of a row's first window (what the previous row consumed)
     int wmax;          // candidates per window (upper bound, even)
-    int nc;            // candidates in the current window
-    int ncand_row;     // candidates of the row consumed so far
+    int ncand_row;     // candidates of the row decided so far
+    int nbuilt;        // candidates of the row put in windows so far (runs one window ahead)
     int kept;          // 1 if the last select kept a candidate
     int row_done;      // 1 once the row is finished (kept or exhausted)
     int kept_pos, kept_j, kept_k, kept_type, kept_c;
     int dirty_k;       // -2: planes current; -1: refresh all components; k: refresh k
     int select_mode;   // 0 first improving (paper), 1 best of window
     int err;           // device-detected error code (0 = none)
-    int nu, nv;        // F-ULF / F-URF candidates of the window
-    int exhausted;     // 1 when the window reached the end of the row's candidates
-    int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // window slots per type, grouped by k
-    int alist[STMF_WMAX];  // all the window's slots to evaluate in phase 2, grouped by k
-    int na;
     long long tried;   // sequential-method candidates tried (cumulative)
     long long issued;  // candidates evaluated on the device (cumulative)
     long long accepted;
     long long refreshes;
     long long windows;
-    unsigned long long ev_t0, ev_t1;   // earliest start / latest end of the running window evaluation
-    unsigned long long ev_r1, ev_d0;   // end of its phase-1 launch / start of its phase-2 launch
+    long long discarded;// candidates of windows evaluated ahead and dropped at the end of a row
     long long res_ns, delta_ns;        // summed durations of the phase-1 / phase-2 launches
     long long eval_ns;                 // summed durations of the window evaluations (%globaltimer)
     long long eval_launches;
@@ -169,11 +182,18 @@ struct stmf_problem {
     unsigned *sval;              // nsort: element q = i n + j, in the iteration's order after the sort
     unsigned long long *scnt;    // slot counter of the keys
     unsigned long long coin_key; // key of the per-element coin (seed ^ 0x5A5A...5A)
+    // window buffers: the arrays below hold two buffers back to back and
+    // point at buffer 0; window_view(P, b) points them at buffer b
+    stmf_win *win;     // the window
     int *cand;         // STMF_WMAX x 8: j, k, type, position (4 spare)
     float *Uc;         // STMF_WMAX x mp candidate U'_.k
     float *Vc;         // STMF_WMAX x np candidate V'_k.
     float2 *part;      // STMF_WMAX x (phase-2 blocks) partial changes, float-float (hi, lo)
     double *fc;        // STMF_WMAX candidate errors
+    // launch shapes of the window evaluation (0: the defaults; set by the
+    // autotuner before any capture): phase 1's column chunk (a multiple of 8
+    // in [32, 128]) and phase 2's blocks per SM (1..5)
+    int res_chunk_sel, delta_bps_sel;
     // FP16 screening (precision 1; all NULL otherwise)
     int precision;
     __half *Rh, *P1h, *P2h;
@@ -196,8 +216,28 @@ struct stmf_problem {
     cudaGraphExec_t sweep_exec;
     cudaGraph_t sweep_graph;
     unsigned long long h_row, h_dirty, h_win;   // cudaGraphConditionalHandle values
+    unsigned long long h_step;                  // second pipeline step of a window-loop iteration
     unsigned long long h_sweep;                 // sweep loop of a device-driven job
 };
+
+// Sizes of one window buffer, in elements of each array.
+inline size_t win_cand_elems() { return 8 * STMF_WMAX; }
+inline size_t win_uc_elems(const stmf_problem *P) { return (size_t)STMF_WMAX * P->mp; }
+inline size_t win_vc_elems(const stmf_problem *P) { return (size_t)STMF_WMAX * P->np; }
+inline size_t win_part_elems(int num_sms) { return (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * num_sms * STMF_WMAX; }
+
+// The problem with its window arrays pointed at buffer b (0 or 1).
+inline stmf_problem window_view(const stmf_problem *P, int b)
+{
+    stmf_problem v = *P;
+    v.win += b;
+    v.cand += b * win_cand_elems();
+    v.Uc += b * win_uc_elems(P);
+    v.Vc += b * win_vc_elems(P);
+    v.part += b * win_part_elems(P->ctx->num_sms);
+    v.fc += b * STMF_WMAX;
+    return v;
+}
 
 // ---------------------------------------------------------------- launchers
 // kernels_product.cu
@@ -241,7 +281,8 @@ cudaError_t launch_copy_rows(cudaStream_t st, const float *src, int lds, float *
 cudaError_t launch_stats(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_seed(cudaStream_t st, stmf_problem *P, int nslots);
 cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode = 0);
-cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph);
+cudaError_t launch_window_eval(cudaStream_t st, stmf_problem *P, int b);
+cudaError_t launch_window_next(cudaStream_t st, stmf_problem *P, int b, int in_graph);
 
 // kernels_eval.cu
 cudaError_t launch_res(cudaStream_t st, stmf_problem *P);
@@ -249,7 +290,9 @@ cudaError_t launch_delta(cudaStream_t st, stmf_problem *P);
 int delta_grid(const stmf_problem *P);
 int delta_parts(const stmf_problem *P);   // phase-2 partials per candidate
 int delta_depth(const stmf_problem *P);
-cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single);
+int res_chunk(const stmf_problem *P);            // phase 1's column chunk for this problem
+int res_chunk_default(const stmf_problem *P);    // the wave heuristic's choice
+cudaError_t launch_select_single(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);
 cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph);
@@ -264,7 +307,8 @@ cudaError_t screen_prepare(stmf_problem *P);
 cudaError_t launch_screen(cudaStream_t st, stmf_problem *P);
 
 // mlp.cu
-stmf_status mlp_predict_rows(stmf_ctx *ctx, stmf_mlp *M, int m, int n, const float *R, int ldr, float *U0);
+stmf_status mlp_predict_rows(stmf_ctx *ctx, stmf_mlp *M, int m, int n, const float *R, int ldr,
+                             const uint32_t *mask, int ldm_words, float *U0);
 int mlp_rank(const stmf_mlp *M);
 
 // peak.cu

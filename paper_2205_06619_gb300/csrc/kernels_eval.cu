@@ -89,16 +89,16 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
 {
     __shared__ __align__(16) float sW[NCT][RES_CHUNK_MAX];
     __shared__ int sslot[NCT];
-    const stmf_ctl *ctl = P.ctl;
+    stmf_win *win = P.win;
     const int tid = threadIdx.x;
     // the window evaluation's span (this launch's start to the end of
     // phase 2) is recorded with the global nanosecond timer: inside a CUDA
     // graph no event can bracket single nodes
-    if (tid == 0) atomicMin(&P.ctl->ev_t0, global_ns());
+    if (tid == 0) atomicMin(&win->ev_t0, global_ns());
     int task = blockIdx.x;
     const int type = task >= ntask0;
     if (type) task -= ntask0;
-    const int cnt = type ? ctl->nv : ctl->nu;
+    const int cnt = type ? win->nv : win->nu;
     if (cnt == 0) return;
     const int nch = type ? nch1 : nch0;
     const int rb = task / nch, c0 = (task % nch) * chunk;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
     const size_t ldw = type ? P.mp : P.np;
     const size_t ldo = type ? P.np : P.mp;
 
-    if (tid < cnt) sslot[tid] = type ? ctl->vlist[tid] : ctl->ulist[tid];
+    if (tid < cnt) sslot[tid] = type ? win->vlist[tid] : win->ulist[tid];
     __syncthreads();
     for (int e = tid; e < cnt * nq; e += RES_THREADS) {
         const int c = e / nq, q = e % nq;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_res(stmf_problem P, int ntask0,
         else res_rows<32>(x4, x4b, has_b, sW, nq, sslot, cnt, OUT, ldo, row);
     }
     __syncthreads();
-    if (tid == 0) atomicMax(&P.ctl->ev_r1, global_ns());
+    if (tid == 0) atomicMax(&win->ev_r1, global_ns());
 }
 
 // ------------------------------------------------------------------ phase 2
@@ -184,12 +184,12 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
     __shared__ float sacc[STMF_WMAX][DEL_THREADS];
     __shared__ __align__(16) float su[STMF_WMAX][4];
     __shared__ int sslot[STMF_WMAX], sk[STMF_WMAX];
-    const stmf_ctl *ctl = P.ctl;
+    stmf_win *win = P.win;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) atomicMin(&P.ctl->ev_d0, global_ns());
-    const int na = ctl->na;
+    if (tid == 0) atomicMin(&win->ev_d0, global_ns());
+    const int na = win->na;
     if (tid < na) {
-        const int slot = ctl->alist[tid];
+        const int slot = win->alist[tid];
         sslot[tid] = slot;
         sk[tid] = P.cand[8 * slot + 1];
     }
@@ -248,20 +248,23 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
             x = ff_add(x, {__shfl_xor_sync(FULLM, x.hi, o), __shfl_xor_sync(FULLM, x.lo, o)});
         if (lane == 0) P.part[(size_t)sslot[c] * gridDim.x + blockIdx.x] = make_float2(x.hi, x.lo);
     }
-    if (tid == 0) atomicMax(&P.ctl->ev_t1, global_ns());
+    if (tid == 0) atomicMax(&win->ev_t1, global_ns());
 }
 
 int res_blocks(int rows) { return (rows + RES_THREADS * RES_RPT - 1) / (RES_THREADS * RES_RPT); }
 
 // Phase-1 tasks all have the same size, so a launch takes as many waves as
 // the tasks need slots; the column chunk (a multiple of 8 up to 128) is the
-// one that minimises waves x chunk.
-int res_chunk(const stmf_problem *P)
+// one that minimises waves x chunk.  Two slots are left to the decision
+// block (1024 threads x 32 registers) that runs beside the evaluation, so
+// that it never pushes a task into another wave.
+int res_chunk_heuristic(const stmf_problem *P)
 {
     static int per_sm = 0;
     if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_res, RES_THREADS, 0) != cudaSuccess)
         per_sm = 1;
-    const long long slots = (long long)per_sm * P->ctx->num_sms;
+    long long slots = (long long)per_sm * P->ctx->num_sms - 2;
+    if (slots < 1) slots = 1;
     int best = RES_CHUNK_MAX;
     long long best_cost = -1;
     for (int c = 32; c <= RES_CHUNK_MAX; c += 8) {
@@ -275,10 +278,20 @@ int res_chunk(const stmf_problem *P)
 
 }  // namespace
 
+int res_chunk_default(const stmf_problem *P) { return res_chunk_heuristic(P); }
+
+int res_chunk(const stmf_problem *P)
+{
+    const int c = P->res_chunk_sel;
+    return (c >= 32 && c <= RES_CHUNK_MAX && c % 8 == 0) ? c : res_chunk_heuristic(P);
+}
+
 int delta_grid(const stmf_problem *P)
 {
     const int ntiles = ((P->m + 3) / 4) * ((P->np + DEL_COLS - 1) / DEL_COLS);
-    const int cap = DEL_BLOCKS_PER_SM * P->ctx->num_sms;
+    const int bps = (P->delta_bps_sel >= 1 && P->delta_bps_sel <= DEL_BLOCKS_PER_SM) ? P->delta_bps_sel
+                                                                                     : DEL_BLOCKS_PER_SM;
+    const int cap = bps * P->ctx->num_sms;
     return ntiles < cap ? ntiles : cap;
 }
 

@@ -72,9 +72,9 @@ __global__ void __launch_bounds__(SCR_THREADS) k_screen(stmf_problem P, int wmax
     __shared__ float su[STMF_WMAX][SCR_ROWS];
     __shared__ int sslot[STMF_WMAX], sk[STMF_WMAX];
     __shared__ float red[2][SCR_THREADS / 32];
-    const stmf_ctl *ctl = P.ctl;
+    const stmf_win *win = P.win;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nu = ctl->nu, nv = ctl->nv, nc = ctl->nc;
+    const int nu = win->nu, nv = win->nv, nc = win->nc;
 
     if ((int)blockIdx.x < wmax) {
         const int c = blockIdx.x;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(SCR_THREADS) k_screen(stmf_problem P, int wmax
     const int rows = min(SCR_ROWS, P.m - s0);
     // F-ULF candidates then F-URF candidates, each list grouped by k
     if (tid < nu + nv) {
-        const int slot = tid < nu ? ctl->ulist[tid] : ctl->vlist[tid - nu];
+        const int slot = tid < nu ? win->ulist[tid] : win->vlist[tid - nu];
         sslot[tid] = slot;
         sk[tid] = P.cand[8 * slot + 1];
     }
@@ -209,9 +209,10 @@ __global__ void __launch_bounds__(SCR_THREADS) k_screen(stmf_problem P, int wmax
 __global__ void __launch_bounds__(1024) k_screen_select(stmf_problem P, int nblk, double depth)
 {
     __shared__ double sd[STMF_WMAX], sn[STMF_WMAX];
-    stmf_ctl *ctl = P.ctl;
+    const stmf_ctl *ctl = P.ctl;
+    stmf_win *win = P.win;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nc = ctl->nc;
+    const int nc = win->nc;
     for (int c = warp; c < nc; c += 32) {
         stmf_ff x = {0.f, 0.f}, y = {0.f, 0.f};
         for (int b = lane; b < nblk; b += 32) {
@@ -246,23 +247,23 @@ __global__ void __launch_bounds__(1024) k_screen_select(stmf_problem P, int nblk
         dropped += drop;
     }
     int nu2 = 0, nv2 = 0;
-    for (int a = 0; a < ctl->nu; ++a) {
-        const int slot = ctl->ulist[a];
-        if (!P.cand[8 * slot + 4]) ctl->ulist[nu2++] = slot;
+    for (int a = 0; a < win->nu; ++a) {
+        const int slot = win->ulist[a];
+        if (!P.cand[8 * slot + 4]) win->ulist[nu2++] = slot;
     }
-    for (int a = 0; a < ctl->nv; ++a) {
-        const int slot = ctl->vlist[a];
-        if (!P.cand[8 * slot + 4]) ctl->vlist[nv2++] = slot;
+    for (int a = 0; a < win->nv; ++a) {
+        const int slot = win->vlist[a];
+        if (!P.cand[8 * slot + 4]) win->vlist[nv2++] = slot;
     }
     int na2 = 0;
-    for (int a = 0; a < ctl->na; ++a) {
-        const int slot = ctl->alist[a];
-        if (!P.cand[8 * slot + 4]) ctl->alist[na2++] = slot;
+    for (int a = 0; a < win->na; ++a) {
+        const int slot = win->alist[a];
+        if (!P.cand[8 * slot + 4]) win->alist[na2++] = slot;
     }
-    ctl->na = na2;
-    ctl->nu = nu2;
-    ctl->nv = nv2;
-    ctl->screened += dropped;
+    win->na = na2;
+    win->nu = nu2;
+    win->nv = nv2;
+    win->screened = dropped;
 }
 
 size_t screen_smem(int wmax) { return sizeof(float2) * (size_t)wmax * SCR_THREADS; }

@@ -310,6 +310,19 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
     for (int w = threadIdx.x; w < CTL_WORDS; w += blockDim.x) d[w] = s[w];
 }
 
+// A built window: not yet evaluated (timestamps reset), awaiting its
+// decision; the next build covers twice the j-candidates, up to wmax / 2.
+__device__ __forceinline__ void window_opened(stmf_win *win, stmf_ctl *ctl)
+{
+    win->live = 1;
+    win->screened = 0;
+    win->ev_t0 = ~0ull;
+    win->ev_t1 = 0ull;
+    win->ev_r1 = 0ull;
+    win->ev_d0 = ~0ull;
+    ctl->wj = min(ctl->wj * 2, ctl->wmax / 2);
+}
+
 // Window of candidates (Algorithm 3; selections of Section "The ByRow
 // strategy"): the next wj pairs (j, k) of the row's order with R_ij given.
 //   TD_A: j along the column order (td_col descending); k_j = argmax_l
@@ -330,11 +343,16 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
 // most STMF_WMAX / 2 of them (phase 1 holds at most that many of one type).
 // Otherwise each pair gives F-ULF (slot 2a) then F-URF (slot 2a+1), the
 // order in which Algorithm 3 tries them.  At the first window of a row the
-// row histogram (and TD_B's j0) is rebuilt.  Runs in a block of 1024
-// threads: at the start of a row (k_row_begin) and after a window that
-// neither kept a candidate nor exhausted the row (k_select).
+// row histogram (and TD_B's j0) is rebuilt.  Windows are built one ahead of
+// the decisions: the position, the slot numbering (nbuilt) and the window
+// size (wj, doubled after each build up to wmax / 2) belong to the builds;
+// a window never depends on the decision of the one before it, only on
+// whether the row goes on.  Runs in a block of 1024 threads: at the start of
+// a row (k_row_begin) and in k_select after a decision that did not end the
+// row; the window goes into P.win and P.cand (the buffer P points at).
 __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ctl, bool row_start)
 {
+    stmf_win *win = P.win;
     __shared__ int sh[STMF_MAX_RANK];
     __shared__ int sj[STMF_WMAX / 2], sk[STMF_WMAX / 2], si[STMF_WMAX / 2], sq[STMF_WMAX / 2], sty[STMF_WMAX / 2];
     __shared__ int scount, spos;
@@ -346,7 +364,7 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
     // of the iteration's sorted order)
     const int lim = elem ? P.m * P.n : mat ? (int)P.ngiven : (sel == STMF_SEL_SEQ ? P.n * r : P.n);
     if (row_start && (elem || mat)) {
-        if (tid == 0) ctl->ncand_row = 0;
+        if (tid == 0) { ctl->ncand_row = 0; ctl->nbuilt = 0; }
         __syncthreads();
     } else if (row_start) {
         if (tid < r) sh[tid] = 0;
@@ -376,6 +394,7 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         if (tid == 0) {
             ctl->pos = 0;
             ctl->ncand_row = 0;
+            ctl->nbuilt = 0;
             ctl->tdb_j0 = sj0 ? td_argmax_index(sj0) : 0;    // every row has a given entry (checked at set-up)
         }
         __syncthreads();
@@ -468,7 +487,7 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
         // within the iteration, screen flag, row i, position in the order
         if (tid < cnt) {
             int *c0 = P.cand + 8 * tid;
-            c0[0] = sj[tid]; c0[1] = sk[tid]; c0[2] = sty[tid]; c0[3] = ctl->ncand_row + tid; c0[4] = 0;
+            c0[0] = sj[tid]; c0[1] = sk[tid]; c0[2] = sty[tid]; c0[3] = ctl->nbuilt + tid; c0[4] = 0;
             c0[5] = si[tid]; c0[6] = sq[tid];
         }
         if (tid == 0) {
@@ -481,23 +500,25 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
             int nu = 0, nv = 0;
             for (int a = 0; a < cnt; ++a) {
                 const int c = idx[a];
-                ctl->alist[a] = c;
-                if (sty[c] == 0) ctl->ulist[nu++] = c;
-                else ctl->vlist[nv++] = c;
+                win->alist[a] = c;
+                if (sty[c] == 0) win->ulist[nu++] = c;
+                else win->vlist[nv++] = c;
             }
-            ctl->nc = cnt;
-            ctl->na = cnt;
-            ctl->nu = nu;
-            ctl->nv = nv;
-            ctl->exhausted = spos >= lim;
+            win->nc = cnt;
+            win->na = cnt;
+            win->nu = nu;
+            win->nv = nv;
+            win->exhausted = spos >= lim;
             ctl->pos = spos;
+            ctl->nbuilt += cnt;
+            window_opened(win, ctl);
         }
         return;
     }
     if (tid < cnt) {
         // slot: j, k, type, index within the row (or ByElement segment),
         // screen flag, row i, position recorded in the trace
-        const int base = ctl->ncand_row / 2;
+        const int base = ctl->nbuilt / 2;
         const int ci = elem ? si[tid] : i, cq = elem ? sq[tid] : base + tid;
         int *c0 = P.cand + 8 * (2 * tid);
         c0[0] = sj[tid]; c0[1] = sk[tid]; c0[2] = 0; c0[3] = base + tid; c0[4] = 0; c0[5] = ci; c0[6] = cq;
@@ -514,17 +535,19 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
             idx[b + 1] = a;
         }
         for (int a = 0; a < cnt; ++a) {
-            ctl->ulist[a] = 2 * idx[a];
-            ctl->vlist[a] = 2 * idx[a] + 1;
-            ctl->alist[2 * a] = 2 * idx[a];
-            ctl->alist[2 * a + 1] = 2 * idx[a] + 1;
+            win->ulist[a] = 2 * idx[a];
+            win->vlist[a] = 2 * idx[a] + 1;
+            win->alist[2 * a] = 2 * idx[a];
+            win->alist[2 * a + 1] = 2 * idx[a] + 1;
         }
-        ctl->nc = 2 * cnt;
-        ctl->na = 2 * cnt;
-        ctl->nu = cnt;
-        ctl->nv = cnt;
-        ctl->exhausted = spos >= lim;
+        win->nc = 2 * cnt;
+        win->na = 2 * cnt;
+        win->nu = cnt;
+        win->nv = cnt;
+        win->exhausted = spos >= lim;
         ctl->pos = spos;
+        ctl->nbuilt += 2 * cnt;
+        window_opened(win, ctl);
     }
 }
 
@@ -535,9 +558,8 @@ __device__ __forceinline__ void build_window(const stmf_problem &P, stmf_ctl *ct
 // grid.x covers max(np, mp).
 __global__ void k_seed(stmf_problem P)
 {
-    const stmf_ctl *ctl = P.ctl;
     const int c = blockIdx.y;
-    if (c >= ctl->nc) return;
+    if (c >= P.win->nc) return;
     const int *cd = P.cand + 8 * c;
     const int j = cd[0], k = cd[1], type = cd[2], i = cd[5];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -577,31 +599,40 @@ __device__ __forceinline__ void put_trace(stmf_ctl *ctl, int pos, int j, int k, 
     ctl->ntrace += 1;
 }
 
-// End of a window: sums the phase-2 block partials of every candidate (fixed order)
-// into its change Delta = f' - f, keeps the first candidate in the paper's
-// order with Delta < 0 (select_mode 1: the smallest), commits it, writes the
-// trace record and advances the row.  In a graph it also sets the
-// conditions of the row loop: h_win (another window of this row), h_dirty
-// (refresh before the next row), h_row (another row in this sweep).
-__global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int in_graph, int single,
-                                                cudaGraphConditionalHandle h_row,
+// Decision of the window in P.win (one pipeline step behind the evaluation):
+// sums the phase-2 block partials of every candidate (fixed order) into its
+// change Delta = f' - f, keeps the first candidate in the paper's order with
+// Delta < 0 (select_mode 1: the smallest), commits it, writes the trace
+// record and advances the row; a window that is not live (the first step of
+// a row) has nothing to decide.  If the row goes on, builds the window after
+// the one being evaluated into the same buffer.  `other` is the other
+// buffer's window (evaluated meanwhile; dropped when this decision ends the
+// row).  In a graph it also sets the conditions of the row loop: h_win and
+// h_step (another pipeline step in this row), h_dirty (refresh before the
+// next row), h_row (another row in this sweep).
+__global__ void __launch_bounds__(1024) k_select(stmf_problem P, const stmf_win *other, int nblk, int in_graph,
+                                                int single, cudaGraphConditionalHandle h_row,
                                                 cudaGraphConditionalHandle h_dirty,
-                                                cudaGraphConditionalHandle h_win)
+                                                cudaGraphConditionalHandle h_win,
+                                                cudaGraphConditionalHandle h_step)
 {
     __shared__ double sf[STMF_WMAX];
-    __shared__ int skept;
+    __shared__ int skept, slive, snc;
     __shared__ stmf_ctl sctl;
+    stmf_win *win = P.win;
+    if (threadIdx.x == 0) { slive = win->live; snc = win->nc; }
     ctl_load(sctl, P.ctl);
     stmf_ctl *ctl = &sctl;
     const int tid = threadIdx.x;
-    const int nc = ctl->nc;
+    const bool live = slive;
+    const int nc = live ? snc : 0;
     // 16 threads per candidate, four independent float-float sums each (the
     // loads of a thread are all in flight together); fixed order
     {
         const int c = tid >> 4, sub = tid & 15;
         stmf_ff x = {0.f, 0.f};
-        const bool live = c < nc && !P.cand[8 * c + 4];    // dropped: proved non-improving by the FP16 screen
-        if (live) {
+        const bool on = c < nc && !P.cand[8 * c + 4];    // dropped: proved non-improving by the FP16 screen
+        if (on) {
             const float2 *part = P.part + (size_t)c * nblk;
             stmf_ff x0 = {0.f, 0.f}, x1 = x0, x2 = x0, x3 = x0;
             int b = sub;
@@ -617,8 +648,8 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         for (int o = 8; o; o >>= 1) x = ff_add(x, {__shfl_xor_sync(FULL, x.hi, o), __shfl_xor_sync(FULL, x.lo, o)});
         if (c < nc && sub == 0) {
             const double d = (double)x.hi + (double)x.lo;
-            sf[c] = live ? d : INFINITY;
-            P.fc[c] = live ? ctl->f + d : INFINITY;
+            sf[c] = on ? d : INFINITY;
+            P.fc[c] = on ? ctl->f + d : INFINITY;
         }
     }
     __syncthreads();
@@ -647,7 +678,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         if (lane == 0) skept = kept;
     }
     __syncthreads();
-    if (tid == 0 && !single && ++ctl->win_row > ctl->win_cap) {
+    if (tid == 0 && !single && live && ++ctl->win_row > ctl->win_cap) {
         // more windows in this row than its candidates allow: stop every loop
         ctl->err = STMF_ERR_TIMEOUT;
         skept = -1;
@@ -658,24 +689,29 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
         ctl->more = 0;
         if (in_graph) {
             cudaGraphSetConditional(h_win, 0u);
+            cudaGraphSetConditional(h_step, 0u);
             cudaGraphSetConditional(h_dirty, 0u);
             cudaGraphSetConditional(h_row, 0u);
         }
+    } else if (tid == 0 && !live) {
+        // first step of a row: window 0 is being evaluated, window 1 is built below
+        if (in_graph && !single && !ctl->row_done) {
+            cudaGraphSetConditional(h_win, 1u);
+            cudaGraphSetConditional(h_step, 1u);
+        }
     } else if (tid == 0) {
         const int kept = skept;
+        win->live = 0;
         ctl->issued += nc;
         ctl->windows += 1;
-        if (ctl->ev_t1 > ctl->ev_t0) {
-            ctl->eval_ns += (long long)(ctl->ev_t1 - ctl->ev_t0);
+        ctl->screened += win->screened;
+        if (win->ev_t1 > win->ev_t0) {
+            ctl->eval_ns += (long long)(win->ev_t1 - win->ev_t0);
             ctl->eval_launches += 1;
             ctl->eval_cands += nc;
-            if (ctl->ev_r1 > ctl->ev_t0) ctl->res_ns += (long long)(ctl->ev_r1 - ctl->ev_t0);
-            if (ctl->ev_t1 > ctl->ev_d0) ctl->delta_ns += (long long)(ctl->ev_t1 - ctl->ev_d0);
+            if (win->ev_r1 > win->ev_t0) ctl->res_ns += (long long)(win->ev_r1 - win->ev_t0);
+            if (win->ev_t1 > win->ev_d0) ctl->delta_ns += (long long)(win->ev_t1 - win->ev_d0);
         }
-        ctl->ev_t0 = ~0ull;
-        ctl->ev_t1 = 0ull;
-        ctl->ev_r1 = 0ull;
-        ctl->ev_d0 = ~0ull;
         ctl->tried += (ctl->select_mode == 0 && kept >= 0) ? kept + 1 : nc;
         ctl->ncand_row += nc;
         ctl->kept = kept >= 0;
@@ -696,15 +732,15 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
                 if (elem) ctl->pos = cd[6] + 1;   // ByElement: the scan goes on from the next element
                 put_trace(ctl, cd[6], cd[0], cd[1], cd[2], ctl->f_new);
                 ctl->row_done = 1;
-            } else if (ctl->exhausted) {
+            } else if (win->exhausted) {
                 if (mat) ctl->i = -1;
                 if (!elem) put_trace(ctl, -1, -1, -1, -1, ctl->f);
                 ctl->row_done = 1;
             } else {
-                ctl->wj = min(ctl->wj * 2, ctl->wmax / 2);
                 ctl->row_done = 0;
             }
             if (ctl->row_done) {
+                if (other && other->live) ctl->discarded += other->nc;   // evaluated ahead, not needed
                 if (mat) {
                     ctl->more = 0;            // ByMatrix: one iteration per sweep
                 } else if (elem) {
@@ -727,6 +763,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
             }
             if (in_graph) {
                 cudaGraphSetConditional(h_win, ctl->row_done ? 0u : 1u);
+                cudaGraphSetConditional(h_step, ctl->row_done ? 0u : 1u);
                 if (ctl->row_done) {
                     cudaGraphSetConditional(h_dirty, kept >= 0 ? 1u : 0u);
                     cudaGraphSetConditional(h_row, ctl->more ? 1u : 0u);
@@ -743,14 +780,23 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, int nblk, int i
     }
     if (!single) {
         __syncthreads();
-        if (!ctl->row_done) build_window(P, ctl, false);
+        if (!ctl->row_done) {
+            build_window(P, ctl, false);
+        } else if (tid == 0) {
+            win->nc = 0;          // nothing to seed or evaluate in this buffer
+            win->live = 0;
+        }
     }
     ctl_store(P.ctl, sctl);
 }
 
-// Start of a row: row state reset and the row's first window; in a graph,
-// opens the window loop.
-__global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph, cudaGraphConditionalHandle h_win,
+// Start of a row: row state reset and the row's first window, built into
+// the buffer P points at; the other buffer (`other`) is emptied, so the
+// first pipeline step has nothing to decide.  In a graph, opens the window
+// loop.
+__global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, stmf_win *other, int in_graph,
+                                                    cudaGraphConditionalHandle h_win,
+                                                    cudaGraphConditionalHandle h_step,
                                                     cudaGraphConditionalHandle h_row)
 {
     __shared__ stmf_ctl sctl;
@@ -760,17 +806,26 @@ __global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, int in_graph
     if (threadIdx.x == 0) {
         if (P.strategy != STMF_STRATEGY_BYELEMENT) ctl->pos = 0;   // ByElement: the scan position carries on
         ctl->ncand_row = 0;
+        ctl->nbuilt = 0;
         ctl->wj = ctl->wj0;
         ctl->kept = 0;
         ctl->row_done = 0;
         ctl->win_row = 0;
+        other->nc = 0;
+        other->live = 0;
         // more row visits in this sweep than the sweep has rows (segments):
         // stop every loop
         if (++ctl->rows_sweep > ctl->row_cap) ctl->err = STMF_ERR_TIMEOUT;
         sstop = ctl->err == STMF_ERR_TIMEOUT;
-        if (sstop) { ctl->row_done = 1; ctl->more = 0; }
+        if (sstop) {
+            ctl->row_done = 1;
+            ctl->more = 0;
+            P.win->nc = 0;
+            P.win->live = 0;
+        }
         if (in_graph) {
             cudaGraphSetConditional(h_win, sstop ? 0u : 1u);
+            cudaGraphSetConditional(h_step, sstop ? 0u : 1u);
             if (sstop) cudaGraphSetConditional(h_row, 0u);
         }
     }
@@ -816,21 +871,29 @@ __global__ void k_sweep_end(stmf_problem P, cudaGraphConditionalHandle h_sweep)
     cudaGraphSetConditional(h_sweep, (ctl->sweep < ctl->sweep_target && !converged && !ctl->err) ? 1u : 0u);
 }
 
-// One explicit candidate (stmf_update_U / stmf_update_V): slot 0.
+// One explicit candidate (stmf_update_U / stmf_update_V): slot 0 of the
+// buffer P points at.
 __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
 {
     stmf_ctl *ctl = P.ctl;
+    stmf_win *win = P.win;
     int *c0 = P.cand;
     c0[0] = j; c0[1] = k; c0[2] = type; c0[3] = 0; c0[4] = 0; c0[5] = i; c0[6] = 0;
     ctl->i = i;
-    ctl->nc = 1;
-    ctl->nu = type == 0 ? 1 : 0;
-    ctl->nv = type == 1 ? 1 : 0;
-    ctl->ulist[0] = 0;
-    ctl->vlist[0] = 0;
-    ctl->alist[0] = 0;
-    ctl->na = 1;
-    ctl->exhausted = 1;
+    win->nc = 1;
+    win->nu = type == 0 ? 1 : 0;
+    win->nv = type == 1 ? 1 : 0;
+    win->ulist[0] = 0;
+    win->vlist[0] = 0;
+    win->alist[0] = 0;
+    win->na = 1;
+    win->exhausted = 1;
+    win->live = 1;
+    win->screened = 0;
+    win->ev_t0 = ~0ull;
+    win->ev_t1 = 0ull;
+    win->ev_r1 = 0ull;
+    win->ev_d0 = ~0ull;
     ctl->ncand_row = 0;
     ctl->select_mode = 0;
 }
@@ -944,27 +1007,37 @@ cudaError_t launch_eval(cudaStream_t st, stmf_problem *P, int mode)
     return e;
 }
 
-// One window of a row (its candidates were chosen by k_row_begin or by the
-// previous k_select): seeds, evaluation, decision and the next window.  With
-// FP16 screening the evaluation splits into phase 1 (every candidate's
+// Evaluation of the window in buffer b (its slots were seeded one step
+// earlier).  With FP16 screening it splits into phase 1 (every candidate's
 // U'/V'), the screen, and phase 2 over the candidates it kept.
-cudaError_t launch_window_body(cudaStream_t st, stmf_problem *P, int in_graph)
+cudaError_t launch_window_eval(cudaStream_t st, stmf_problem *P, int b)
 {
-    cudaError_t e = launch_seed(st, P, P->ctl_host->wmax);
+    stmf_problem v = window_view(P, b);
     if (P->precision == 1) {
-        if (e == cudaSuccess) e = launch_eval(st, P, 1);
-        if (e == cudaSuccess) e = launch_screen(st, P);
-        if (e == cudaSuccess) e = launch_eval(st, P, 2);
-    } else if (e == cudaSuccess) {
-        e = launch_eval(st, P, 0);
+        cudaError_t e = launch_eval(st, &v, 1);
+        if (e == cudaSuccess) e = launch_screen(st, &v);
+        if (e == cudaSuccess) e = launch_eval(st, &v, 2);
+        return e;
     }
-    if (e == cudaSuccess) e = launch_select(st, P, in_graph, 0);
+    return launch_eval(st, &v, 0);
+}
+
+// Decision of the window in buffer b, the build of the next window into it
+// and that window's seeds.
+cudaError_t launch_window_next(cudaStream_t st, stmf_problem *P, int b, int in_graph)
+{
+    stmf_problem v = window_view(P, b);
+    k_select<<<1, 1024, 0, st>>>(v, P->win + (1 - b), delta_parts(P), in_graph, 0, P->h_row, P->h_dirty, P->h_win,
+                                 P->h_step);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_seed(st, &v, P->ctl_host->wmax);
     return e;
 }
 
-cudaError_t launch_select(cudaStream_t st, stmf_problem *P, int in_graph, int single)
+// The decision of a single explicit candidate (buffer 0).
+cudaError_t launch_select_single(cudaStream_t st, stmf_problem *P)
 {
-    k_select<<<1, 1024, 0, st>>>(*P, delta_parts(P), in_graph, single, P->h_row, P->h_dirty, P->h_win);
+    k_select<<<1, 1024, 0, st>>>(*P, nullptr, delta_parts(P), 0, 1, P->h_row, P->h_dirty, P->h_win, P->h_step);
     return cudaGetLastError();
 }
 
@@ -990,8 +1063,9 @@ cudaError_t launch_row_begin(cudaStream_t st, stmf_problem *P, int in_graph)
         const cudaError_t e = launch_matrix_order(st, P);  // the iteration's order of all given elements
         if (e != cudaSuccess) return e;
     }
-    k_row_begin<<<1, 1024, 0, st>>>(*P, in_graph, P->h_win, P->h_row);
-    return cudaGetLastError();
+    k_row_begin<<<1, 1024, 0, st>>>(*P, P->win + 1, in_graph, P->h_win, P->h_step, P->h_row);
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : launch_seed(st, P, P->ctl_host->wmax);   // window 0 (buffer 0)
 }
 
 cudaError_t launch_job_begin(cudaStream_t st, stmf_problem *P)

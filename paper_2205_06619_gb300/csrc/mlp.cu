@@ -2,10 +2,11 @@
 // with Random Acol).  A row of R is summarised by a 32-quantile sketch of its
 // given entries, centred on the row median; an MLP 32 -> 128 -> 128 -> r
 // (ReLU) maps the sketch to the row of U minus the median.  Weights are held
-// in BF16 for the forward pass and in FP32 (master copy) for Adam; every
-// product accumulates in FP32.  Kernels here: the row sketch, forward,
-// backward (deterministic: every gradient element is one thread's fixed-order
-// sum over the batch), Adam and the BF16 refresh.
+// in BF16 for the products and in FP32 (master copy) for Adam.  Every matrix
+// product of the forward and backward passes runs on the tensor cores
+// (mma.sync, BF16 operands, FP32 accumulation, fixed order: reproducible).
+// Kernels here: the row sketch, the GEMM with its epilogues, the loss, the
+// bias gradients, Adam and the BF16 refresh.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -71,51 +72,99 @@ __global__ void __launch_bounds__(1024) k_row_sketch(const float *__restrict__ R
     if (threadIdx.x == 0) med[s] = md;
 }
 
-// ---------------------------------------------------------------- forward
-// 32 rows of the batch per block, one thread per hidden unit.  Stores the
-// hidden activations for the backward pass (H1, H2 may be NULL at inference).
-__global__ void __launch_bounds__(HID) k_mlp_fwd(int B, int r, const float *__restrict__ X,
-                                                 const __nv_bfloat16 *__restrict__ W1, const float *__restrict__ b1,
-                                                 const __nv_bfloat16 *__restrict__ W2, const float *__restrict__ b2,
-                                                 const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ b3,
-                                                 float *__restrict__ H1, float *__restrict__ H2, float *__restrict__ Y)
+// ------------------------------------------------------- tensor-core GEMM
+// C[M x N] = A[M x K] * B[K x N] on the tensor cores (mma.sync m16n8k16,
+// BF16 operands, FP32 accumulation), for every product of the network's
+// forward and backward passes.  A(i, k) = A[i*sai + k*sak] and
+// B(k, j) = B[k*sbk + j*sbj] are FP32 (activations, gradients: rounded to
+// BF16 to nearest even when staged) or BF16 (weights).  Block: 4 warps, a
+// 64 x 32 tile of C; warp w owns rows 16w..16w+15 of it, four 8-column MMA
+// tiles; K in chunks of 32 through shared memory (rows padded to 40 BF16 so
+// the fragment loads are free of bank conflicts).  Epilogues:
+//   EPI_STORE     C = acc
+//   EPI_BIAS_RELU C = max(acc + bias[j], 0)
+//   EPI_BIAS      C = acc + bias[j]
+//   EPI_MASK      C = H(i, j) > 0 ? acc : 0   (ReLU derivative, H FP32)
+// The summation order is fixed, so the results are reproducible.
+enum { EPI_STORE = 0, EPI_BIAS_RELU = 1, EPI_BIAS = 2, EPI_MASK = 3 };
+constexpr int GBM = 64, GBN = 32, GBK = 32, GPAD = 40;
+
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ __nv_bfloat16 to_bf16(__nv_bfloat16 x) { return x; }
+
+template <class TA, class TB, int EPI>
+__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const TA *__restrict__ A, int sai, int sak,
+                                                   const TB *__restrict__ B, int sbk, int sbj,
+                                                   const float *__restrict__ bias, const float *__restrict__ H,
+                                                   int ldh, float *__restrict__ C, int ldc)
 {
-    __shared__ float sx[32][SK];
-    __shared__ float sh1[32][HID + 1];
-    __shared__ float sh2[32][HID + 1];
-    const int j = threadIdx.x, row0 = blockIdx.x * 32;
-    const int nr = min(32, B - row0);
-    for (int e = j; e < 32 * SK; e += HID) {
-        const int a = e / SK, c = e % SK;
-        sx[a][c] = a < nr ? X[(size_t)(row0 + a) * SK + c] : 0.f;
-    }
-    __syncthreads();
-    float w[SK];
+    __shared__ __align__(16) __nv_bfloat16 As[GBM][GPAD];     // [row][k]
+    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GPAD];     // [col][k] (transposed: k pairs adjacent)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = lane >> 2, tig = lane & 3;
+    const int i0 = blockIdx.y * GBM, j0 = blockIdx.x * GBN;
+    float acc[4][4];
 #pragma unroll
-    for (int i = 0; i < SK; ++i) w[i] = __bfloat162float(W1[i * HID + j]);
-    for (int a = 0; a < nr; ++a) {
-        float acc = b1[j];
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
-        for (int i = 0; i < SK; ++i) acc = fmaf(sx[a][i], w[i], acc);
-        acc = fmaxf(acc, 0.f);
-        sh1[a][j] = acc;
-        if (H1) H1[(size_t)(row0 + a) * HID + j] = acc;
+        for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+        __syncthreads();
+        // stage A (64 x 32) and B (32 x 32); the index that is contiguous in
+        // memory runs fastest across threads
+        for (int e = tid; e < GBM * GBK; e += 128) {
+            const int r = sak == 1 ? e / GBK : e % GBM, c = sak == 1 ? e % GBK : e / GBM;
+            const int i = i0 + r, k = k0 + c;
+            As[r][c] = (i < M && k < K) ? to_bf16(A[(size_t)i * sai + (size_t)k * sak]) : __float2bfloat16_rn(0.f);
+        }
+        for (int e = tid; e < GBK * GBN; e += 128) {
+            const int c = sbj == 1 ? e % GBN : e / GBK, kk = sbj == 1 ? e / GBN : e % GBK;
+            const int j = j0 + c, k = k0 + kk;
+            Bs[c][kk] = (j < N && k < K) ? to_bf16(B[(size_t)k * sbk + (size_t)j * sbj]) : __float2bfloat16_rn(0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < GBK; ks += 16) {
+            const int ra = warp * 16 + grp;
+            uint32_t a[4];
+            a[0] = *reinterpret_cast<const uint32_t *>(&As[ra][ks + 2 * tig]);
+            a[1] = *reinterpret_cast<const uint32_t *>(&As[ra + 8][ks + 2 * tig]);
+            a[2] = *reinterpret_cast<const uint32_t *>(&As[ra][ks + 2 * tig + 8]);
+            a[3] = *reinterpret_cast<const uint32_t *>(&As[ra + 8][ks + 2 * tig + 8]);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int cb = t * 8 + grp;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&Bs[cb][ks + 2 * tig]);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&Bs[cb][ks + 2 * tig + 8]);
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                    "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+                    : "+f"(acc[t][0]), "+f"(acc[t][1]), "+f"(acc[t][2]), "+f"(acc[t][3])
+                    : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+            }
+        }
     }
-    __syncthreads();
-    for (int a = 0; a < nr; ++a) {
-        float acc = b2[j];
-        for (int i = 0; i < HID; ++i) acc = fmaf(sh1[a][i], __bfloat162float(W2[i * HID + j]), acc);
-        acc = fmaxf(acc, 0.f);
-        sh2[a][j] = acc;
-        if (H2) H2[(size_t)(row0 + a) * HID + j] = acc;
-    }
-    __syncthreads();
-    for (int e = j; e < nr * r; e += HID) {
-        const int a = e / r, o = e % r;
-        float acc = b3[o];
-        for (int i = 0; i < HID; ++i) acc = fmaf(sh2[a][i], __bfloat162float(W3[i * r + o]), acc);
-        Y[(size_t)(row0 + a) * r + o] = acc;
-    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + warp * 16 + grp + (q >= 2 ? 8 : 0);
+            const int j = j0 + t * 8 + 2 * tig + (q & 1);
+            if (i >= M || j >= N) continue;
+            float v = acc[t][q];
+            if (EPI == EPI_BIAS_RELU) v = fmaxf(v + bias[j], 0.f);
+            if (EPI == EPI_BIAS) v = v + bias[j];
+            if (EPI == EPI_MASK) v = H[(size_t)i * ldh + j] > 0.f ? v : 0.f;
+            C[(size_t)i * ldc + j] = v;
+        }
+}
+
+template <class TA, class TB, int EPI>
+void gemm(cudaStream_t st, int M, int N, int K, const TA *A, int sai, int sak, const TB *B, int sbk, int sbj,
+          const float *bias, const float *H, int ldh, float *C, int ldc)
+{
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
+    k_gemm_bf16<TA, TB, EPI><<<grid, 128, 0, st>>>(M, N, K, A, sai, sak, B, sbk, sbj, bias, H, ldh, C, ldc);
 }
 
 // ---------------------------------------------------------------- backward
@@ -134,34 +183,14 @@ __global__ void k_mse(int B, int r, const float *__restrict__ Y, const float *__
     rowloss[a] = l / (double)(B * r);
 }
 
-// dH[a][i] = (H[a][i] > 0) * sum_o dOut[a][o] * W[i][o]   (W: in x out, BF16)
-__global__ void k_back_act(int B, int in, int out, const float *__restrict__ dOut, const __nv_bfloat16 *__restrict__ W,
-                           const float *__restrict__ H, float *__restrict__ dH)
+// gb[o] = sum over a of dOut[a][o] in batch order (the bias gradients)
+__global__ void k_colsum(int B, int out, const float *__restrict__ dOut, float *__restrict__ gb)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= B * in) return;
-    const int a = e / in, i = e % in;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= out) return;
     float acc = 0.f;
-    for (int o = 0; o < out; ++o) acc = fmaf(dOut[(size_t)a * out + o], __bfloat162float(W[(size_t)i * out + o]), acc);
-    dH[e] = H[e] > 0.f ? acc : 0.f;
-}
-
-// gW[i][o] = sum_a In[a][i] * dOut[a][o];  gb[o] = sum_a dOut[a][o]  (fixed order over a)
-__global__ void k_back_w(int B, int in, int out, const float *__restrict__ In, const float *__restrict__ dOut,
-                         float *__restrict__ gW, float *__restrict__ gb)
-{
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < in * out) {
-        const int i = e / out, o = e % out;
-        float acc = 0.f;
-        for (int a = 0; a < B; ++a) acc = fmaf(In[(size_t)a * in + i], dOut[(size_t)a * out + o], acc);
-        gW[e] = acc;
-    } else if (e < in * out + out) {
-        const int o = e - in * out;
-        float acc = 0.f;
-        for (int a = 0; a < B; ++a) acc += dOut[(size_t)a * out + o];
-        gb[o] = acc;
-    }
+    for (int a = 0; a < B; ++a) acc += dOut[(size_t)a * out + o];
+    gb[o] = acc;
 }
 
 // Adam (Kingma and Ba) on the FP32 master parameters, then the BF16 copy.
@@ -238,11 +267,16 @@ cudaError_t mlp_reserve(stmf_mlp *M, int B)
     return e;
 }
 
+// Forward pass: H1 = relu(X W1 + b1), H2 = relu(H1 W2 + b2), Y = H2 W3 + b3
+// (H1, H2: the buffers kept for the backward pass, or scratch).
 void launch_fwd(stmf_mlp *M, int B, const float *X, float *H1, float *H2, float *Y)
 {
     const __nv_bfloat16 *W1 = M->pb, *W2 = W1 + SK * HID, *W3 = W2 + HID * HID;
     const float *b1 = M->p + M->nw, *b2 = b1 + HID, *b3 = b2 + HID;
-    k_mlp_fwd<<<(B + 31) / 32, HID, 0, M->ctx->stream>>>(B, M->r, X, W1, b1, W2, b2, W3, b3, H1, H2, Y);
+    cudaStream_t st = M->ctx->stream;
+    gemm<float, __nv_bfloat16, EPI_BIAS_RELU>(st, B, HID, SK, X, SK, 1, W1, HID, 1, b1, nullptr, 0, H1, HID);
+    gemm<float, __nv_bfloat16, EPI_BIAS_RELU>(st, B, HID, HID, H1, HID, 1, W2, HID, 1, b2, nullptr, 0, H2, HID);
+    gemm<float, __nv_bfloat16, EPI_BIAS>(st, B, M->r, HID, H2, HID, 1, W3, M->r, 1, b3, nullptr, 0, Y, M->r);
 }
 
 // U0[s][l] = Y[s][l] + median[s]
@@ -253,13 +287,102 @@ __global__ void k_add_median(const float *__restrict__ Y, const float *__restric
     if (e < m * r) U0[e] = Y[e] + med[e / r];
 }
 
+// ------------------------------------------------------------ targets
+// The gauge of a factorization: U (x) V is unchanged by U_.l + c, V_l. - c
+// for any c per component, and by any order of the components.  Training
+// targets fix it: c_l = max over t < n of V_lt (so that max_t V'_lt = 0), and
+// the components go in decreasing order of their sum over rows of U_sl + c_l
+// (FP64, rows in index order; equal sums keep the smaller l first).
+__global__ void __launch_bounds__(256) k_tgt_colmax(int n, const float *__restrict__ V, int ldv,
+                                                    float *__restrict__ c)
+{
+    __shared__ float red[8];
+    const int l = blockIdx.x;
+    float x = -INFINITY;
+    for (int t = threadIdx.x; t < n; t += 256) x = fmaxf(x, V[(size_t)l * ldv + t]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) x = fmaxf(x, red[w]);
+        c[l] = x;
+    }
+}
+
+// One warp: lane l sums its component in row order, then the lanes rank the
+// sums; order[p] = the component at position p.
+__global__ void k_tgt_order(int m, int r, const float *__restrict__ U, int ldu, const float *__restrict__ c,
+                            int *__restrict__ order)
+{
+    const int l = threadIdx.x;
+    double key = -INFINITY;
+    if (l < r) {
+        key = 0.0;
+        for (int s = 0; s < m; ++s) key += (double)(U[(size_t)s * ldu + l] + c[l]);
+    }
+    int pos = 0;
+    for (int q = 0; q < r; ++q) {
+        const double kq = __shfl_sync(0xffffffffu, key, q);
+        pos += (kq > key || (kq == key && q < l)) ? 1 : 0;
+    }
+    if (l < r) order[pos] = l;
+}
+
+// Rank of lane l's value x among the r lanes, in decreasing order (equal
+// values: the smaller lane first).
+__device__ __forceinline__ int desc_rank(float x, int l, int r)
+{
+    int pos = 0;
+    for (int q = 0; q < r; ++q) {
+        const float xq = __shfl_sync(0xffffffffu, x, q);
+        pos += (xq > x || (xq == x && q < l)) ? 1 : 0;
+    }
+    return pos;
+}
+
+// One warp per row: T[s][p] = (U_s,order[p] + c_order[p]) - median[s]
+// (canonical), or the row's values U_sl + c_l in decreasing order, minus the
+// median (sorted).  FP32.
+__global__ void __launch_bounds__(256) k_tgt_rows(int m, int r, const float *__restrict__ U, int ldu,
+                                                  const float *__restrict__ c, const int *__restrict__ order,
+                                                  const float *__restrict__ median, int sorted,
+                                                  float *__restrict__ T)
+{
+    const int s = blockIdx.x * 8 + (threadIdx.x >> 5), l = threadIdx.x & 31;
+    if (s >= m) return;
+    const int comp = sorted ? l : (l < r ? order[l] : 0);
+    const float x = l < r ? U[(size_t)s * ldu + comp] + c[comp] : -INFINITY;
+    const int p = sorted ? desc_rank(x, l, r) : l;
+    if (l < r) T[(size_t)s * r + p] = x - median[s];
+}
+
+// One warp per row: out[s][l] = the value of Y[s] whose rank (decreasing)
+// equals the rank of U_ref[s][l] in its row (decreasing; equal values: the
+// smaller index first).
+__global__ void __launch_bounds__(256) k_assign_by_rank(int m, int r, const float *__restrict__ Y, int ldy,
+                                                        const float *__restrict__ Uref, int ldu,
+                                                        float *__restrict__ out, int ldo)
+{
+    __shared__ float sv[8][32];
+    const int w = threadIdx.x >> 5, s = blockIdx.x * 8 + w, l = threadIdx.x & 31;
+    if (s >= m) return;               // whole warps leave together
+    const float y = l < r ? Y[(size_t)s * ldy + l] : -INFINITY;
+    const float u = l < r ? Uref[(size_t)s * ldu + l] : -INFINITY;
+    const int ry = desc_rank(y, l, r), ru = desc_rank(u, l, r);
+    if (l < r) sv[w][ry] = y;
+    __syncwarp();
+    if (l < r) out[(size_t)s * ldo + l] = sv[w][ru];
+}
+
 }  // namespace
 
 // Learned initial rows of a problem (the addition to Algorithm 3's Random
 // Acol start): U0[s] = MLP(sketch of row s) + median of row s, with the row's
-// given entries those of R that are not NaN.  Runs on ctx's stream, which must
-// be the MLP's.
-stmf_status mlp_predict_rows(stmf_ctx *ctx, stmf_mlp *M, int m, int n, const float *R, int ldr, float *U0)
+// given entries those the mask marks (mask NULL: those of R that are not
+// NaN).  Runs on ctx's stream, which must be the MLP's.
+stmf_status mlp_predict_rows(stmf_ctx *ctx, stmf_mlp *M, int m, int n, const float *R, int ldr,
+                             const uint32_t *mask, int ldm_words, float *U0)
 {
     if (M->ctx != ctx) return mfail(ctx, STMF_ERR_INVALID, "the MLP was created on another context");
     if (n > 12288) return mfail(ctx, STMF_ERR_INVALID, "learned initialisation needs n <= 12288 (row sketch)");
@@ -268,17 +391,18 @@ stmf_status mlp_predict_rows(stmf_ctx *ctx, stmf_mlp *M, int m, int n, const flo
     cudaError_t e = cudaMalloc(&buf, sizeof(float) * (nsk + nmd + ny));
     if (e != cudaSuccess) return mfail(ctx, STMF_ERR_OOM, cudaGetErrorString(e));
     float *sk = buf, *md = buf + nsk, *Y = md + nmd;
+    if (e == cudaSuccess) e = mlp_reserve(M, m);     // hidden activations of the forward pass
     int np2 = 1;
     while (np2 < n) np2 <<= 1;
     const size_t smem = sizeof(float) * np2;
-    if (smem > 48 * 1024)
+    if (e == cudaSuccess && smem > 48 * 1024)
         e = cudaFuncSetAttribute(k_row_sketch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        k_row_sketch<<<m, 1024, smem, ctx->stream>>>(R, ldr, nullptr, 0, m, n, np2, sk, md);
+        k_row_sketch<<<m, 1024, smem, ctx->stream>>>(R, ldr, mask, ldm_words, m, n, np2, sk, md);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        launch_fwd(M, m, sk, nullptr, nullptr, Y);
+        launch_fwd(M, m, sk, M->H1, M->H2, Y);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -368,8 +492,9 @@ stmf_status stmf_mlp_forward(stmf_mlp *M, int B, const float *X, float *Y)
 {
     if (!M || B < 1 || !X || !Y) return STMF_ERR_INVALID;
     cudaError_t e = cudaSetDevice(M->ctx->device);
+    if (e == cudaSuccess) e = mlp_reserve(M, B);
     if (e == cudaSuccess) {
-        launch_fwd(M, B, X, nullptr, nullptr, Y);
+        launch_fwd(M, B, X, M->H1, M->H2, Y);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? STMF_OK : mfail(M->ctx, STMF_ERR_CUDA, cudaGetErrorString(e));
@@ -387,13 +512,20 @@ stmf_status stmf_mlp_gradient(stmf_mlp *M, int B, const float *X, const float *T
     const __nv_bfloat16 *W2 = M->pb + SK * HID, *W3 = W2 + HID * HID;
     float *gW1 = M->g, *gW2 = gW1 + SK * HID, *gW3 = gW2 + HID * HID;
     float *gb1 = M->g + M->nw, *gb2 = gb1 + HID, *gb3 = gb2 + HID;
+    // forward, then per layer: weight gradient In^T dOut, bias gradient (the
+    // column sums of dOut) and the gradient of the layer's input
+    // (dOut W^T masked by the ReLU derivative), all GEMMs on the tensor cores
     launch_fwd(M, B, X, M->H1, M->H2, M->Y);
     k_mse<<<(B + 255) / 256, 256, 0, st>>>(B, r, M->Y, T, M->dY, M->rowloss);
-    k_back_w<<<(HID * r + r + 255) / 256, 256, 0, st>>>(B, HID, r, M->H2, M->dY, gW3, gb3);
-    k_back_act<<<(B * HID + 255) / 256, 256, 0, st>>>(B, HID, r, M->dY, W3, M->H2, M->dH2);
-    k_back_w<<<(HID * HID + HID + 255) / 256, 256, 0, st>>>(B, HID, HID, M->H1, M->dH2, gW2, gb2);
-    k_back_act<<<(B * HID + 255) / 256, 256, 0, st>>>(B, HID, HID, M->dH2, W2, M->H1, M->dH1);
-    k_back_w<<<(SK * HID + HID + 255) / 256, 256, 0, st>>>(B, SK, HID, X, M->dH1, gW1, gb1);
+    gemm<float, float, EPI_STORE>(st, HID, r, B, M->H2, 1, HID, M->dY, r, 1, nullptr, nullptr, 0, gW3, r);
+    k_colsum<<<1, 128, 0, st>>>(B, r, M->dY, gb3);
+    gemm<float, __nv_bfloat16, EPI_MASK>(st, B, HID, r, M->dY, r, 1, W3, 1, r, nullptr, M->H2, HID, M->dH2, HID);
+    gemm<float, float, EPI_STORE>(st, HID, HID, B, M->H1, 1, HID, M->dH2, HID, 1, nullptr, nullptr, 0, gW2, HID);
+    k_colsum<<<1, 128, 0, st>>>(B, HID, M->dH2, gb2);
+    gemm<float, __nv_bfloat16, EPI_MASK>(st, B, HID, HID, M->dH2, HID, 1, W2, 1, HID, nullptr, M->H1, HID, M->dH1,
+                                         HID);
+    gemm<float, float, EPI_STORE>(st, SK, HID, B, X, 1, SK, M->dH1, HID, 1, nullptr, nullptr, 0, gW1, HID);
+    k_colsum<<<1, 128, 0, st>>>(B, HID, M->dH1, gb1);
     e = cudaGetLastError();
     if (e == cudaSuccess && loss) {
         std::vector<double> h(B);
@@ -406,6 +538,54 @@ stmf_status stmf_mlp_gradient(stmf_mlp *M, int B, const float *X, const float *T
     if (e == cudaSuccess && grad_host) {
         e = cudaMemcpyAsync(grad_host, M->g, sizeof(float) * M->np, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return e == cudaSuccess ? STMF_OK : mfail(ctx, STMF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+stmf_status stmf_mlp_predict(stmf_mlp *M, int m, int n, const float *R, int ldr, const uint32_t *mask,
+                             int ldm_words, float *U0)
+{
+    if (!M) return STMF_ERR_INVALID;
+    stmf_ctx *ctx = M->ctx;
+    if (m < 1 || n < 1 || !R || !U0 || ldr < n) return mfail(ctx, STMF_ERR_INVALID, "bad prediction arguments");
+    if (mask && ldm_words < (n + 31) / 32) return mfail(ctx, STMF_ERR_INVALID, "ldm_words < ceil(n/32)");
+    const cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return mfail(ctx, STMF_ERR_CUDA, cudaGetErrorString(e));
+    return mlp_predict_rows(ctx, M, m, n, R, ldr, mask, ldm_words, U0);
+}
+
+stmf_status stmf_mlp_targets(stmf_ctx *ctx, int m, int n, int r, const float *U, int ldu, const float *V, int ldv,
+                             const float *median, int sorted, float *T)
+{
+    if (!ctx) return STMF_ERR_INVALID;
+    if (m < 1 || n < 1 || r < 1 || r > STMF_MAX_RANK || ldu < r || ldv < n || !U || !V || !median || !T)
+        return mfail(ctx, STMF_ERR_INVALID, "bad target arguments");
+    cudaStream_t st = ctx->stream;
+    void *buf = nullptr;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&buf, sizeof(float) * STMF_MAX_RANK + sizeof(int) * STMF_MAX_RANK);
+    if (e != cudaSuccess) return mfail(ctx, STMF_ERR_OOM, cudaGetErrorString(e));
+    float *c = static_cast<float *>(buf);
+    int *order = reinterpret_cast<int *>(c + STMF_MAX_RANK);
+    k_tgt_colmax<<<r, 256, 0, st>>>(n, V, ldv, c);
+    k_tgt_order<<<1, 32, 0, st>>>(m, r, U, ldu, c, order);
+    k_tgt_rows<<<(m + 7) / 8, 256, 0, st>>>(m, r, U, ldu, c, order, median, sorted ? 1 : 0, T);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the scratch lives until the kernels end
+    cudaFree(buf);
+    return e == cudaSuccess ? STMF_OK : mfail(ctx, STMF_ERR_CUDA, cudaGetErrorString(e));
+}
+
+stmf_status stmf_assign_by_rank(stmf_ctx *ctx, int m, int r, const float *Y, int ldy, const float *U_ref, int ldu,
+                                float *out, int ldo)
+{
+    if (!ctx) return STMF_ERR_INVALID;
+    if (m < 1 || r < 1 || r > STMF_MAX_RANK || ldy < r || ldu < r || ldo < r || !Y || !U_ref || !out || out == Y)
+        return mfail(ctx, STMF_ERR_INVALID, "bad rank-assignment arguments");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) {
+        k_assign_by_rank<<<(m + 7) / 8, 256, 0, ctx->stream>>>(m, r, Y, ldy, U_ref, ldu, out, ldo);
+        e = cudaGetLastError();
     }
     return e == cudaSuccess ? STMF_OK : mfail(ctx, STMF_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -115,7 +115,7 @@ void problem_free(stmf_problem *P)
     if (P->sweep_graph) cudaGraphDestroy(P->sweep_graph);
     void *ptrs[] = {P->R, P->RT, P->U, P->V, P->P1, P->P2, P->A, P->cmin1, P->cmin2, P->carg,
                     P->rmin1, P->rmin2, P->rarg, P->tdpart, P->chpart, P->tdcol, P->colhist,
-                    P->rowhist, P->rank, P->order, P->cand, P->Uc, P->Vc, P->part, P->fc,
+                    P->rowhist, P->rank, P->order, P->win, P->cand, P->Uc, P->Vc, P->part, P->fc,
                     P->ctl, P->trace_dev, P->perm, P->Rh, P->P1h, P->P2h, P->scr_sum, P->scr_cnt,
                     P->scr_umax, P->scr_vmax, P->rowkey, P->rowrank, P->roworder, P->colarg, P->cperm,
                     P->tdr_seq, P->tdc_seq, P->skey, P->sval, P->scnt};
@@ -152,10 +152,12 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     A(dalloc(&P->rmin1, (size_t)r * mp)); A(dalloc(&P->rmin2, (size_t)r * mp)); A(dalloc(&P->rarg, (size_t)r * mp));
     A(dalloc(&P->tdpart, (size_t)nparts * np)); A(dalloc(&P->chpart, (size_t)nparts * np * r));
     A(dalloc(&P->tdcol, np)); A(dalloc(&P->colhist, np * r)); A(dalloc(&P->rowhist, STMF_MAX_RANK));
-    A(dalloc(&P->rank, np)); A(dalloc(&P->order, np)); A(dalloc(&P->cand, 8 * STMF_WMAX));
-    A(dalloc(&P->Uc, (size_t)STMF_WMAX * mp)); A(dalloc(&P->Vc, (size_t)STMF_WMAX * np));
-    A(dalloc(&P->part, (size_t)STMF_DELTA_MAX_BLOCKS_PER_SM * ctx->num_sms * STMF_WMAX));   // float2
-    A(dalloc(&P->fc, STMF_WMAX)); A(dalloc(&P->ctl, 1));
+    A(dalloc(&P->rank, np)); A(dalloc(&P->order, np));
+    // two window buffers (window_view)
+    A(dalloc(&P->win, 2)); A(dalloc(&P->cand, 2 * win_cand_elems()));
+    A(dalloc(&P->Uc, 2 * win_uc_elems(P))); A(dalloc(&P->Vc, 2 * win_vc_elems(P)));
+    A(dalloc(&P->part, 2 * win_part_elems(ctx->num_sms)));   // float2
+    A(dalloc(&P->fc, 2 * STMF_WMAX)); A(dalloc(&P->ctl, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&P->ctl_host, sizeof(stmf_ctl));
     if (e != cudaSuccess) {
         problem_free(P);
@@ -170,8 +172,6 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     c.wj0 = 2;
     c.wmax = window;
     c.dirty_k = -1;
-    c.ev_t0 = ~0ull;
-    c.ev_d0 = ~0ull;
     c.win_cap = c.row_cap = 1ll << 60;   // refined by the factorization's set-up
     e = cudaMemsetAsync(P->U, 0, sizeof(float) * mp * r, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->V, 0, sizeof(float) * r * np, st);
@@ -179,6 +179,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     if (e == cudaSuccess) e = cudaMemsetAsync(P->P2, 0, sizeof(float) * mp * np, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->A, 0, mp * np, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->win, 0, 2 * sizeof(stmf_win), st);   // empty, not live
     if (e != cudaSuccess) { problem_free(P); return fail(ctx, STMF_ERR_CUDA, "memset: %s", cudaGetErrorString(e)); }
     *out = P;
     return STMF_OK;
@@ -280,7 +281,7 @@ stmf_status update(stmf_problem *P, int i, int j, int k, int type, int commit_if
     CK(launch_single(st, P, i, j, k, type));
     CK(launch_seed(st, P, 1));
     CK(launch_eval(st, P));
-    CK(launch_select(st, P, 0, 1));
+    CK(launch_select_single(st, P));
     if (!commit_if_decreases) CK(launch_commit0(st, P));
     stmf_status s = read_ctl(P);
     if (s != STMF_OK) return s;
@@ -344,25 +345,70 @@ stmf_status add_conditional(stmf_ctx *ctx, cudaGraph_t g, const cudaGraphNode_t 
         if (s_ != STMF_OK) return s_;       \
     } while (0)
 
+// One pipeline step into graph g after the nodes deps: the evaluation of the
+// window in buffer b on `cap`, beside the decision of the window in buffer
+// 1 - b, the build of the next window into it and its seeds on `side`.  The
+// step's two end nodes go to ends (nullable).
+stmf_status capture_step(stmf_ctx *ctx, cudaStream_t cap, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join,
+                         cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps, stmf_problem *P, int b,
+                         std::vector<cudaGraphNode_t> *ends)
+{
+    CK(cudaStreamBeginCaptureToGraph(cap, g, deps, nullptr, ndeps, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(fork, cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+    if (e == cudaSuccess) e = launch_window_eval(cap, P, b);
+    if (e == cudaSuccess) e = launch_window_next(side, P, 1 - b, 1);
+    if (e == cudaSuccess) e = cudaEventRecord(join, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join, 0);
+    if (e == cudaSuccess && ends) {
+        cudaStreamCaptureStatus stat;
+        const cudaGraphNode_t *dep = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(cap, &stat, nullptr, nullptr, &dep, nullptr, &nd);
+        if (e == cudaSuccess) ends->assign(dep, dep + nd);
+    }
+    cudaGraph_t tmp;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &tmp);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(ctx, STMF_ERR_CUDA, "capture of a pipeline step: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return STMF_OK;
+}
+
 // Adds one problem's row loop to graph g (its conditional handles are created
 // on `top`, the graph that will be instantiated):
 //   sweep_begin;
 //   while (h_row) {
 //     if (h_dirty) { stats(k), planes, td_col/colhist, rank, order + f }
-//     row_begin;
-//     while (h_win) { window, seed, eval, select }
+//     row_begin (window 0 into buffer 0, its seeds);
+//     while (h_win) {
+//       eval(buffer 0) | select(buffer 1), next window into buffer 1, seeds;
+//       if (h_step) { eval(buffer 1) | select(buffer 0), next window into buffer 0, seeds }
+//     }
 //   }
+// ("|": two branches that run at the same time.)  Step t evaluates window t
+// while window t-1 is decided; when that decision ends the row, window t's
+// evaluation is dropped.
 // With job = true the row loop is wrapped in a device-driven sweep loop:
 //   job_begin; while (h_sweep) { <row loop>; sweep_end }
 stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, bool job, cudaStream_t cap)
 {
     stmf_ctx *ctx = P->ctx;
-    cudaGraphConditionalHandle hr, hd, hw, hs = 0;
+    cudaGraphConditionalHandle hr, hd, hw, hp, hs = 0;
     CK(cudaGraphConditionalHandleCreate(&hr, top, 0, 0));
     CK(cudaGraphConditionalHandleCreate(&hd, top, 0, 0));
     CK(cudaGraphConditionalHandleCreate(&hw, top, 0, 0));
+    CK(cudaGraphConditionalHandleCreate(&hp, top, 0, 0));
     if (job) CK(cudaGraphConditionalHandleCreate(&hs, top, 0, 0));
-    P->h_row = hr; P->h_dirty = hd; P->h_win = hw; P->h_sweep = hs;
+    P->h_row = hr; P->h_dirty = hd; P->h_win = hw; P->h_step = hp; P->h_sweep = hs;
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+    CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    struct SS { cudaStream_t s; ~SS() { cudaStreamDestroy(s); } } ss{side};
+    CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    struct EF { cudaEvent_t e; ~EF() { cudaEventDestroy(e); } } ef{fork};
+    CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    struct EJ { cudaEvent_t e; ~EJ() { cudaEventDestroy(e); } } ej{join};
 
     cudaGraph_t target = g;
     if (job) {
@@ -386,8 +432,12 @@ stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, b
     }, nullptr));
     CS(capture_into(ctx, cap, body_row, &nif, 1, [&](cudaStream_t c) { return launch_row_begin(c, P, 1); }, &rb));
     CS(add_conditional(ctx, body_row, &rb, 1, hw, cudaGraphCondTypeWhile, &wwin, &body_win));
-    CS(capture_into(ctx, cap, body_win, nullptr, 0, [&](cudaStream_t c) { return launch_window_body(c, P, 1); },
-                    nullptr));
+    std::vector<cudaGraphNode_t> ends;
+    CS(capture_step(ctx, cap, side, fork, join, body_win, nullptr, 0, P, 0, &ends));
+    cudaGraphNode_t nstep = nullptr;
+    cudaGraph_t body_step = nullptr;
+    CS(add_conditional(ctx, body_win, ends.data(), ends.size(), hp, cudaGraphCondTypeIf, &nstep, &body_step));
+    CS(capture_step(ctx, cap, side, fork, join, body_step, nullptr, 0, P, 1, nullptr));
     return STMF_OK;
 }
 
@@ -412,8 +462,23 @@ bool use_graph()
     return !(e && e[0] == '1');
 }
 
-// One sweep driven from the host (one synchronisation per window); used when
-// graphs are disabled.
+// One row (ByElement: segment; ByMatrix: iteration) driven from the host:
+// the graph's pipeline steps in order on one stream, one synchronisation per
+// step.
+stmf_status row_host(stmf_problem *P)
+{
+    stmf_ctx *ctx = P->ctx;
+    cudaStream_t st = ctx->stream;
+    CK(launch_row_begin(st, P, 0));
+    for (int b = 0;; b ^= 1) {
+        CK(launch_window_eval(st, P, b));
+        CK(launch_window_next(st, P, 1 - b, 0));
+        CS(read_ctl(P));
+        if (P->ctl_host->row_done) return STMF_OK;
+    }
+}
+
+// One sweep driven from the host; used when graphs are disabled.
 stmf_status sweep_host(stmf_problem *P)
 {
     stmf_ctx *ctx = P->ctx;
@@ -426,13 +491,8 @@ stmf_status sweep_host(stmf_problem *P)
             s = refresh(P);
             if (s != STMF_OK) return s;
         }
-        CK(launch_row_begin(st, P, 0));
-        while (true) {
-            CK(launch_window_body(st, P, 0));
-            s = read_ctl(P);
-            if (s != STMF_OK) return s;
-            if (P->ctl_host->row_done) break;
-        }
+        s = row_host(P);
+        if (s != STMF_OK) return s;
     }
     return STMF_OK;
 }
@@ -498,6 +558,10 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
         return fail(ctx, STMF_ERR_INVALID, "selection %d unknown", o.selection);
     if (o.strategy < STMF_STRATEGY_BYROW || o.strategy > STMF_STRATEGY_BYMATRIX)
         return fail(ctx, STMF_ERR_INVALID, "strategy %d unknown", o.strategy);
+    if (o.res_chunk && (o.res_chunk < 32 || o.res_chunk > 128 || o.res_chunk % 8))
+        return fail(ctx, STMF_ERR_INVALID, "res_chunk %d: 0 or a multiple of 8 in [32, 128]", o.res_chunk);
+    if (o.delta_blocks_per_sm < 0 || o.delta_blocks_per_sm > 5)
+        return fail(ctx, STMF_ERR_INVALID, "delta_blocks_per_sm %d outside [0, 5]", o.delta_blocks_per_sm);
     const bool elem = o.strategy == STMF_STRATEGY_BYELEMENT, mat = o.strategy == STMF_STRATEGY_BYMATRIX;
     if ((elem || mat) && (o.perm || o.selection != STMF_SEL_TD_A))
         return fail(ctx, STMF_ERR_INVALID, "the %s strategy takes no row permutation and no selection",
@@ -525,6 +589,8 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     P->transposed = tr; P->m0 = m0; P->n0 = n0;
     P->sel = o.selection;
     P->strategy = o.strategy;
+    P->res_chunk_sel = o.res_chunk;
+    P->delta_bps_sel = o.delta_blocks_per_sm;
     {
         cudaError_t ea = cudaSuccess;
         if (P->sel == STMF_SEL_TD) {
@@ -604,7 +670,7 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
             cudaGetLastError();
             return fail(ctx, STMF_ERR_OOM, "learned initialisation buffer");
         }
-        s = mlp_predict_rows(ctx, net, m, n, P->R, P->np, U0_learned);
+        s = mlp_predict_rows(ctx, net, m, n, P->R, P->np, nullptr, 0, U0_learned);
         if (s != STMF_OK) { cudaFree(U0_learned); problem_free(P); return s; }
     }
     s = problem_init(P, o.U0 ? o.U0 : U0_learned, o.acol_p, o.seed, o.picks, o.U0 ? o.V0 : nullptr);
@@ -714,6 +780,9 @@ void fill_report(const stmf_problem *P, stmf_report *rep)
     rep->candidates_screened = c.screened;
     rep->eval_res_ns = c.res_ns;
     rep->eval_delta_ns = c.delta_ns;
+    rep->candidates_discarded = c.discarded;
+    rep->eval_res_chunk = res_chunk(P);
+    rep->eval_delta_blocks = delta_grid(P);
 }
 
 stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *trace_out, int64_t trace_cap)
@@ -734,13 +803,22 @@ stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *tra
 }
 
 // ------------------------------------------------------------ autotuner
-// Picks the candidate window (candidates evaluated per device pass) of a
-// problem size class.  Each trial runs the first rows of sweep 0 on a scratch
-// copy of the problem, host-driven, and is scored by its device time: the
-// window evaluations' summed durations plus a fixed cost per window for the
-// window, seed and select kernels and the graph step.  Decisions do not depend
-// on the window, so only speed is compared.
+// Autotuner of a problem size class: the candidate window (candidates
+// evaluated per device pass), then the launch shapes of the window
+// evaluation (phase 1's column chunk, phase 2's blocks per SM).  Each trial
+// runs the first rows of sweep 0 on a scratch copy of the problem,
+// host-driven.  Decisions depend on none of these, so only speed is compared:
+// a window is scored by the evaluations' summed device durations, plus the
+// windows evaluated ahead and dropped, plus a fixed cost per pipeline step
+// (the graph step, and what of the decision branch is not hidden); the
+// shapes are scored per phase by the mean duration of that phase's launches,
+// from the same trials (at the chosen window, every trial evaluates the same
+// windows).
 constexpr double TUNE_WINDOW_OVERHEAD_S = 12e-6;
+
+struct tune_result {
+    int window, res_chunk, delta_bps;
+};
 
 stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, int ldr, const uint32_t *mask,
                          int ldm_words, const stmf_options *opts, stmf_problem **out);
@@ -754,32 +832,66 @@ uint64_t size_class(int m, int n, int r)
     return ((uint64_t)lg << 8) | (uint64_t)r;
 }
 
-stmf_status tune_window(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_options &base, int *best)
+// One trial: window w, shapes (chunk, bps) (0: defaults).  Returns the
+// window score and the mean phase durations; *chunk_used is the chunk the
+// trial ran with.
+stmf_status tune_trial(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_options &base, int w, int chunk,
+                       int bps, double *cost, double *res_s, double *delta_s, int *chunk_used)
 {
-    auto *cache = static_cast<std::map<uint64_t, int> *>(ctx->tune);
-    if (!cache) ctx->tune = cache = new std::map<uint64_t, int>();
+    stmf_options o = base;
+    o.window = w; o.trace = nullptr; o.trace_cap = 0; o.perm = nullptr; o.picks = nullptr; o.U0 = nullptr;
+    o.V0 = nullptr;
+    o.seed = bp.seed;
+    stmf_problem *P = nullptr;
+    CS(fastmf_begin(ctx, bp.m, bp.n, bp.r, bp.R, bp.ldr, bp.mask, bp.ldm_words, &o, &P));
+    P->res_chunk_sel = chunk;
+    P->delta_bps_sel = bps;
+    if (chunk_used) *chunk_used = res_chunk(P);
+    stmf_status s = sweep_rows_host(P, 24);
+    if (s == STMF_OK) s = read_ctl(P);
+    if (s != STMF_OK) { problem_free(P); return s; }
+    const stmf_ctl &c = *P->ctl_host;
+    // a dropped window costs about as much per candidate as the others
+    const double dropped = c.eval_cands ? c.eval_ns * 1e-9 * (double)c.discarded / (double)c.eval_cands : 0.0;
+    *cost = c.eval_ns * 1e-9 + dropped + c.windows * TUNE_WINDOW_OVERHEAD_S;
+    const double nl = c.eval_launches > 0 ? (double)c.eval_launches : 1.0;
+    *res_s = c.res_ns * 1e-9 / nl;
+    *delta_s = c.delta_ns * 1e-9 / nl;
+    problem_free(P);
+    return STMF_OK;
+}
+
+stmf_status tune_shapes(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_options &base, tune_result *best)
+{
+    auto *cache = static_cast<std::map<uint64_t, tune_result> *>(ctx->tune);
+    if (!cache) ctx->tune = cache = new std::map<uint64_t, tune_result>();
     const uint64_t key = size_class(bp.m, bp.n, bp.r);
     auto it = cache->find(key);
     if (it != cache->end()) { *best = it->second; return STMF_OK; }
     const int trial[3] = {16, 32, 64};
-    double best_cost = 1e30;
-    int best_w = 64;
+    double best_cost = 1e30, best_res = 0.0, best_delta = 0.0;
+    tune_result t = {64, 0, 0};
+    int chunk0 = 0;
     for (int w : trial) {
-        stmf_options o = base;
-        o.window = w; o.trace = nullptr; o.trace_cap = 0; o.perm = nullptr; o.picks = nullptr; o.U0 = nullptr;
-        o.V0 = nullptr;
-        o.seed = bp.seed;
-        stmf_problem *P = nullptr;
-        CS(fastmf_begin(ctx, bp.m, bp.n, bp.r, bp.R, bp.ldr, bp.mask, bp.ldm_words, &o, &P));
-        stmf_status s = sweep_rows_host(P, 24);
-        if (s == STMF_OK) s = read_ctl(P);
-        if (s != STMF_OK) { problem_free(P); return s; }
-        const double cost = P->ctl_host->eval_ns * 1e-9 + P->ctl_host->windows * TUNE_WINDOW_OVERHEAD_S;
-        problem_free(P);
-        if (cost < best_cost) { best_cost = cost; best_w = w; }
+        double cost, rs, ds;
+        int cu;
+        CS(tune_trial(ctx, bp, base, w, 0, 0, &cost, &rs, &ds, &cu));
+        if (cost < best_cost) { best_cost = cost; t.window = w; best_res = rs; best_delta = ds; chunk0 = cu; }
     }
-    (*cache)[key] = best_w;
-    *best = best_w;
+    // shapes at the chosen window: the heuristic's chunk and 5 blocks per SM
+    // (measured above) against neighbouring chunks and fewer blocks per SM
+    t.res_chunk = chunk0;
+    t.delta_bps = 5;
+    const int alt_chunk[2] = {chunk0 - 8, chunk0 + 8}, alt_bps[2] = {4, 3};
+    for (int a = 0; a < 2; ++a) {
+        const int ch = alt_chunk[a] >= 32 && alt_chunk[a] <= 128 ? alt_chunk[a] : chunk0;
+        double cost, rs, ds;
+        CS(tune_trial(ctx, bp, base, t.window, ch, alt_bps[a], &cost, &rs, &ds, nullptr));
+        if (rs < best_res) { best_res = rs; t.res_chunk = ch; }
+        if (ds < best_delta) { best_delta = ds; t.delta_bps = alt_bps[a]; }
+    }
+    (*cache)[key] = t;
+    *best = t;
     return STMF_OK;
 }
 
@@ -794,12 +906,7 @@ stmf_status sweep_rows_host(stmf_problem *P, int rows)
     const int nr = rows < P->m ? rows : P->m;
     for (int i = 0; i < nr && P->ctl_host->more; ++i) {
         if (P->ctl_host->dirty_k != -2) CS(refresh(P));
-        CK(launch_row_begin(st, P, 0));
-        while (true) {
-            CK(launch_window_body(st, P, 0));
-            CS(read_ctl(P));
-            if (P->ctl_host->row_done) break;
-        }
+        CS(row_host(P));
     }
     return STMF_OK;
 }
@@ -822,22 +929,24 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
         if (b.trace_cap < 0 || (b.trace_cap > 0 && !b.trace))
             return fail(ctx, STMF_ERR_INVALID, "problem %d: trace_cap without a trace buffer", q);
     }
-    std::vector<int> win(nprob, o.window ? (o.window + 1) / 2 * 2 : 0);
+    std::vector<tune_result> tr(nprob, tune_result{o.window ? (o.window + 1) / 2 * 2 : 0, 0, 0});
     if (!o.window)
-        for (int q = 0; q < nprob; ++q) CS(tune_window(ctx, probs[q], o, &win[q]));
+        for (int q = 0; q < nprob; ++q) CS(tune_shapes(ctx, probs[q], o, &tr[q]));
     if (tuned)
-        for (int q = 0; q < nprob; ++q) tuned[q] = win[q];
+        for (int q = 0; q < nprob; ++q) tuned[q] = tr[q].window;
 
     std::vector<stmf_problem *> Ps(nprob, nullptr);
     struct Free { std::vector<stmf_problem *> &v; ~Free() { for (auto *p : v) problem_free(p); } } fr{Ps};
     for (int q = 0; q < nprob; ++q) {
         const stmf_batch_problem &b = probs[q];
         stmf_options po = o;
-        po.window = win[q]; po.seed = b.seed; po.perm = nullptr; po.picks = nullptr; po.U0 = nullptr;
+        po.window = tr[q].window; po.seed = b.seed; po.perm = nullptr; po.picks = nullptr; po.U0 = nullptr;
         po.V0 = nullptr;
         po.trace = b.trace_cap > 0 ? b.trace : nullptr;
         po.trace_cap = b.trace_cap > 0 ? b.trace_cap : 0;
         CS(fastmf_begin(ctx, b.m, b.n, b.r, b.R, b.ldr, b.mask, b.ldm_words, &po, &Ps[q]));
+        if (!o.res_chunk) Ps[q]->res_chunk_sel = tr[q].res_chunk;          // the caller's shapes win
+        if (!o.delta_blocks_per_sm) Ps[q]->delta_bps_sel = tr[q].delta_bps;
         CK(set_ctl(Ps[q], &stmf_ctl::sweep_target, b.sweeps));
         CK(set_ctl(Ps[q], &stmf_ctl::eps, o.eps));
         CK(set_ctl(Ps[q], &stmf_ctl::sweep, 0));
@@ -915,7 +1024,7 @@ void stmf_destroy(stmf_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->ws) cudaFree(ctx->ws);
-    delete static_cast<std::map<uint64_t, int> *>(ctx->tune);
+    delete static_cast<std::map<uint64_t, tune_result> *>(ctx->tune);
     delete ctx;
 }
 

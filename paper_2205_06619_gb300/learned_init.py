@@ -13,9 +13,18 @@ Pipeline (every numeric step runs in the library's CUDA kernels):
      and compute V").
 
 Gauge: U (x) V is unchanged by U_.l + c, V_l. - c (any c per component) and by
-permuting components.  Targets are made canonical: each component is shifted
-so that max_t V_lt = 0, and components are ordered by decreasing mean of
-U_.l.  Row shifts of R move U_i. with them, hence the median centring.
+permuting components.  Targets are made canonical (stmf_mlp_targets): each
+component is shifted so that max_t V_lt = 0, and components are ordered by
+decreasing sum over rows of U_.l.  Row shifts of R move U_i. with them, hence
+the median centring.
+
+Two kinds of target.  "canonical": the gauge-fixed row itself, components in
+the global order above.  "sorted": the gauge-fixed row's values sorted in
+decreasing order, a target that does not depend on how the components are
+numbered; at initialisation the predicted values are handed to the
+components in the order of a reference start's row (Random Acol's), so the
+start keeps Acol's structure (which component leads in which row) and takes
+its magnitudes from the network.
 """
 from __future__ import annotations
 
@@ -36,16 +45,6 @@ def init_params(rank, seed=0):
                            np.zeros(rank)]).astype(np.float32)
 
 
-def canonical_U(U, V):
-    """Gauge-fixed U (numpy, m x r): per component, shift so that max_t V_lt = 0,
-    then order components by decreasing mean of U_.l."""
-    U = np.asarray(U, dtype=np.float64); V = np.asarray(V, dtype=np.float64)
-    c = V.max(axis=1)
-    Uc = U + c[None, :]
-    order = np.argsort(-Uc.mean(axis=0), kind="stable")
-    return Uc[:, order]
-
-
 def gene_like(m, n, seed):
     """A gene-expression style matrix (the recipe of the 1000 x 5000 workload at
     another size): planted rank 10, 0.5*log2(1+LogNormal(3,2)) factors,
@@ -54,9 +53,10 @@ def gene_like(m, n, seed):
     return R, M
 
 
-def training_set(count, m, n, rank, sweeps, seed):
-    """(X, T) CUDA tensors: sketches and canonical targets from `count`
-    factorizations computed by the method (one batched launch)."""
+def training_set(count, m, n, rank, sweeps, seed, target="canonical", chunk=64):
+    """(X, T) CUDA tensors: sketches and targets ("canonical" or "sorted") from
+    `count` factorizations computed by the method (batched launches of up to
+    `chunk` problems)."""
     import torch
     rng = np.random.default_rng(seed)
     probs, masks = [], []
@@ -64,13 +64,14 @@ def training_set(count, m, n, rank, sweeps, seed):
         R, M = gene_like(m, n, int(rng.integers(0, 2**31 - 1)))
         probs.append(dict(R=torch.from_numpy(R).cuda(), mask_words=api.pack_mask(M), rank=rank, sweeps=sweeps,
                           seed=int(rng.integers(0, 2**31 - 1))))
-    outs, _ = api.factorize_batched(probs)
+    outs = []
+    for a in range(0, count, chunk):
+        outs += api.factorize_batched(probs[a:a + chunk])[0]
     X, T = [], []
     for pr, (U, V, _) in zip(probs, outs):
         sk, md = api.row_sketch(pr["R"], pr["mask_words"])
-        Uc = canonical_U(U.cpu().numpy(), V.cpu().numpy())
         X.append(sk)
-        T.append(torch.from_numpy((Uc - md.cpu().numpy()[:, None].astype(np.float64)).astype(np.float32)).cuda())
+        T.append(api.mlp_targets(U, V, md, sorted_rows=(target == "sorted")))
     return torch.cat(X), torch.cat(T)
 
 
@@ -92,7 +93,10 @@ def train(X, T, rank, epochs=30, batch=256, lr=1e-3, seed=0):
     return net, hist
 
 
-def predict_U(net, R, mask_words):
-    """U (m x r, caller frame) = MLP(sketch) + row median."""
-    sk, md = api.row_sketch(R, mask_words)
-    return net.forward(sk) + md[:, None]
+def predict_U(net, R, mask_words, U_ref=None):
+    """U (m x r, caller frame) = MLP(sketch) + row median.  With U_ref (a net
+    trained on "sorted" targets, and a reference start in the same frame),
+    row s's predicted values, in decreasing order, go to its components in
+    decreasing order of U_ref[s]."""
+    Y = net.predict(R, mask_words)
+    return Y if U_ref is None else api.assign_by_rank(Y, U_ref.contiguous())

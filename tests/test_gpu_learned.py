@@ -1,6 +1,8 @@
 """GPU parity of the learned-initialisation kernels with the FP64 reference:
-row sketch (bit-exact), MLP forward and gradient (BF16 weights, FP32
-accumulation; the reference uses the same BF16-rounded weights)."""
+row sketch, training targets and rank hand-over (bit-exact), MLP forward,
+prediction and gradient (tensor-core products with BF16 operands and FP32
+accumulation; the reference rounds the same operands to BF16 and computes in
+FP64)."""
 import numpy as np
 import pytest
 
@@ -26,11 +28,12 @@ def _bf16_params(p, r):
 
 
 # Gradient tolerance, relative to the sum of the absolute values of the terms
-# of each entry: FP32 sums of up to 256 products, with the error of the
-# forward pass's FP32 activations carried through three layers (about 2^-24
-# per operation and level; measured up to 2^-14 on GB300).  2^-12 still fails
-# when one batch row's term (1/256 of the magnitude or more) is dropped or has
-# its sign flipped.
+# of each entry.  Both sides multiply the same BF16 operands (exact in FP32);
+# the library sums in FP32 (about 2^-24 per addition, up to 256 terms), and an
+# operand computed in FP32 on the GPU and in FP64 in the reference can round to
+# neighbouring BF16 values (2^-8 of one term).  2^-12 still fails when one
+# batch row's term (1/256 of the magnitude or more) is dropped or has its
+# sign flipped.
 GRAD_TOL = 2.0 ** -12
 
 
@@ -40,7 +43,7 @@ def _grad_magnitudes(params, X, T, r):
     its absolute value and the reference's ReLU masks), with the output's
     dependence on the forward pass's FP32 rounding folded into |dY|."""
     W1, W2, W3, b1, b2, b3 = om.split(params, r)
-    Y, (X, h1, h2) = om.forward(params, X, r)
+    Y, (X, h1, h2) = om.forward(params, X, r, bf16_operands=True)
     B = X.shape[0]
     Yabs = np.abs(h2) @ np.abs(W3) + np.abs(b3)
     dY = (np.abs(Y - np.asarray(T, dtype=np.float64)) + 2.0 ** -10 * Yabs) * (2.0 / (B * r))
@@ -59,10 +62,10 @@ def _clear_relu_edges(params, X, r, rng, rel=2.0 ** -14):
     compare two different (equally correct) derivatives."""
     W1, W2, W3, b1, b2, b3 = om.split(params, r)
     for _ in range(200):
-        z1 = X @ W1 + b1
+        z1 = om.bf16(X) @ W1 + b1
         m1 = np.abs(X) @ np.abs(W1) + np.abs(b1)
         h1 = np.maximum(z1, 0.0)
-        z2 = h1 @ W2 + b2
+        z2 = om.bf16(h1) @ W2 + b2
         m2 = h1 @ np.abs(W2) + np.abs(b2)
         bad = np.any(np.abs(z1) <= rel * m1, axis=1) | np.any(np.abs(z2) <= rel * m2, axis=1)
         if not bad.any():
@@ -98,10 +101,10 @@ def test_mlp_forward_and_gradient_match_reference(r, B):
     X = _clear_relu_edges(pb, X, r, rng)
     Xg, Tg = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
     Y = net.forward(Xg).cpu().numpy()
-    eY, _ = om.forward(pb, X, r)
+    eY, _ = om.forward(pb, X, r, bf16_operands=True)
     assert np.allclose(Y, eY, rtol=1e-4, atol=1e-4)
     loss, g = net.gradient(Xg, Tg)
-    eloss, eg = om.loss_and_grad(pb, X, T, r)
+    eloss, eg = om.loss_and_grad(pb, X, T, r, bf16_operands=True)
     assert abs(loss - eloss) <= 1e-4 * abs(eloss)
     # element by element: every gradient entry is a sum of products; the
     # library forms them in FP32 (BF16 weights, the same as the reference's),
@@ -109,6 +112,43 @@ def test_mlp_forward_and_gradient_match_reference(r, B):
     # sum of the absolute values of its terms
     ag = _grad_magnitudes(pb, X, T, r)
     assert np.all(np.abs(g - eg) <= GRAD_TOL * ag), np.max(np.abs(g - eg) / np.maximum(ag, 1e-30))
+
+
+@pytest.mark.parametrize("m,n,r", [(37, 301, 10), (5, 9, 1), (130, 64, 32)])
+def test_targets_and_rank_assignment_match_the_oracle(m, n, r):
+    """stmf_mlp_targets (canonical and sorted) and stmf_assign_by_rank against
+    the oracle, bit for bit: the same FP32 operations, the same FP64
+    row-order sums for the component order, and exact sorts."""
+    from paper_2205_06619_gb300 import api
+    rng = np.random.default_rng(m + n + r)
+    U = rng.normal(0, 3, size=(m, r)).astype(np.float32)
+    V = rng.normal(0, 3, size=(r, n)).astype(np.float32)
+    med = rng.normal(size=m).astype(np.float32)
+    Ug, Vg, mg = (torch.from_numpy(x).cuda() for x in (U, V, med))
+    for srt in (False, True):
+        T = api.mlp_targets(Ug, Vg, mg, sorted_rows=srt).cpu().numpy()
+        assert np.array_equal(T, om.targets(U, V, med, srt)), srt
+    Y = rng.normal(size=(m, r)).astype(np.float32)
+    Ur = rng.integers(0, 4, size=(m, r)).astype(np.float32)      # ties in every row
+    out = api.assign_by_rank(torch.from_numpy(Y).cuda(), torch.from_numpy(Ur).cuda()).cpu().numpy()
+    assert np.array_equal(out, om.assign_by_rank(Y, Ur))
+
+
+def test_predict_matches_the_reference():
+    """MLP.predict (stmf_mlp_predict: sketch, forward, plus the median, in one
+    call) against the reference forward pass on the oracle's sketch."""
+    from paper_2205_06619_gb300 import api
+    r = 6
+    rng = np.random.default_rng(8)
+    p = learned_init.init_params(r, seed=2)
+    p[-(2 * om.HID + r):] = rng.normal(0, 0.1, size=2 * om.HID + r).astype(np.float32)
+    net = api.MLP(r, p)
+    R, M, _, _ = synth.lognormal_planted(40, 500, 4, 0.05, 0.7, 4)
+    U0 = net.predict(torch.from_numpy(R).cuda(), api.pack_mask(M)).cpu().numpy()
+    sk, med = om.row_sketch(R, M)
+    sk32 = (sk + med[:, None]).astype(np.float32) - med[:, None].astype(np.float32)   # FP32 as the library
+    Y, _ = om.forward(_bf16_params(p, r), sk32, r, bf16_operands=True)
+    assert np.allclose(U0, Y + med[:, None], rtol=1e-4, atol=1e-4)
 
 
 def test_training_reduces_loss_and_init_is_valid():

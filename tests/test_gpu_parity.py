@@ -269,15 +269,43 @@ def test_factorize_in_pieces_equals_one_call():
     assert [t[:6] for t in tr1] == [t[:6] for t in fz.trace_records()]
 
 
-def test_graph_and_host_driven_loops_agree(monkeypatch):
-    """The device-driven sweep (one CUDA graph with conditional nodes) and the
-    host-driven loop make the same decisions."""
+@pytest.mark.parametrize("window", [4, 64])
+def test_graph_and_host_driven_loops_agree(monkeypatch, window):
+    """The device-driven sweep (one CUDA graph with conditional nodes, the
+    evaluation of window t beside the decision of window t-1) and the
+    host-driven loop (the same steps one after another) make the same
+    decisions and do the same work, including the windows evaluated ahead
+    and dropped at the end of a row (at most one per row visit)."""
     R, M, _, _ = synth.uniform_planted(40, 50, 3, 0.01, 0.8, seed=41)
-    a = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=2, seed=2, trace_cap=200)
+    a = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=2, seed=2, trace_cap=200, window=window)
     monkeypatch.setenv("STMF_NO_GRAPH", "1")
-    b = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=2, seed=2, trace_cap=200)
+    b = api().factorize(tg(R), api().pack_mask(M), rank=3, sweeps=2, seed=2, trace_cap=200, window=window)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     assert [t[:6] for t in a[3]] == [t[:6] for t in b[3]]
+    for key in ("candidates_tried", "candidates_issued", "windows", "accepted", "candidates_discarded",
+                "eval_launches", "eval_candidates"):
+        assert a[2][key] == b[2][key], key
+    rows = 2 * 40
+    assert 0 < a[2]["candidates_discarded"] <= rows * window
+
+
+def test_launch_shapes_never_change_a_decision():
+    """Phase 1's column chunk and phase 2's blocks per SM (the shapes the
+    batched form's autotuner picks) change the grouping of the work, never a
+    decision: the same trace and factors for every shape tried, and the
+    reports name the shapes used."""
+    R, M, _, _ = synth.uniform_planted(70, 900, 4, 0.01, 0.8, seed=43)
+    runs = []
+    for shapes in (None, (32, 1), (40, 3), (128, 5)):
+        runs.append(api().factorize(tg(R), api().pack_mask(M), rank=4, sweeps=2, seed=6, trace_cap=300,
+                                    window=16, shapes=shapes))
+        if shapes is not None:
+            assert runs[-1][2]["eval_res_chunk"] == shapes[0]
+    for U, V, rep, tr in runs[1:]:
+        assert torch.equal(U, runs[0][0]) and torch.equal(V, runs[0][1])
+        assert [t[:6] for t in tr] == [t[:6] for t in runs[0][3]]
+    with pytest.raises(api().StmfError, match="res_chunk"):
+        api().factorize(tg(R), api().pack_mask(M), rank=4, sweeps=1, shapes=(36, 0))
 
 
 # ------------------------------------------------------ checkpoint / faults
