@@ -51,17 +51,21 @@ sys.path.insert(0, ROOT)
 METRIC = "FastSTMF sweeps/s & max-plus Gop/s (% FP32 peak); time-to-error vs plain"
 # k_delta DRAM bytes per launch (read + write), ncu capture of the gene
 # workload, valid for the kernel source it was taken on
-EVAL_TRAFFIC = {"source_sha256_prefix": "c42953f68e1d4a66", "bytes": 47.69e6, "workload": "gene"}
+# DRAM bytes per phase-2 launch from the ncu captures in profiles/ (gene
+# workload, 64 candidates, cold), valid for the captured source only
+EVAL_TRAFFIC = {"workload": "gene",
+                "k_delta8": {"source_sha256_prefix": "9f429065321a3c31", "bytes": 47.74e6}}
 CPU_ROWS = 20   # rows of the CPU baseline (the reference arm's first rows)
 
 
-def eval_traffic(workload_name):
+def eval_traffic(workload_name, kernel):
     import hashlib
+    rec = EVAL_TRAFFIC.get(kernel)
     src = os.path.join(ROOT, "paper_2205_06619_gb300", "csrc", "kernels_eval.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if sha != EVAL_TRAFFIC["source_sha256_prefix"] or workload_name != EVAL_TRAFFIC["workload"]:
+    if rec is None or sha != rec["source_sha256_prefix"] or workload_name != EVAL_TRAFFIC["workload"]:
         return None
-    return EVAL_TRAFFIC["bytes"]
+    return rec["bytes"]
 
 
 def measured_peaks(api):
@@ -540,7 +544,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shapes", default="", help="launch shapes of the window evaluation: "
-                                               "res_chunk,delta_blocks_per_sm (0: default)")
+                                               "res_chunk,delta_blocks_per_sm[,delta_tile_rows] (0: default)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         raise SystemExit("at least 3 warm-up sweeps are required")
@@ -696,17 +700,20 @@ def main():
                          "candidates_per_window": d["candidates_issued"] / max(d["windows"], 1),
                          "candidates_dropped_per_sweep": d["candidates_discarded"] / args.steps,
                          "launch_shapes": {"k_res_chunk": rep1["eval_res_chunk"],
-                                           "k_delta_blocks": rep1["eval_delta_blocks"]},
+                                           "k_delta_blocks": rep1["eval_delta_blocks"],
+                                           "k_delta_tile_rows": rep1["eval_delta_rows"]},
                          "window_eval_share_of_sweep": d["eval_ns"] * 1e-9 / t_timed if world == 1 else None},
         "peaks_measured_Tops": {k: rd(v) for k, v in peaks.items()},
         "heldout_rmse": heldout,
-        "roofline": {"kernel": "k_delta (phase 2 of a window: error changes of all its candidates)",
+        "roofline": {"kernel": "%s (phase 2 of a window: error changes of all its candidates)"
+                               % ("k_delta8" if rep1["eval_delta_rows"] == 8 else "k_delta"),
                      "bound": "alu", "achieved": ach_del, "peak": peaks["k_delta_mix"], "unit": "Top/s",
                      "frac": ach_del / peaks["k_delta_mix"] if ach_del else None,
                      "peak_source": "measured at run time (stmf_peak_addmax mode 6: k_delta's instruction mix, "
                                     "4 algorithmic ops per entry and candidate)",
                      "frac_of_addmax_1to1": ach_del / peaks["addmax_1to1"] if ach_del else None,
-                     "traffic": eval_traffic(args.workload), "traffic_unit": "bytes per launch",
+                     "traffic": eval_traffic(args.workload, "k_delta8" if rep1["eval_delta_rows"] == 8 else "k_delta"),
+                     "traffic_unit": "bytes per launch",
                      "launches": d["eval_launches"], "avg_launch_us": d["eval_delta_ns"] / 1e3 / max(d["eval_launches"], 1),
                      "candidates_per_launch": ec / max(d["eval_launches"], 1),
                      "ops_per_given_entry_per_candidate": 4,

@@ -158,9 +158,12 @@ typedef struct {
                             per task, a multiple of 8 in [32, 128]; 0 = the
                             library's choice (the batched form's autotuner, else a
                             wave heuristic).  Never changes a result.             */
-    int delta_blocks_per_sm; /* phase 2's blocks per SM, 1..5; 0 = the library's
-                            choice.  Never changes a decision (the error sums
-                            are regrouped, within their float-float accuracy).   */
+    int delta_blocks_per_sm; /* phase 2's blocks per SM, 1..5 (1..4 with 8-row
+                            tiles); 0 = the library's choice.                    */
+    int delta_tile_rows; /* phase 2's thread tile: 4 or 8 rows of one float4 column;
+                            0 = the library's choice.  The last two regroup the
+                            FP32 error sums (within their float-float accuracy)
+                            and change no decision but at an exact tie.          */
 } stmf_options;
 
 /* A trace record: sweep, row (oriented, permuted index), position of the kept
@@ -194,6 +197,7 @@ typedef struct {
                                      candidates_issued)                              */
     int64_t eval_res_chunk;   /* phase 1's column chunk (launch shape in use)          */
     int64_t eval_delta_blocks;/* phase 2's blocks per launch (launch shape in use)     */
+    int64_t eval_delta_rows;  /* phase 2's thread-tile rows (launch shape in use)      */
 } stmf_report;
 
 /* Context: binds a device and a stream (cudaStream_t passed as void*; NULL =

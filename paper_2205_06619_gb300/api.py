@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("perm", C.c_void_p), ("picks", C.c_void_p), ("U0", C.c_void_p),
                 ("trace", C.c_void_p), ("trace_cap", C.c_int64), ("V0", C.c_void_p), ("mlp", C.c_void_p),
                 ("selection", C.c_int), ("strategy", C.c_int), ("res_chunk", C.c_int),
-                ("delta_blocks_per_sm", C.c_int)]
+                ("delta_blocks_per_sm", C.c_int), ("delta_tile_rows", C.c_int)]
 
 
 # selections of (j, k) within a row (Section "The ByRow strategy"; stmf.h STMF_SEL_*)
@@ -80,7 +80,7 @@ class Report(C.Structure):
                 ("eval_launches", C.c_int64), ("eval_candidates", C.c_int64), ("seconds", C.c_double),
                 ("candidates_screened", C.c_int64), ("eval_res_ns", C.c_int64), ("eval_delta_ns", C.c_int64),
                 ("candidates_discarded", C.c_int64), ("eval_res_chunk", C.c_int64),
-                ("eval_delta_blocks", C.c_int64)]
+                ("eval_delta_blocks", C.c_int64), ("eval_delta_rows", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -303,8 +303,8 @@ def selection_stats_noalloc(R, U, V, mask_words=None, td_col=None, colhist=None)
 
 def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=0, perm=None, picks=None,
              U0=None, trace=None, mlp=None, V0=None, selection="TD_A", strategy="ByRow", shapes=None):
-    """shapes: (res_chunk, delta_blocks_per_sm), the window evaluation's launch
-    shapes (0: the library's choice); they never change a decision."""
+    """shapes: (res_chunk, delta_blocks_per_sm[, delta_tile_rows]), the window
+    evaluation's launch shapes (0: the library's choice)."""
     o = Options()
     load().stmf_default_options(C.byref(o))
     o.sweeps, o.eps, o.window, o.select, o.precision, o.acol_p, o.seed = (
@@ -313,6 +313,7 @@ def _options(sweeps=1, eps=0.0, window=0, select=0, precision=0, acol_p=5, seed=
     o.strategy = _strategy(strategy)
     if shapes is not None:
         o.res_chunk, o.delta_blocks_per_sm = int(shapes[0]), int(shapes[1])
+        o.delta_tile_rows = int(shapes[2]) if len(shapes) > 2 else 0
     keep = []
     if perm is not None:
         a = np.ascontiguousarray(perm, dtype=np.int32); keep.append(a); o.perm = a.ctypes.data
@@ -412,7 +413,7 @@ def factorize(R, mask_words=None, rank=3, sweeps=1, eps=0.0, window=0, select=0,
               seed=0, perm=None, picks=None, U0=None, trace_cap=0, mlp=None, V0=None, selection="TD_A",
               strategy="ByRow", shapes=None):
     """FastSTMF (Algorithm 3) on the device.  R: float32 CUDA (m x n).
-    shapes: (res_chunk, delta_blocks_per_sm) launch shapes, or None.
+    shapes: (res_chunk, delta_blocks_per_sm[, delta_tile_rows]) launch shapes, or None.
     mlp: an MLP (learned initialisation on the device) or None (Random Acol).
     selection: "TD_A" (the method as published), "TD_B", "TD" or "SEQ"
     (Section "The ByRow strategy").  strategy: "ByRow" (Algorithm 3),

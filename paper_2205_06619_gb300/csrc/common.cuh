@@ -192,8 +192,9 @@ struct stmf_problem {
     double *fc;        // STMF_WMAX candidate errors
     // launch shapes of the window evaluation (0: the defaults; set by the
     // autotuner before any capture): phase 1's column chunk (a multiple of 8
-    // in [32, 128]) and phase 2's blocks per SM (1..5)
-    int res_chunk_sel, delta_bps_sel;
+    // in [32, 128]), phase 2's blocks per SM (1..5; 1..4 with 8-row tiles)
+    // and phase 2's thread-tile rows (4 or 8)
+    int res_chunk_sel, delta_bps_sel, delta_rows_sel;
     // FP16 screening (precision 1; all NULL otherwise)
     int precision;
     __half *Rh, *P1h, *P2h;
@@ -289,7 +290,10 @@ cudaError_t launch_res(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_delta(cudaStream_t st, stmf_problem *P);
 int delta_grid(const stmf_problem *P);
 int delta_parts(const stmf_problem *P);   // phase-2 partials per candidate
+bool delta_fills_gpu(const stmf_problem *P);   // phase 2 alone has a tile for every resident block
 int delta_depth(const stmf_problem *P);
+int delta_rows(const stmf_problem *P);
+cudaError_t delta_prepare();                     // before any capture
 int res_chunk(const stmf_problem *P);            // phase 1's column chunk for this problem
 int res_chunk_default(const stmf_problem *P);    // the wave heuristic's choice
 cudaError_t launch_select_single(cudaStream_t st, stmf_problem *P);

@@ -251,6 +251,118 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
     if (tid == 0) atomicMax(&win->ev_t1, global_ns());
 }
 
+// Phase 2 with tiles of 8 rows x DEL_COLS columns (a thread owns 8 rows x
+// one float4 column): the per-candidate costs (the V' load, the U' loads,
+// the accumulator update, the loop and the k test) spread over 32 entries
+// instead of 16, and each V' load feeds twice the entries.  P1 and E stay in
+// registers; P2 and A of the thread's entries go to its own slots of dynamic
+// shared memory (never shared, so no barrier) and are read only to rebuild E
+// when k changes.  The per-entry arithmetic is that of tile_change; the tile
+// sum is a fixed tree of depth 5.
+constexpr int DEL8_ROWS = 8;
+constexpr int DEL8_MAX_BLOCKS_PER_SM = 4;   // at 4 the kernel spills about 35 registers; at 3 it fits in 163
+constexpr size_t DEL8_SMEM = (size_t)DEL8_ROWS * DEL_THREADS * (sizeof(float4) + sizeof(uint32_t));
+
+__device__ __forceinline__ float tile_change8(const float (&p1)[8][4], const float (&E)[8][4], const float4 u0,
+                                              const float4 u1, const float4 v)
+{
+    const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    const float2 v01 = f2(v.x, v.y), v23 = f2(v.z, v.w);
+    float2 q[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float2 ui = f2(uu[i], uu[i]);
+        const float2 x01 = __fadd2_rn(ui, v01), x23 = __fadd2_rn(ui, v23);
+        const float2 n01 = f2(-fmaxf(E[i][0], x01.x), -fmaxf(E[i][1], x01.y));
+        const float2 n23 = f2(-fmaxf(E[i][2], x23.x), -fmaxf(E[i][3], x23.y));
+        const float2 d01 = __fadd2_rn(f2(p1[i][0], p1[i][1]), n01);
+        const float2 d23 = __fadd2_rn(f2(p1[i][2], p1[i][3]), n23);
+        q[i] = __fadd2_rn(d01, d23);
+    }
+    const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[0], q[1]), __fadd2_rn(q[2], q[3])),
+                                __fadd2_rn(__fadd2_rn(q[4], q[5]), __fadd2_rn(q[6], q[7])));
+    return s.x + s.y;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(DEL_THREADS, MINB) k_delta8(stmf_problem P, int ntiles, int nct)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4 *sP2 = reinterpret_cast<float4 *>(dsm);                                   // [8][DEL_THREADS]
+    uint32_t *sA = reinterpret_cast<uint32_t *>(dsm + sizeof(float4) * DEL8_ROWS * DEL_THREADS);   // [8][DEL_THREADS]
+    __shared__ float sacc[STMF_WMAX][DEL_THREADS];
+    __shared__ __align__(16) float su[STMF_WMAX][DEL8_ROWS];
+    __shared__ int sslot[STMF_WMAX], sk[STMF_WMAX];
+    stmf_win *win = P.win;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) atomicMin(&win->ev_d0, global_ns());
+    const int na = win->na;
+    if (tid < na) {
+        const int slot = win->alist[tid];
+        sslot[tid] = slot;
+        sk[tid] = P.cand[8 * slot + 1];
+    }
+    for (int c = 0; c < na; ++c) sacc[c][tid] = 0.f;
+    const int nf4 = P.np >> 2;
+    for (int tile = blockIdx.x; tile < ntiles && na > 0; tile += gridDim.x) {
+        const int s0 = (tile / nct) * DEL8_ROWS;
+        const int f = (tile % nct) * DEL_THREADS + tid;
+        __syncthreads();
+        for (int e = tid; e < DEL8_ROWS * na; e += DEL_THREADS)
+            su[e >> 3][e & 7] = P.Uc[(size_t)sslot[e >> 3] * P.mp + s0 + (e & 7)];
+        __syncthreads();
+        if (f >= nf4) continue;
+
+        float p1[8][4], E[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const size_t o4 = (size_t)(s0 + i) * nf4 + f;
+            const float4 y = reinterpret_cast<const float4 *>(P.P1)[o4];
+            sP2[i * DEL_THREADS + tid] = reinterpret_cast<const float4 *>(P.P2)[o4];
+            sA[i * DEL_THREADS + tid] = reinterpret_cast<const uint32_t *>(P.A)[o4];
+            p1[i][0] = y.x; p1[i][1] = y.y; p1[i][2] = y.z; p1[i][3] = y.w;
+        }
+        const float4 *Vc4 = reinterpret_cast<const float4 *>(P.Vc) + f;
+        const size_t ldv4 = (size_t)nf4;
+        float4 vn0 = Vc4[sslot[0] * ldv4];
+        float4 vn1 = na > 1 ? Vc4[sslot[1] * ldv4] : vn0;
+        int kcur = -1;
+#pragma unroll 1
+        for (int c = 0; c < na; ++c) {
+            const float4 v4 = vn0;
+            vn0 = vn1;
+            if (c + 2 < na) vn1 = Vc4[sslot[c + 2] * ldv4];
+            const int k = sk[c];
+            if (k != kcur) {
+                kcur = k;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float4 z = sP2[i * DEL_THREADS + tid];
+                    const uint32_t a = sA[i * DEL_THREADS + tid];
+                    const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj)
+                        E[i][jj] = ((a >> (8 * jj)) & 0xffu) == (uint32_t)k ? zz[jj] : p1[i][jj];
+                }
+            }
+            const float4 u0 = *reinterpret_cast<const float4 *>(&su[c][0]);
+            const float4 u1 = *reinterpret_cast<const float4 *>(&su[c][4]);
+            sacc[c][tid] += tile_change8(p1, E, u0, u1, v4);
+        }
+    }
+    __syncthreads();
+    // block partial of every candidate, fixed order, float-float
+    for (int c = warp; c < na; c += DEL_THREADS / 32) {
+        stmf_ff x = {0.f, 0.f};
+        for (int t = lane; t < DEL_THREADS; t += 32) x = ff_add(x, {sacc[c][t], 0.f});
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+            x = ff_add(x, {__shfl_xor_sync(FULLM, x.hi, o), __shfl_xor_sync(FULLM, x.lo, o)});
+        if (lane == 0) P.part[(size_t)sslot[c] * gridDim.x + blockIdx.x] = make_float2(x.hi, x.lo);
+    }
+    if (tid == 0) atomicMax(&win->ev_t1, global_ns());
+}
+
 int res_blocks(int rows) { return (rows + RES_THREADS * RES_RPT - 1) / (RES_THREADS * RES_RPT); }
 
 // Phase-1 tasks all have the same size, so a launch takes as many waves as
@@ -286,22 +398,65 @@ int res_chunk(const stmf_problem *P)
     return (c >= 32 && c <= RES_CHUNK_MAX && c % 8 == 0) ? c : res_chunk_heuristic(P);
 }
 
+// Phase 2's thread-tile height: 4 (k_delta) or 8 (k_delta8).  By default 8
+// where the 8-row tiles still give every resident block (3 per SM) one,
+// else 4: measured on the 1000 x 5000 workload, k_delta8 at 3 blocks per SM
+// takes 69.3 us per 64-candidate window against 73.8 us for k_delta at 5 (at
+// 4 blocks per SM it spills and takes 82.3 us).
+int delta_rows(const stmf_problem *P)
+{
+    if (P->delta_rows_sel == 4 || P->delta_rows_sel == DEL8_ROWS) return P->delta_rows_sel;
+    const long long t8 = (long long)((P->m + DEL8_ROWS - 1) / DEL8_ROWS) * ((P->np + DEL_COLS - 1) / DEL_COLS);
+    return t8 >= 3LL * P->ctx->num_sms ? DEL8_ROWS : 4;
+}
+
+int delta_tiles(const stmf_problem *P)
+{
+    const int tr = delta_rows(P);
+    return ((P->m + tr - 1) / tr) * ((P->np + DEL_COLS - 1) / DEL_COLS);
+}
+
+int delta_bps(const stmf_problem *P)
+{
+    const int cap = delta_rows(P) == DEL8_ROWS ? DEL8_MAX_BLOCKS_PER_SM : DEL_BLOCKS_PER_SM;
+    const int def = delta_rows(P) == DEL8_ROWS ? 3 : DEL_BLOCKS_PER_SM;
+    return (P->delta_bps_sel >= 1 && P->delta_bps_sel <= cap) ? P->delta_bps_sel : def;
+}
+
 int delta_grid(const stmf_problem *P)
 {
-    const int ntiles = ((P->m + 3) / 4) * ((P->np + DEL_COLS - 1) / DEL_COLS);
-    const int bps = (P->delta_bps_sel >= 1 && P->delta_bps_sel <= DEL_BLOCKS_PER_SM) ? P->delta_bps_sel
-                                                                                     : DEL_BLOCKS_PER_SM;
-    const int cap = bps * P->ctx->num_sms;
+    const int ntiles = delta_tiles(P);
+    const int cap = delta_bps(P) * P->ctx->num_sms;
     return ntiles < cap ? ntiles : cap;
 }
 
 int delta_parts(const stmf_problem *P) { return delta_grid(P); }
 
-int delta_depth(const stmf_problem *P)
+bool delta_fills_gpu(const stmf_problem *P)
 {
     const int ntiles = ((P->m + 3) / 4) * ((P->np + DEL_COLS - 1) / DEL_COLS);
+    return ntiles >= DEL_BLOCKS_PER_SM * P->ctx->num_sms;
+}
+
+int delta_depth(const stmf_problem *P)
+{
+    const int ntiles = delta_tiles(P);
     const int g = delta_grid(P);
-    return 5 + (ntiles + g - 1) / g;      // tile tree (4) + one per tile a block takes
+    // per term: the change, the tile tree (4 levels for 4 rows, 5 for 8),
+    // the pair sum, and one addition per tile a block takes
+    return (delta_rows(P) == DEL8_ROWS ? 6 : 5) + (ntiles + g - 1) / g;
+}
+
+// Set-up before any capture: the dynamic shared memory of the 8-row kernel.
+cudaError_t delta_prepare()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_delta8<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DEL8_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_delta8<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DEL8_SMEM);
+    if (e == cudaSuccess) done = true;
+    return e;
 }
 
 cudaError_t launch_res(cudaStream_t st, stmf_problem *P)
@@ -316,7 +471,12 @@ cudaError_t launch_res(cudaStream_t st, stmf_problem *P)
 cudaError_t launch_delta(cudaStream_t st, stmf_problem *P)
 {
     const int nct = (P->np + DEL_COLS - 1) / DEL_COLS;
-    const int ntiles = ((P->m + 3) / 4) * nct;
-    k_delta<<<delta_grid(P), DEL_THREADS, 0, st>>>(*P, ntiles, nct);
+    const int ntiles = delta_tiles(P), grid = delta_grid(P);
+    if (delta_rows(P) == DEL8_ROWS) {
+        if (delta_bps(P) >= 4) k_delta8<4><<<grid, DEL_THREADS, DEL8_SMEM, st>>>(*P, ntiles, nct);
+        else k_delta8<3><<<grid, DEL_THREADS, DEL8_SMEM, st>>>(*P, ntiles, nct);
+    } else {
+        k_delta<<<grid, DEL_THREADS, 0, st>>>(*P, ntiles, nct);
+    }
     return cudaGetLastError();
 }

@@ -159,6 +159,7 @@ stmf_status problem_alloc(stmf_ctx *ctx, int m, int n, int r, int window, stmf_p
     A(dalloc(&P->part, 2 * win_part_elems(ctx->num_sms)));   // float2
     A(dalloc(&P->fc, 2 * STMF_WMAX)); A(dalloc(&P->ctl, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&P->ctl_host, sizeof(stmf_ctl));
+    if (e == cudaSuccess) e = delta_prepare();
     if (e != cudaSuccess) {
         problem_free(P);
         cudaGetLastError();
@@ -391,7 +392,10 @@ stmf_status capture_step(stmf_ctx *ctx, cudaStream_t cap, cudaStream_t side, cud
 // evaluation is dropped.
 // With job = true the row loop is wrapped in a device-driven sweep loop:
 //   job_begin; while (h_sweep) { <row loop>; sweep_end }
-stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, bool job, cudaStream_t cap)
+// and the job starts after the nodes deps (nullable); *end (nullable)
+// receives its last node, the sweep loop.
+stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, bool job, cudaStream_t cap,
+                              const cudaGraphNode_t *deps = nullptr, size_t ndeps = 0, cudaGraphNode_t *end = nullptr)
 {
     stmf_ctx *ctx = P->ctx;
     cudaGraphConditionalHandle hr, hd, hw, hp, hs = 0;
@@ -413,8 +417,9 @@ stmf_status add_problem_nodes(stmf_problem *P, cudaGraph_t top, cudaGraph_t g, b
     cudaGraph_t target = g;
     if (job) {
         cudaGraphNode_t jb = nullptr, wsw = nullptr;
-        CS(capture_into(ctx, cap, g, nullptr, 0, [&](cudaStream_t c) { return launch_job_begin(c, P); }, &jb));
+        CS(capture_into(ctx, cap, g, deps, ndeps, [&](cudaStream_t c) { return launch_job_begin(c, P); }, &jb));
         CS(add_conditional(ctx, g, &jb, 1, hs, cudaGraphCondTypeWhile, &wsw, &target));
+        if (end) *end = wsw;
     }
     cudaGraphNode_t sb = nullptr, wrow = nullptr;
     CS(capture_into(ctx, cap, target, nullptr, 0, [&](cudaStream_t c) { return launch_sweep_begin(c, P, 1); }, &sb));
@@ -560,8 +565,11 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
         return fail(ctx, STMF_ERR_INVALID, "strategy %d unknown", o.strategy);
     if (o.res_chunk && (o.res_chunk < 32 || o.res_chunk > 128 || o.res_chunk % 8))
         return fail(ctx, STMF_ERR_INVALID, "res_chunk %d: 0 or a multiple of 8 in [32, 128]", o.res_chunk);
-    if (o.delta_blocks_per_sm < 0 || o.delta_blocks_per_sm > 5)
-        return fail(ctx, STMF_ERR_INVALID, "delta_blocks_per_sm %d outside [0, 5]", o.delta_blocks_per_sm);
+    if (o.delta_tile_rows != 0 && o.delta_tile_rows != 4 && o.delta_tile_rows != 8)
+        return fail(ctx, STMF_ERR_INVALID, "delta_tile_rows %d: 0, 4 or 8", o.delta_tile_rows);
+    if (o.delta_blocks_per_sm < 0 || o.delta_blocks_per_sm > (o.delta_tile_rows == 8 ? 4 : 5))
+        return fail(ctx, STMF_ERR_INVALID, "delta_blocks_per_sm %d outside [0, %d]", o.delta_blocks_per_sm,
+                    o.delta_tile_rows == 8 ? 4 : 5);
     const bool elem = o.strategy == STMF_STRATEGY_BYELEMENT, mat = o.strategy == STMF_STRATEGY_BYMATRIX;
     if ((elem || mat) && (o.perm || o.selection != STMF_SEL_TD_A))
         return fail(ctx, STMF_ERR_INVALID, "the %s strategy takes no row permutation and no selection",
@@ -591,6 +599,7 @@ stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, i
     P->strategy = o.strategy;
     P->res_chunk_sel = o.res_chunk;
     P->delta_bps_sel = o.delta_blocks_per_sm;
+    P->delta_rows_sel = o.delta_tile_rows;
     {
         cudaError_t ea = cudaSuccess;
         if (P->sel == STMF_SEL_TD) {
@@ -783,6 +792,7 @@ void fill_report(const stmf_problem *P, stmf_report *rep)
     rep->candidates_discarded = c.discarded;
     rep->eval_res_chunk = res_chunk(P);
     rep->eval_delta_blocks = delta_grid(P);
+    rep->eval_delta_rows = delta_rows(P);
 }
 
 stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *trace_out, int64_t trace_cap)
@@ -805,7 +815,8 @@ stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *tra
 // ------------------------------------------------------------ autotuner
 // Autotuner of a problem size class: the candidate window (candidates
 // evaluated per device pass), then the launch shapes of the window
-// evaluation (phase 1's column chunk, phase 2's blocks per SM).  Each trial
+// evaluation (phase 1's column chunk, phase 2's thread-tile rows and blocks
+// per SM).  Each trial
 // runs the first rows of sweep 0 on a scratch copy of the problem,
 // host-driven.  Decisions depend on none of these, so only speed is compared:
 // a window is scored by the evaluations' summed device durations, plus the
@@ -817,7 +828,7 @@ stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *tra
 constexpr double TUNE_WINDOW_OVERHEAD_S = 12e-6;
 
 struct tune_result {
-    int window, res_chunk, delta_bps;
+    int window, res_chunk, delta_bps, delta_rows;
 };
 
 stmf_status fastmf_begin(stmf_ctx *ctx, int m0, int n0, int r, const float *R, int ldr, const uint32_t *mask,
@@ -832,11 +843,12 @@ uint64_t size_class(int m, int n, int r)
     return ((uint64_t)lg << 8) | (uint64_t)r;
 }
 
-// One trial: window w, shapes (chunk, bps) (0: defaults).  Returns the
-// window score and the mean phase durations; *chunk_used is the chunk the
-// trial ran with.
+// One trial: window w, shapes (chunk, bps, rows) (0: defaults).  Returns
+// the window score and the mean phase durations; *chunk_used, *rows_used
+// (nullable) the chunk and tile rows the trial ran with.
 stmf_status tune_trial(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_options &base, int w, int chunk,
-                       int bps, double *cost, double *res_s, double *delta_s, int *chunk_used)
+                       int bps, int rows, double *cost, double *res_s, double *delta_s, int *chunk_used,
+                       int *rows_used = nullptr)
 {
     stmf_options o = base;
     o.window = w; o.trace = nullptr; o.trace_cap = 0; o.perm = nullptr; o.picks = nullptr; o.U0 = nullptr;
@@ -846,7 +858,9 @@ stmf_status tune_trial(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_o
     CS(fastmf_begin(ctx, bp.m, bp.n, bp.r, bp.R, bp.ldr, bp.mask, bp.ldm_words, &o, &P));
     P->res_chunk_sel = chunk;
     P->delta_bps_sel = bps;
+    P->delta_rows_sel = rows;
     if (chunk_used) *chunk_used = res_chunk(P);
+    if (rows_used) *rows_used = delta_rows(P);
     stmf_status s = sweep_rows_host(P, 24);
     if (s == STMF_OK) s = read_ctl(P);
     if (s != STMF_OK) { problem_free(P); return s; }
@@ -870,25 +884,32 @@ stmf_status tune_shapes(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_
     if (it != cache->end()) { *best = it->second; return STMF_OK; }
     const int trial[3] = {16, 32, 64};
     double best_cost = 1e30, best_res = 0.0, best_delta = 0.0;
-    tune_result t = {64, 0, 0};
-    int chunk0 = 0;
+    tune_result t = {64, 0, 0, 0};
+    int chunk0 = 0, rows0 = 4;
     for (int w : trial) {
         double cost, rs, ds;
-        int cu;
-        CS(tune_trial(ctx, bp, base, w, 0, 0, &cost, &rs, &ds, &cu));
-        if (cost < best_cost) { best_cost = cost; t.window = w; best_res = rs; best_delta = ds; chunk0 = cu; }
+        int cu, ru;
+        CS(tune_trial(ctx, bp, base, w, 0, 0, 0, &cost, &rs, &ds, &cu, &ru));
+        if (cost < best_cost) {
+            best_cost = cost; t.window = w; best_res = rs; best_delta = ds; chunk0 = cu; rows0 = ru;
+        }
     }
-    // shapes at the chosen window: the heuristic's chunk and 5 blocks per SM
-    // (measured above) against neighbouring chunks and fewer blocks per SM
+    // shapes at the chosen window: the defaults (measured above: the wave
+    // heuristic's chunk, the size's default tile rows) against neighbouring
+    // chunks and the other tile heights and blocks per SM
     t.res_chunk = chunk0;
-    t.delta_bps = 5;
-    const int alt_chunk[2] = {chunk0 - 8, chunk0 + 8}, alt_bps[2] = {4, 3};
+    t.delta_rows = rows0;
+    t.delta_bps = rows0 == 8 ? 3 : 5;
+    // phase 2: the other tile height at its default blocks per SM, and the
+    // default height at one block per SM fewer
+    const int other = rows0 == 8 ? 4 : 8;
+    const int alt[2][3] = {{chunk0 - 8, other, other == 8 ? 3 : 5}, {chunk0 + 8, rows0, t.delta_bps - 1}};
     for (int a = 0; a < 2; ++a) {
-        const int ch = alt_chunk[a] >= 32 && alt_chunk[a] <= 128 ? alt_chunk[a] : chunk0;
+        const int ch = alt[a][0] >= 32 && alt[a][0] <= 128 ? alt[a][0] : chunk0;
         double cost, rs, ds;
-        CS(tune_trial(ctx, bp, base, t.window, ch, alt_bps[a], &cost, &rs, &ds, nullptr));
+        CS(tune_trial(ctx, bp, base, t.window, ch, alt[a][2], alt[a][1], &cost, &rs, &ds, nullptr));
         if (rs < best_res) { best_res = rs; t.res_chunk = ch; }
-        if (ds < best_delta) { best_delta = ds; t.delta_bps = alt_bps[a]; }
+        if (ds < best_delta) { best_delta = ds; t.delta_bps = alt[a][2]; t.delta_rows = alt[a][1]; }
     }
     (*cache)[key] = t;
     *best = t;
@@ -929,7 +950,7 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
         if (b.trace_cap < 0 || (b.trace_cap > 0 && !b.trace))
             return fail(ctx, STMF_ERR_INVALID, "problem %d: trace_cap without a trace buffer", q);
     }
-    std::vector<tune_result> tr(nprob, tune_result{o.window ? (o.window + 1) / 2 * 2 : 0, 0, 0});
+    std::vector<tune_result> tr(nprob, tune_result{o.window ? (o.window + 1) / 2 * 2 : 0, 0, 0, 0});
     if (!o.window)
         for (int q = 0; q < nprob; ++q) CS(tune_shapes(ctx, probs[q], o, &tr[q]));
     if (tuned)
@@ -946,7 +967,10 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
         po.trace_cap = b.trace_cap > 0 ? b.trace_cap : 0;
         CS(fastmf_begin(ctx, b.m, b.n, b.r, b.R, b.ldr, b.mask, b.ldm_words, &po, &Ps[q]));
         if (!o.res_chunk) Ps[q]->res_chunk_sel = tr[q].res_chunk;          // the caller's shapes win
-        if (!o.delta_blocks_per_sm) Ps[q]->delta_bps_sel = tr[q].delta_bps;
+        if (!o.delta_tile_rows && !o.delta_blocks_per_sm) {
+            Ps[q]->delta_rows_sel = tr[q].delta_rows;
+            Ps[q]->delta_bps_sel = tr[q].delta_bps;
+        }
         CK(set_ctl(Ps[q], &stmf_ctl::sweep_target, b.sweeps));
         CK(set_ctl(Ps[q], &stmf_ctl::eps, o.eps));
         CK(set_ctl(Ps[q], &stmf_ctl::sweep, 0));
@@ -958,7 +982,17 @@ stmf_status batched(stmf_ctx *ctx, int nprob, const stmf_batch_problem *probs, c
     cudaGraph_t g;
     CK(cudaGraphCreate(&g, 0));
     struct GG { cudaGraph_t g; cudaGraphExec_t x = nullptr; ~GG() { if (x) cudaGraphExecDestroy(x); cudaGraphDestroy(g); } } gg{g};
-    for (int q = 0; q < nprob; ++q) CS(add_problem_nodes(Ps[q], g, g, true, cap));
+    // A problem whose phase 2 fills every SM on its own gains nothing from
+    // running beside another such problem and loses L2: each one's per-window
+    // working set (R, R^T, P1, P2, A) fits the L2 only alone.  Those run one
+    // after another, in input order; the smaller ones run side by side.
+    cudaGraphNode_t prev = nullptr;
+    for (int q = 0; q < nprob; ++q) {
+        const bool big = delta_fills_gpu(Ps[q]);
+        cudaGraphNode_t end = nullptr;
+        CS(add_problem_nodes(Ps[q], g, g, true, cap, big && prev ? &prev : nullptr, big && prev ? 1 : 0, &end));
+        if (big) prev = end;
+    }
     CK(cudaGraphInstantiate(&gg.x, g, 0));
     cudaStream_t st = ctx->stream;
     CK(cudaStreamSynchronize(st));

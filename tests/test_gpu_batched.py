@@ -45,6 +45,25 @@ def test_batched_equals_one_at_a_time(window):
         assert abs(rep["f_final"] - rep1["f_final"]) <= 1e-9 * max(rep1["f_final"], 1e-30)
 
 
+def test_batched_chains_gpu_filling_problems():
+    """Problems whose phase 2 fills every SM alone (here 800 x 2048: 800
+    tiles for 760 resident blocks) run one after another inside the batched
+    graph, the small ones beside them; every problem still makes the decisions
+    of its single call."""
+    from paper_2205_06619_gb300 import api
+    rng = np.random.default_rng(17)
+    probs = []
+    for q, (m, n, r) in enumerate([(800, 2048, 3), (40, 60, 2), (2048, 800, 4), (800, 2100, 2), (30, 90, 3)]):
+        R, M, _, _ = synth.uniform_planted(m, n, r, 0.01, 0.7, seed=int(rng.integers(1 << 30)))
+        probs.append(dict(R=_tg(R), mask_words=api.pack_mask(M), rank=r, sweeps=1, seed=q))
+    outs, _ = api.factorize_batched(probs, window=16)
+    for pr, (U, V, rep) in zip(probs, outs):
+        U1, V1, rep1, _ = api.factorize(pr["R"], pr["mask_words"], rank=pr["rank"], sweeps=1, seed=pr["seed"],
+                                        window=16)
+        assert torch.equal(U, U1) and torch.equal(V, V1)
+        assert rep["candidates_tried"] == rep1["candidates_tried"]
+
+
 def _ragged_problems(seed, count, sweeps):
     """Problems of uneven shape (tall and wide), rank and density, with their
     host copies for the oracle."""

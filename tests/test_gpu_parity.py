@@ -296,16 +296,19 @@ def test_launch_shapes_never_change_a_decision():
     reports name the shapes used."""
     R, M, _, _ = synth.uniform_planted(70, 900, 4, 0.01, 0.8, seed=43)
     runs = []
-    for shapes in (None, (32, 1), (40, 3), (128, 5)):
+    for shapes in (None, (32, 1), (40, 3), (128, 5), (0, 3, 8), (48, 4, 8), (0, 1, 8)):
         runs.append(api().factorize(tg(R), api().pack_mask(M), rank=4, sweeps=2, seed=6, trace_cap=300,
                                     window=16, shapes=shapes))
         if shapes is not None:
-            assert runs[-1][2]["eval_res_chunk"] == shapes[0]
+            assert runs[-1][2]["eval_res_chunk"] == (shapes[0] or runs[0][2]["eval_res_chunk"])
+            assert runs[-1][2]["eval_delta_rows"] == (shapes[2] if len(shapes) > 2 else 4)
     for U, V, rep, tr in runs[1:]:
         assert torch.equal(U, runs[0][0]) and torch.equal(V, runs[0][1])
         assert [t[:6] for t in tr] == [t[:6] for t in runs[0][3]]
     with pytest.raises(api().StmfError, match="res_chunk"):
         api().factorize(tg(R), api().pack_mask(M), rank=4, sweeps=1, shapes=(36, 0))
+    with pytest.raises(api().StmfError, match="delta_tile_rows"):
+        api().factorize(tg(R), api().pack_mask(M), rank=4, sweeps=1, shapes=(0, 0, 6))
 
 
 # ------------------------------------------------------ checkpoint / faults
