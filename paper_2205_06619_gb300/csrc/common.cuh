@@ -111,6 +111,7 @@ struct stmf_ctl {
     int pos;           // next position in the column order (of the next window to build)
     int wj;            // j-candidates of the next window to build (each gives F-ULF, F-URF)
     int wj0;           // j-candidates of a row's first window (what the previous row consumed)
+    int wj0_fixed;     // > 0: every row's first window takes this many instead (autotuner trials)
     int wmax;          // candidates per window (upper bound, even)
     int ncand_row;     // candidates of the row decided so far
     int nbuilt;        // candidates of the row put in windows so far (runs one window ahead)

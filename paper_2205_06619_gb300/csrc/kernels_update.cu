@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, const stmf_win 
                 const int used = kept >= 0 ? P.cand[8 * kept + 3] + 1 : ctl->ncand_row / 2;
                 int w = 2;
                 while (w < used && w < ctl->wmax / 2) w *= 2;
-                ctl->wj0 = w;
+                ctl->wj0 = ctl->wj0_fixed > 0 ? ctl->wj0_fixed : w;
             }
             if (in_graph) {
                 cudaGraphSetConditional(h_win, ctl->row_done ? 0u : 1u);

@@ -813,20 +813,19 @@ stmf_status fastmf_end(stmf_problem *P, float *U_out, float *V_out, int32_t *tra
 }
 
 // ------------------------------------------------------------ autotuner
-// Autotuner of a problem size class: the candidate window (candidates
-// evaluated per device pass), then the launch shapes of the window
+// Autotuner of a problem size class: the launch shapes of the window
 // evaluation (phase 1's column chunk, phase 2's thread-tile rows and blocks
-// per SM).  Each trial
-// runs the first rows of sweep 0 on a scratch copy of the problem,
-// host-driven.  Decisions depend on none of these, so only speed is compared:
-// a window is scored by the evaluations' summed device durations, plus the
-// windows evaluated ahead and dropped, plus a fixed cost per pipeline step
-// (the graph step, and what of the decision branch is not hidden); the
-// shapes are scored per phase by the mean duration of that phase's launches,
-// from the same trials (at the chosen window, every trial evaluates the same
-// windows).
-constexpr double TUNE_WINDOW_OVERHEAD_S = 12e-6;
-
+// per SM).  Each trial runs the first rows of sweep 0 on a scratch copy of the
+// problem, host-driven, with every window full (64 candidates from each
+// row's start, as in the later sweeps, where rows scan thousands of
+// candidates); the shapes change no decision, so every trial evaluates the
+// same windows, and each phase's shape is scored by the mean %globaltimer
+// span of its own kernel.  The window itself is not tuned: it is the largest
+// (64 candidates), since a row's first window already adapts to what the
+// previous row consumed, and trials in sweep 0, whose rows keep an update
+// within a few windows, favoured smaller caps that multiply the windows of
+// the later sweeps (four problems of up to 1294 x 6914 entries, 10 sweeps
+// each, ran at 0.80x of one problem at a time with them).
 struct tune_result {
     int window, res_chunk, delta_bps, delta_rows;
 };
@@ -856,6 +855,11 @@ stmf_status tune_trial(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_o
     o.seed = bp.seed;
     stmf_problem *P = nullptr;
     CS(fastmf_begin(ctx, bp.m, bp.n, bp.r, bp.R, bp.ldr, bp.mask, bp.ldm_words, &o, &P));
+    const int full = P->ctl_host->wmax / 2;                   // j-candidates of a full window
+    stmf_status sf = STMF_OK;
+    if (set_ctl(P, &stmf_ctl::wj0_fixed, full) != cudaSuccess || set_ctl(P, &stmf_ctl::wj0, full) != cudaSuccess)
+        sf = fail(ctx, STMF_ERR_CUDA, "autotuner set-up failed");
+    if (sf != STMF_OK) { problem_free(P); return sf; }
     P->res_chunk_sel = chunk;
     P->delta_bps_sel = bps;
     P->delta_rows_sel = rows;
@@ -867,7 +871,7 @@ stmf_status tune_trial(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_o
     const stmf_ctl &c = *P->ctl_host;
     // a dropped window costs about as much per candidate as the others
     const double dropped = c.eval_cands ? c.eval_ns * 1e-9 * (double)c.discarded / (double)c.eval_cands : 0.0;
-    *cost = c.eval_ns * 1e-9 + dropped + c.windows * TUNE_WINDOW_OVERHEAD_S;
+    *cost = c.eval_ns * 1e-9 + dropped;
     const double nl = c.eval_launches > 0 ? (double)c.eval_launches : 1.0;
     *res_s = c.res_ns * 1e-9 / nl;
     *delta_s = c.delta_ns * 1e-9 / nl;
@@ -882,21 +886,13 @@ stmf_status tune_shapes(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_
     const uint64_t key = size_class(bp.m, bp.n, bp.r);
     auto it = cache->find(key);
     if (it != cache->end()) { *best = it->second; return STMF_OK; }
-    const int trial[3] = {16, 32, 64};
-    double best_cost = 1e30, best_res = 0.0, best_delta = 0.0;
-    tune_result t = {64, 0, 0, 0};
+    tune_result t = {STMF_WMAX, 0, 0, 0};
+    double cost, best_res, best_delta;
     int chunk0 = 0, rows0 = 4;
-    for (int w : trial) {
-        double cost, rs, ds;
-        int cu, ru;
-        CS(tune_trial(ctx, bp, base, w, 0, 0, 0, &cost, &rs, &ds, &cu, &ru));
-        if (cost < best_cost) {
-            best_cost = cost; t.window = w; best_res = rs; best_delta = ds; chunk0 = cu; rows0 = ru;
-        }
-    }
-    // shapes at the chosen window: the defaults (measured above: the wave
-    // heuristic's chunk, the size's default tile rows) against neighbouring
-    // chunks and the other tile heights and blocks per SM
+    CS(tune_trial(ctx, bp, base, t.window, 0, 0, 0, &cost, &best_res, &best_delta, &chunk0, &rows0));
+    // the defaults (measured above: the wave heuristic's chunk, the size's
+    // default tile rows) against neighbouring chunks and the other tile
+    // heights and blocks per SM
     t.res_chunk = chunk0;
     t.delta_rows = rows0;
     t.delta_bps = rows0 == 8 ? 3 : 5;
