@@ -256,14 +256,17 @@ __global__ void __launch_bounds__(DEL_THREADS, DEL_BLOCKS_PER_SM) k_delta(stmf_p
 // the accumulator update, the loop and the k test) spread over 32 entries
 // instead of 16, and each V' load feeds twice the entries.  P1 and E stay in
 // registers; P2 and A of the thread's entries go to its own slots of dynamic
-// shared memory (never shared, so no barrier) and are read only to rebuild E
-// when k changes.  The per-entry arithmetic is that of tile_change; the tile
-// sum is a fixed tree of depth 5.
+// shared memory (never shared, so no barrier) and are read only when k
+// changes.  Per entry the term is tile_change's P1 - max(E, x), formed as
+// min(P1 - E, P1 - x): rounding is monotone, so fl(P1 - max(E, x)) =
+// min(fl(P1 - E), fl(P1 - x)) bit for bit, and P1 - E (0 where A != k) is
+// rebuilt per k-group in place of E; no negation is needed.  The tile sum is
+// a fixed tree of depth 5.
 constexpr int DEL8_ROWS = 8;
 constexpr int DEL8_MAX_BLOCKS_PER_SM = 4;   // at 4 the kernel spills about 35 registers; at 3 it fits in 163
 constexpr size_t DEL8_SMEM = (size_t)DEL8_ROWS * DEL_THREADS * (sizeof(float4) + sizeof(uint32_t));
 
-__device__ __forceinline__ float tile_change8(const float (&p1)[8][4], const float (&E)[8][4], const float4 u0,
+__device__ __forceinline__ float tile_change8(const float (&p1)[8][4], const float (&B)[8][4], const float4 u0,
                                               const float4 u1, const float4 v)
 {
     const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
@@ -273,10 +276,11 @@ __device__ __forceinline__ float tile_change8(const float (&p1)[8][4], const flo
     for (int i = 0; i < 8; ++i) {
         const float2 ui = f2(uu[i], uu[i]);
         const float2 x01 = __fadd2_rn(ui, v01), x23 = __fadd2_rn(ui, v23);
-        const float2 n01 = f2(-fmaxf(E[i][0], x01.x), -fmaxf(E[i][1], x01.y));
-        const float2 n23 = f2(-fmaxf(E[i][2], x23.x), -fmaxf(E[i][3], x23.y));
-        const float2 d01 = __fadd2_rn(f2(p1[i][0], p1[i][1]), n01);
-        const float2 d23 = __fadd2_rn(f2(p1[i][2], p1[i][3]), n23);
+        // P1 - x with one rounding: fma(-1, x, P1)
+        const float2 y01 = __ffma2_rn(x01, f2(-1.f, -1.f), f2(p1[i][0], p1[i][1]));
+        const float2 y23 = __ffma2_rn(x23, f2(-1.f, -1.f), f2(p1[i][2], p1[i][3]));
+        const float2 d01 = f2(fminf(B[i][0], y01.x), fminf(B[i][1], y01.y));
+        const float2 d23 = f2(fminf(B[i][2], y23.x), fminf(B[i][3], y23.y));
         q[i] = __fadd2_rn(d01, d23);
     }
     const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(q[0], q[1]), __fadd2_rn(q[2], q[3])),
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(DEL_THREADS, MINB) k_delta8(stmf_problem P, in
         __syncthreads();
         if (f >= nf4) continue;
 
-        float p1[8][4], E[8][4];
+        float p1[8][4], B[8][4];   // B = P1 - E of the current k (0 where A != k)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const size_t o4 = (size_t)(s0 + i) * nf4 + f;
@@ -342,12 +346,12 @@ __global__ void __launch_bounds__(DEL_THREADS, MINB) k_delta8(stmf_problem P, in
                     const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj)
-                        E[i][jj] = ((a >> (8 * jj)) & 0xffu) == (uint32_t)k ? zz[jj] : p1[i][jj];
+                        B[i][jj] = ((a >> (8 * jj)) & 0xffu) == (uint32_t)k ? p1[i][jj] - zz[jj] : 0.f;
                 }
             }
             const float4 u0 = *reinterpret_cast<const float4 *>(&su[c][0]);
             const float4 u1 = *reinterpret_cast<const float4 *>(&su[c][4]);
-            sacc[c][tid] += tile_change8(p1, E, u0, u1, v4);
+            sacc[c][tid] += tile_change8(p1, B, u0, u1, v4);
         }
     }
     __syncthreads();
