@@ -228,7 +228,7 @@ def progress(msg):
 
 
 def run_batch(args):
-    """Many independent problems (SURVEY config 3: 64 problems, rows
+    """Many independent problems (the batched workload: 64 problems, rows
     U{100..2000}, columns U{200..8000}, ranks U{3..20}, given densities
     U[0.2, 0.9], generated as the small workload, 10 sweeps each).  The
     autotuner runs first, on jobs of 0 sweeps (its trials are cached per size
