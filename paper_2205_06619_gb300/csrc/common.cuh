@@ -93,7 +93,7 @@ struct stmf_win {
     int exhausted;     // 1 when the window reached the end of the row's candidates
     int live;          // 1 from the build until the decision
     int screened;      // candidates the FP16 screen proved non-improving
-    int pad_;
+    int placeholder;   // 1: an empty window that only keeps the pipeline in step (short rows)
     int ulist[STMF_WMAX / 2], vlist[STMF_WMAX / 2];   // phase-1 slots per type, grouped by k
     int alist[STMF_WMAX];                             // phase-2 slots, grouped by k
     unsigned long long ev_t0, ev_t1;   // earliest start / latest end of the window's evaluation
@@ -112,6 +112,14 @@ struct stmf_ctl {
     int wj;            // j-candidates of the next window to build (each gives F-ULF, F-URF)
     int wj0;           // j-candidates of a row's first window (what the previous row consumed)
     int wj0_fixed;     // > 0: every row's first window takes this many instead (autotuner trials)
+    // short rows: a row whose predecessor decided at most two real windows
+    // follows each of its first two real windows with an empty placeholder,
+    // so that no window is evaluated before the decision that may end the row
+    int short_row;     // this row runs so
+    int real_prev;     // real windows the previous row decided
+    int real_built;    // real windows built in this row
+    int real_dec;      // real windows decided in this row
+    int last_ph;       // 1 if the last window built is a placeholder
     int wmax;          // candidates per window (upper bound, even)
     int ncand_row;     // candidates of the row decided so far
     int nbuilt;        // candidates of the row put in windows so far (runs one window ahead)

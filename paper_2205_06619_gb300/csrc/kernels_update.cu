@@ -315,12 +315,29 @@ __device__ __forceinline__ void ctl_store(stmf_ctl *dst, const stmf_ctl &src)
 __device__ __forceinline__ void window_opened(stmf_win *win, stmf_ctl *ctl)
 {
     win->live = 1;
+    win->placeholder = 0;
+    ctl->real_built += 1;
+    ctl->last_ph = 0;
     win->screened = 0;
     win->ev_t0 = ~0ull;
     win->ev_t1 = 0ull;
     win->ev_r1 = 0ull;
     win->ev_d0 = ~0ull;
     ctl->wj = min(ctl->wj * 2, ctl->wmax / 2);
+}
+
+// An empty window in the pipeline (short rows): it takes no position, slot
+// number or size, so the windows after it are those of the unpipelined loop;
+// its evaluation does no work and its decision only moves the row on.
+__device__ __forceinline__ void open_placeholder(stmf_win *win, stmf_ctl *ctl)
+{
+    win->nc = 0; win->na = 0; win->nu = 0; win->nv = 0;
+    win->exhausted = 0;
+    win->live = 1;
+    win->placeholder = 1;
+    win->screened = 0;
+    win->ev_t0 = ~0ull; win->ev_t1 = 0ull; win->ev_r1 = 0ull; win->ev_d0 = ~0ull;
+    ctl->last_ph = 1;
 }
 
 // Window of candidates (Algorithm 3; selections of Section "The ByRow
@@ -704,8 +721,9 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, const stmf_win 
         win->live = 0;
         ctl->issued += nc;
         ctl->windows += 1;
+        ctl->real_dec += win->placeholder ? 0 : 1;
         ctl->screened += win->screened;
-        if (win->ev_t1 > win->ev_t0) {
+        if (nc > 0 && win->ev_t1 > win->ev_t0) {     // an empty window does no evaluation work
             ctl->eval_ns += (long long)(win->ev_t1 - win->ev_t0);
             ctl->eval_launches += 1;
             ctl->eval_cands += nc;
@@ -741,6 +759,7 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, const stmf_win 
             }
             if (ctl->row_done) {
                 if (other && other->live) ctl->discarded += other->nc;   // evaluated ahead, not needed
+                ctl->real_prev = ctl->real_dec;
                 if (mat) {
                     ctl->more = 0;            // ByMatrix: one iteration per sweep
                 } else if (elem) {
@@ -780,7 +799,14 @@ __global__ void __launch_bounds__(1024) k_select(stmf_problem P, const stmf_win 
     }
     if (!single) {
         __syncthreads();
-        if (!ctl->row_done) {
+        // every thread takes the same branch (build_window has barriers):
+        // the choice is read from the shared control block before anyone writes it
+        const bool ph = !ctl->row_done && ctl->short_row && !ctl->last_ph && ctl->real_built <= 2;
+        const bool real = !ctl->row_done && !ph;
+        __syncthreads();
+        if (ph) {
+            if (tid == 0) open_placeholder(win, ctl);
+        } else if (real) {
             build_window(P, ctl, false);
         } else if (tid == 0) {
             win->nc = 0;          // nothing to seed or evaluate in this buffer
@@ -811,6 +837,10 @@ __global__ void __launch_bounds__(1024) k_row_begin(stmf_problem P, stmf_win *ot
         ctl->kept = 0;
         ctl->row_done = 0;
         ctl->win_row = 0;
+        ctl->short_row = ctl->real_prev <= 2;
+        ctl->real_built = 0;
+        ctl->real_dec = 0;
+        ctl->last_ph = 0;
         other->nc = 0;
         other->live = 0;
         // more row visits in this sweep than the sweep has rows (segments):
@@ -889,6 +919,7 @@ __global__ void k_single(stmf_problem P, int i, int j, int k, int type)
     win->na = 1;
     win->exhausted = 1;
     win->live = 1;
+    win->placeholder = 0;
     win->screened = 0;
     win->ev_t0 = ~0ull;
     win->ev_t1 = 0ull;

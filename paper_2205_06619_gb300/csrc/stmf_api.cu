@@ -712,7 +712,7 @@ cudaError_t set_loop_bounds(stmf_problem *P)
     long long lim = P->n;
     if (P->sel == STMF_SEL_SEQ) lim = (long long)P->n * P->r;
     if (P->strategy == STMF_STRATEGY_BYELEMENT || P->strategy == STMF_STRATEGY_BYMATRIX) lim = (long long)P->m * P->n;
-    long long win_cap = lim + 2;
+    long long win_cap = lim + 4;          // and up to two placeholders (short rows)
     const char *t = getenv("STMF_TEST_WINDOW_CAP");
     if (t && atoll(t) > 0) win_cap = atoll(t);
     cudaError_t e = set_ctl(P, &stmf_ctl::win_cap, win_cap);
