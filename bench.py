@@ -54,7 +54,7 @@ METRIC = "FastSTMF sweeps/s & max-plus Gop/s (% FP32 peak); time-to-error vs pla
 # DRAM bytes per phase-2 launch from the ncu captures in profiles/ (gene
 # workload, 64 candidates, cold), valid for the captured source only
 EVAL_TRAFFIC = {"workload": "gene",
-                "k_delta8": {"source_sha256_prefix": "853298a09f4baff7", "bytes": 47.74e6}}
+                "k_delta8": {"source_sha256_prefix": "4baf8c918da4073a", "bytes": 47.74e6}}
 CPU_ROWS = 20   # rows of the CPU baseline (the reference arm's first rows)
 
 

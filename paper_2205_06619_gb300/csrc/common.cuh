@@ -304,7 +304,6 @@ int delta_depth(const stmf_problem *P);
 int delta_rows(const stmf_problem *P);
 cudaError_t delta_prepare();                     // before any capture
 int res_chunk(const stmf_problem *P);            // phase 1's column chunk for this problem
-int res_chunk_default(const stmf_problem *P);    // the wave heuristic's choice
 cudaError_t launch_select_single(cudaStream_t st, stmf_problem *P);
 cudaError_t launch_single(cudaStream_t st, stmf_problem *P, int i, int j, int k, int type);
 cudaError_t launch_commit0(cudaStream_t st, stmf_problem *P);

@@ -394,8 +394,6 @@ int res_chunk_heuristic(const stmf_problem *P)
 
 }  // namespace
 
-int res_chunk_default(const stmf_problem *P) { return res_chunk_heuristic(P); }
-
 int res_chunk(const stmf_problem *P)
 {
     const int c = P->res_chunk_sel;

@@ -843,11 +843,10 @@ uint64_t size_class(int m, int n, int r)
 }
 
 // One trial: window w, shapes (chunk, bps, rows) (0: defaults).  Returns
-// the window score and the mean phase durations; *chunk_used, *rows_used
+// the mean durations of the two phases' launches; *chunk_used, *rows_used
 // (nullable) the chunk and tile rows the trial ran with.
 stmf_status tune_trial(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_options &base, int w, int chunk,
-                       int bps, int rows, double *cost, double *res_s, double *delta_s, int *chunk_used,
-                       int *rows_used = nullptr)
+                       int bps, int rows, double *res_s, double *delta_s, int *chunk_used, int *rows_used = nullptr)
 {
     stmf_options o = base;
     o.window = w; o.trace = nullptr; o.trace_cap = 0; o.perm = nullptr; o.picks = nullptr; o.U0 = nullptr;
@@ -869,9 +868,6 @@ stmf_status tune_trial(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_o
     if (s == STMF_OK) s = read_ctl(P);
     if (s != STMF_OK) { problem_free(P); return s; }
     const stmf_ctl &c = *P->ctl_host;
-    // a dropped window costs about as much per candidate as the others
-    const double dropped = c.eval_cands ? c.eval_ns * 1e-9 * (double)c.discarded / (double)c.eval_cands : 0.0;
-    *cost = c.eval_ns * 1e-9 + dropped;
     const double nl = c.eval_launches > 0 ? (double)c.eval_launches : 1.0;
     *res_s = c.res_ns * 1e-9 / nl;
     *delta_s = c.delta_ns * 1e-9 / nl;
@@ -887,9 +883,9 @@ stmf_status tune_shapes(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_
     auto it = cache->find(key);
     if (it != cache->end()) { *best = it->second; return STMF_OK; }
     tune_result t = {STMF_WMAX, 0, 0, 0};
-    double cost, best_res, best_delta;
+    double best_res, best_delta;
     int chunk0 = 0, rows0 = 4;
-    CS(tune_trial(ctx, bp, base, t.window, 0, 0, 0, &cost, &best_res, &best_delta, &chunk0, &rows0));
+    CS(tune_trial(ctx, bp, base, t.window, 0, 0, 0, &best_res, &best_delta, &chunk0, &rows0));
     // the defaults (measured above: the wave heuristic's chunk, the size's
     // default tile rows) against neighbouring chunks and the other tile
     // heights and blocks per SM
@@ -902,8 +898,8 @@ stmf_status tune_shapes(stmf_ctx *ctx, const stmf_batch_problem &bp, const stmf_
     const int alt[2][3] = {{chunk0 - 8, other, other == 8 ? 3 : 5}, {chunk0 + 8, rows0, t.delta_bps - 1}};
     for (int a = 0; a < 2; ++a) {
         const int ch = alt[a][0] >= 32 && alt[a][0] <= 128 ? alt[a][0] : chunk0;
-        double cost, rs, ds;
-        CS(tune_trial(ctx, bp, base, t.window, ch, alt[a][2], alt[a][1], &cost, &rs, &ds, nullptr));
+        double rs, ds;
+        CS(tune_trial(ctx, bp, base, t.window, ch, alt[a][2], alt[a][1], &rs, &ds, nullptr));
         if (rs < best_res) { best_res = rs; t.res_chunk = ch; }
         if (ds < best_delta) { best_delta = ds; t.delta_bps = alt[a][2]; t.delta_rows = alt[a][1]; }
     }
