@@ -42,6 +42,8 @@ def test_default_options_without_gpu():
     o = api.Options()
     lib.stmf_default_options(ctypes.byref(o))
     assert o.sweeps == 1 and o.acol_p == 5 and o.window == 0 and o.seed == 0 and not o.trace and not o.mlp
+    # the evaluation's launch shapes default to the library's choice
+    assert (o.res_chunk, o.delta_blocks_per_sm, o.delta_tile_rows) == (0, 0, 0)
 
 
 def test_struct_layouts_match_the_library():
@@ -131,3 +133,8 @@ def test_options_carry_selection_and_strategy():
     assert (o.selection, o.strategy) == (api.SELECTIONS["TD_A"], api.STRATEGIES["ByMatrix"])
     # the two fields sit at the end of the C struct, after the MLP handle
     assert api.Options.strategy.offset > api.Options.selection.offset > api.Options.mlp.offset
+    # launch shapes: (res_chunk, delta_blocks_per_sm[, delta_tile_rows])
+    o, _ = api._options(1, shapes=(72, 3, 8))
+    assert (o.res_chunk, o.delta_blocks_per_sm, o.delta_tile_rows) == (72, 3, 8)
+    o, _ = api._options(1, shapes=(40, 4))
+    assert (o.res_chunk, o.delta_blocks_per_sm, o.delta_tile_rows) == (40, 4, 0)
